@@ -1,0 +1,264 @@
+"""FP64 CPU oracle for the small-scale spectrum estimators of Philcox (arXiv:2005.01739).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` leg of ``bench.py`` may import this
+package.  The product path (``paper_2005_01739_gb300``) never imports it, and the
+two share no code: not the kernels, the tables, the quadrature, nor the
+finalisation.  The only module both sides use is the seeded input generator
+``paper_2005_01739_gb300.catalogs`` (random numbers only, none of the method's
+arithmetic), and this package does not import even that.
+
+What is computed, and where each piece comes from:
+
+* ``hip_oracle.c`` -- brute-force ordered pair sums in double precision:
+  the window W (Eq. window_defn), the bin-averaged Bessel function jbar (Eq.
+  jla-def with D_l from App. C), the power-spectrum pair sum (Sec. 3) and the
+  per-primary A_lm / C_l accumulators contracted into the bispectrum sum (Eq.
+  AC-def, binned form of Sec. 4.4).
+* this module -- the analytic random-pair terms and the final estimators:
+  the binned window transform W~^a (Eq. wka-def) by composite Gauss-Legendre
+  quadrature, P^a_l (binned estimator of Sec. 3) and B^ab_l (summary, Sec. 4.5).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hip_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libhip_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc + OpenMP (portable flags only)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            d, i, i64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
+            P = ctypes.c_void_p
+            L.orc_window.restype = d
+            L.orc_window.argtypes = [d]
+            L.orc_si.restype = d
+            L.orc_si.argtypes = [d]
+            L.orc_sph_jn.restype = d
+            L.orc_sph_jn.argtypes = [i, d]
+            L.orc_dhat.restype = d
+            L.orc_dhat.argtypes = [i, d]
+            L.orc_jbar.restype = d
+            L.orc_jbar.argtypes = [i, d, d, d]
+            L.orc_legendre.restype = d
+            L.orc_legendre.argtypes = [i, d]
+            L.orc_ylm_export.restype = None
+            L.orc_ylm_export.argtypes = [d, d, d, P, P]
+            L.orc_num_threads.restype = i
+            L.orc_set_threads.argtypes = [i]
+            L.orc_power_pairs.restype = i
+            L.orc_power_pairs.argtypes = [P, P, i64, d, d, P, i, i, i, P, i64, P, P]
+            L.orc_bispec_primaries.restype = i
+            L.orc_bispec_primaries.argtypes = [P, P, P, i64, P, P, i64, d, d, P, i, i, P, P]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+# ----------------------------------------------------------- scalar pieces ---
+def window(x: float) -> float:
+    """W(x) of Eq. window_defn, x = r / R0."""
+    return lib().orc_window(float(x))
+
+
+def sine_integral(u: float) -> float:
+    return lib().orc_si(float(u))
+
+
+def sph_jn(n: int, x: float) -> float:
+    return lib().orc_sph_jn(int(n), float(x))
+
+
+def dhat(l: int, u: float) -> float:
+    """D_l(u) = int_0^u t^2 j_l(t) dt (App. C, definite from 0)."""
+    return lib().orc_dhat(int(l), float(u))
+
+
+def jbar(l: int, r: float, klo: float, khi: float) -> float:
+    """Bin-averaged spherical Bessel function, Eq. jla-def."""
+    return lib().orc_jbar(int(l), float(r), float(klo), float(khi))
+
+
+def legendre(l: int, mu: float) -> float:
+    return lib().orc_legendre(int(l), float(mu))
+
+
+def ylm(u) -> np.ndarray:
+    """Complex Y_lm(u) for l <= 4, index l*l + l + m (Condon-Shortley phase)."""
+    re = np.zeros(25)
+    im = np.zeros(25)
+    lib().orc_ylm_export(float(u[0]), float(u[1]), float(u[2]), _ptr(re), _ptr(im))
+    return re + 1j * im
+
+
+# --------------------------------------------------------- window transform ---
+def _gl_panels(a: float, b: float, hmax: float, order: int = 16):
+    n = max(1, int(np.ceil((b - a) / hmax)))
+    x, wq = np.polynomial.legendre.leggauss(order)
+    edges = np.linspace(a, b, n + 1)
+    lo, hi = edges[:-1, None], edges[1:, None]
+    pts = 0.5 * (hi - lo) * x[None, :] + 0.5 * (hi + lo)
+    wts = 0.5 * (hi - lo) * wq[None, :]
+    return pts.ravel(), wts.ravel()
+
+
+def window_transform_binned(edges, R0: float) -> np.ndarray:
+    """W~^a(R0) = 4 pi int_0^R0 r^2 jbar^a_0(r) W(r/R0) dr (Eq. wka-def).
+
+    Composite Gauss-Legendre on the three polynomial pieces of W, [0, R0/2],
+    [R0/2, 3R0/4], [3R0/4, R0], each cut into panels no wider than pi/(4 k_hi).
+    jbar^a_0 = 3 [D_0(r k_hi) - D_0(r k_lo)] / (r^3 (k_hi^3 - k_lo^3)).
+    """
+    edges = np.asarray(edges, dtype=np.float64)
+    out = np.zeros(len(edges) - 1)
+    for a in range(len(edges) - 1):
+        klo, khi = edges[a], edges[a + 1]
+        hmax = np.pi / (4.0 * khi)
+        tot = 0.0
+        for lo, hi in ((0.0, 0.5 * R0), (0.5 * R0, 0.75 * R0), (0.75 * R0, R0)):
+            pts, wts = _gl_panels(lo, hi, hmax)
+            for r, wq in zip(pts, wts):
+                tot += wq * r * r * jbar(0, r, klo, khi) * window(r / R0)
+        out[a] = 4.0 * np.pi * tot
+    return out
+
+
+# ------------------------------------------------------------ pair sums ------
+def power_pair_sum(pos, w, L, R0, edges, ell_max=4, los=2, primaries=None):
+    """Ordered-pair sum DD[l/2][a] = sum_{i in S} sum_{j != i} w_i w_j W jbar^a_l L_l(mu).
+
+    Returns (DD [n_ell, nk], number of ordered pairs counted)."""
+    pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+    N = pos.shape[0]
+    wv = None if w is None else np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    edges = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+    nk = len(edges) - 1
+    n_ell = ell_max // 2 + 1
+    prim = np.arange(N, dtype=np.int64) if primaries is None else np.ascontiguousarray(
+        np.asarray(primaries, dtype=np.int64))
+    DD = np.zeros((n_ell, nk))
+    npairs = ctypes.c_int64(0)
+    rc = lib().orc_power_pairs(_ptr(pos), _ptr(wv), N, float(L), float(R0), _ptr(edges), nk, n_ell,
+                               int(los), _ptr(prim), len(prim), _ptr(DD), ctypes.byref(npairs))
+    if rc != 0:
+        raise ValueError(f"orc_power_pairs failed ({rc})")
+    return DD, int(npairs.value)
+
+
+def bispectrum_primary_sum(prim_pos, prim_w, prim_self, data_pos, data_w, L, R0, edges, lmax=4):
+    """T[l][a][b] = sum_p prim_w[p] [4pi/(2l+1) Re sum_m A^a_lm A^b*_lm - C^ab_l](p)."""
+    pp = np.ascontiguousarray(np.asarray(prim_pos, dtype=np.float64).reshape(-1, 3))
+    pw = np.ascontiguousarray(np.asarray(prim_w, dtype=np.float64))
+    ps = None if prim_self is None else np.ascontiguousarray(np.asarray(prim_self, dtype=np.int64))
+    dp = np.ascontiguousarray(np.asarray(data_pos, dtype=np.float64).reshape(-1, 3))
+    dw = None if data_w is None else np.ascontiguousarray(np.asarray(data_w, dtype=np.float64))
+    edges = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+    nk = len(edges) - 1
+    T = np.zeros((lmax + 1, nk, nk))
+    npairs = ctypes.c_int64(0)
+    rc = lib().orc_bispec_primaries(_ptr(pp), _ptr(pw), _ptr(ps), pp.shape[0], _ptr(dp), _ptr(dw),
+                                    dp.shape[0], float(L), float(R0), _ptr(edges), nk, int(lmax),
+                                    _ptr(T), ctypes.byref(npairs))
+    if rc != 0:
+        raise ValueError(f"orc_bispec_primaries failed ({rc})")
+    return T, int(npairs.value)
+
+
+# ------------------------------------------------------------- estimators ----
+def power_from_pairs(DD, S1, L, Wt):
+    """P^a_l = (-1)^(l/2) (2l+1) DD^a_l / (n_w^2 V) - delta_l0 W~^a (Sec. 3).
+
+    (-i)^l = (-1)^(l/2) for even l.  n_w = S1 / V with S1 = sum of weights
+    (= N for unit weights, the paper's n)."""
+    V = float(L) ** 3
+    n_w = float(S1) / V
+    P = np.zeros_like(DD)
+    for il in range(DD.shape[0]):
+        l = 2 * il
+        P[il] = ((-1.0) ** (l // 2)) * (2 * l + 1) * DD[il] / (n_w * n_w * V)
+    P[0] -= Wt
+    return P
+
+
+def power_spectrum(pos, w, L, R0, edges, ell_max=4, los=2):
+    """Full brute-force P^a_l for ell = 0, 2, ..., ell_max (binned estimator, Sec. 3)."""
+    DD, npairs = power_pair_sum(pos, w, L, R0, edges, ell_max, los)
+    N = np.asarray(pos).reshape(-1, 3).shape[0]
+    S1 = float(N) if w is None else float(np.sum(np.asarray(w, dtype=np.float64)))
+    Wt = window_transform_binned(edges, R0)
+    return power_from_pairs(DD, S1, L, Wt), DD, npairs
+
+
+def bispectrum_from_sums(Tdata, Trand, S, S1, N_r, L, Wt):
+    """B^ab_l from the summary of Sec. 4.5.
+
+    B = (-1)^l (2l+1) [Tdata - (S1/N_r) Trand] / (V n_w^3)
+        - delta_l0 (W~^a S^b + W~^b S^a) / (V n_w^2) + 2 delta_l0 W~^a W~^b,
+    S^a = sum_{i != j} w_i w_j jbar^a_0 W (the ordered DD_0 pair sum), and each
+    random primary carries weight S1/N_r (= 1/f_rand for unit weights)."""
+    V = float(L) ** 3
+    n_w = float(S1) / V
+    nl = Tdata.shape[0]
+    B = np.zeros_like(Tdata)
+    for l in range(nl):
+        B[l] = ((-1.0) ** l) * (2 * l + 1) * (Tdata[l] - (float(S1) / float(N_r)) * Trand[l]) / (V * n_w ** 3)
+    B[0] -= (np.outer(Wt, S) + np.outer(S, Wt)) / (V * n_w * n_w)
+    B[0] += 2.0 * np.outer(Wt, Wt)
+    return B
+
+
+def bispectrum(pos, w, rand_pos, L, R0, edges, lmax=4, data_primaries=None, rand_primaries=None):
+    """Brute-force B^ab_l.  Optional primary subsets restrict the A/C sums (used for
+    sampled parity at large N); S^a is always the full pair sum when no subset is
+    given, else the same subset's ordered sum (callers compare like with like)."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    rp = np.asarray(rand_pos, dtype=np.float64).reshape(-1, 3)
+    N = pos.shape[0]
+    wv = np.ones(N) if w is None else np.asarray(w, dtype=np.float64)
+    dsel = np.arange(N) if data_primaries is None else np.asarray(data_primaries, dtype=np.int64)
+    rsel = np.arange(rp.shape[0]) if rand_primaries is None else np.asarray(rand_primaries, dtype=np.int64)
+    Td, npd = bispectrum_primary_sum(pos[dsel], wv[dsel], dsel, pos, w, L, R0, edges, lmax)
+    Tr, npr = bispectrum_primary_sum(rp[rsel], np.ones(len(rsel)), None, pos, w, L, R0, edges, lmax)
+    DD, _ = power_pair_sum(pos, w, L, R0, edges, 0, 2, primaries=dsel)
+    Wt = window_transform_binned(edges, R0)
+    S1 = float(np.sum(wv))
+    B = bispectrum_from_sums(Td, Tr, DD[0], S1, rp.shape[0], L, Wt)
+    return B, dict(Tdata=Td, Trand=Tr, S=DD[0], Wt=Wt, npairs_data=npd, npairs_rand=npr)

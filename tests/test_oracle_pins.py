@@ -1,0 +1,390 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks one piece of ``oracle/`` against something other than itself:
+exact values of the window, library special functions and quadrature, the
+plane-wave definitions the estimators are derived from (Eq. discrete-xy for P,
+Eq. general-XYZ-counts for B), brute-force triple sums (the DDD reformulation of
+Sec. 4.2), Monte Carlo nulls and symmetries.  A plausible slip anywhere in the
+oracle -- a dropped term, a wrong sign or index, a transposed operand -- fails
+at least one of these.
+"""
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.special import sici, spherical_jn, eval_legendre
+
+import oracle
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+
+
+def _minimage(d, L):
+    return d - L * np.round(d / L)
+
+
+# ------------------------------------------------------------------ window ---
+def test_window_values_and_smoothness():
+    # Eq. window_defn: W = 1 on [0,1/2), 1/2 at x = 3/4, 0 from x = 1.
+    assert oracle.window(0.0) == 1.0
+    assert oracle.window(0.49) == 1.0
+    assert oracle.window(0.5) == pytest.approx(1.0, abs=1e-15)
+    assert oracle.window(0.75) == pytest.approx(0.5, abs=1e-15)
+    assert oracle.window(1.0) == 0.0
+    assert oracle.window(1.2) == 0.0
+    # continuity and C^1 at the joins (slopes 0, -4, 0)
+    h = 1e-7
+    for x0, slope in ((0.5, 0.0), (0.75, -4.0), (1.0, 0.0)):
+        left = (oracle.window(x0 - h) - oracle.window(x0 - 2 * h)) / h
+        right = (oracle.window(x0 + 2 * h) - oracle.window(x0 + h)) / h
+        assert left == pytest.approx(slope, abs=1e-5)
+        assert right == pytest.approx(slope, abs=1e-5)
+        assert abs(oracle.window(x0 - 1e-12) - oracle.window(x0 + 1e-12)) < 1e-9
+
+
+def test_window_moments_exact_rationals():
+    # int_0^1 x^2 W dx = 47/320 and int_0^1 x^2 W^2 dx = 3713/31680, exact
+    # rationals from integrating the piecewise polynomial of Eq. window_defn.
+    m1 = integrate.quad(lambda x: x * x * oracle.window(x), 0, 1, points=[0.5, 0.75], epsabs=1e-15)[0]
+    m2 = integrate.quad(lambda x: x * x * oracle.window(x) ** 2, 0, 1, points=[0.5, 0.75], epsabs=1e-15)[0]
+    assert m1 == pytest.approx(47 / 320, rel=1e-13)
+    assert m2 == pytest.approx(3713 / 31680, rel=1e-13)
+
+
+# ------------------------------------------------------- special functions ---
+def test_sine_integral_matches_library():
+    u = np.concatenate([np.linspace(0, 10, 2001), np.linspace(10, 1500, 3001)])
+    ours = np.array([oracle.sine_integral(x) for x in u])
+    assert np.max(np.abs(ours - sici(u)[0])) < 5e-15
+    assert oracle.sine_integral(-3.0) == pytest.approx(-sici(3.0)[0], abs=1e-15)
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 3, 4])
+def test_dhat_matches_quadrature(l):
+    # D_l(u) = int_0^u t^2 j_l(t) dt (App. C, definite from 0), across the
+    # series / recursion switch at u = 4 and up to u = 400.
+    for u in [1e-3, 0.05, 0.3, 1.5, 3.9, 3.999, 4.0, 4.1, 6.0, 11.0, 25.0, 137.0, 400.0]:
+        ref = integrate.quad(lambda t: t * t * spherical_jn(l, t), 0, u, limit=5000,
+                             epsabs=1e-16, epsrel=1e-14)[0]
+        got = oracle.dhat(l, u)
+        scale = max(abs(ref), u ** (l + 3) / 1e6 if u < 1 else 1e-300)
+        assert abs(got - ref) <= 5e-12 * max(abs(ref), 1e-300) + 1e-14 * scale, (l, u, got, ref)
+
+
+def test_dhat_closed_forms_and_constants():
+    # D_0 = sin u - u cos u exactly; odd-l constants of integration: the App. C
+    # closed form is -2 (l=1) and -8 (l=3) at u = 0, so the definite integral
+    # adds them back.
+    for u in [4.5, 9.0, 33.0]:
+        assert oracle.dhat(0, u) == pytest.approx(np.sin(u) - u * np.cos(u), rel=1e-13, abs=1e-13)
+        j = [spherical_jn(n, u) for n in range(6)]
+        I1 = -j[0]
+        I3 = (2 * I1 - 5 * j[2]) / 3
+        assert oracle.dhat(1, u) == pytest.approx(u * u * j[2] - u * j[1] + 2 * I1 + 2.0, rel=1e-12)
+        assert oracle.dhat(3, u) == pytest.approx(u * u * j[4] - 3 * u * j[3] + 12 * I3 + 8.0, rel=1e-12)
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 3, 4])
+def test_jbar_is_shell_average(l):
+    # Eq. jla-def: jbar^a_l(r) = (4 pi / v_a) int k^2 j_l(k r) dk over the bin.
+    for klo, khi in [(0.0, 0.05), (0.2, 0.26), (1.9, 2.0), (4.95, 5.0)]:
+        norm = 3.0 / (khi ** 3 - klo ** 3)
+        for r in [1e-3, 0.7, 3.3, 19.9, 49.0]:
+            ref = norm * integrate.quad(lambda k: k * k * spherical_jn(l, k * r), klo, khi,
+                                        epsabs=1e-16, epsrel=1e-13, limit=200)[0]
+            got = oracle.jbar(l, r, klo, khi)
+            assert abs(got - ref) < 1e-10 * max(1.0, abs(ref)) + 1e-12, (l, klo, khi, r, got, ref)
+
+
+def test_jbar_limits():
+    assert oracle.jbar(0, 0.0, 0.1, 0.2) == 1.0
+    for l in range(1, 5):
+        assert oracle.jbar(l, 0.0, 0.1, 0.2) == 0.0
+    assert oracle.jbar(0, 1e-6, 0.1, 0.2) == pytest.approx(1.0, abs=1e-11)
+    # narrow bin -> j_l(k_c r)
+    for l in range(5):
+        kc, r = 1.3, 7.7
+        assert oracle.jbar(l, r, kc - 1e-6, kc + 1e-6) == pytest.approx(spherical_jn(l, kc * r), abs=1e-9)
+
+
+def test_ylm_addition_theorem_and_norm():
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        a = rng.normal(size=3)
+        a /= np.linalg.norm(a)
+        b = rng.normal(size=3)
+        b /= np.linalg.norm(b)
+        Ya, Yb = oracle.ylm(a), oracle.ylm(b)
+        for l in range(5):
+            sl = slice(l * l, l * l + 2 * l + 1)
+            lhs = np.sum(Ya[sl] * np.conj(Yb[sl]))
+            assert lhs.real == pytest.approx((2 * l + 1) / (4 * np.pi) * eval_legendre(l, a @ b), abs=1e-13)
+            assert abs(lhs.imag) < 1e-13
+    # orthonormality on the sphere (Gauss-Legendre x trapezoid)
+    ct, wt = np.polynomial.legendre.leggauss(16)
+    phis = np.arange(32) * 2 * np.pi / 32
+    G = np.zeros((25, 25), dtype=complex)
+    for c, wc in zip(ct, wt):
+        s = np.sqrt(1 - c * c)
+        for p in phis:
+            Y = oracle.ylm((s * np.cos(p), s * np.sin(p), c))
+            G += wc * (2 * np.pi / 32) * np.outer(Y, np.conj(Y))
+    assert np.max(np.abs(G - np.eye(25))) < 1e-12
+
+
+# ------------------------------------------------------- window transform ---
+def test_window_transform_low_k_limit():
+    # W~^a -> 4 pi R0^3 int x^2 W dx = 4 pi R0^3 47/320 as the bin shrinks to k = 0.
+    R0 = 37.0
+    Wt = oracle.window_transform_binned([0.0, 1e-5], R0)
+    assert Wt[0] == pytest.approx(4 * np.pi * R0 ** 3 * 47 / 320, rel=1e-8)
+
+
+def test_window_transform_matches_double_integral():
+    # Eq. wka-def: W~^a = (4 pi / v_a) int k^2 W~(k R0) dk with
+    # W~(k R0) = 4 pi int r^2 j_0(k r) W dr (RR term of Sec. 3), done here in the
+    # opposite order with library quadrature.
+    R0 = 20.0
+    edges = [0.05, 0.25, 0.9, 1.0]
+
+    def Wk(k):
+        return 4 * np.pi * integrate.quad(lambda r: r * r * spherical_jn(0, k * r) * oracle.window(r / R0),
+                                          0, R0, points=[R0 / 2, 0.75 * R0], limit=400,
+                                          epsabs=1e-13, epsrel=1e-13)[0]
+
+    got = oracle.window_transform_binned(edges, R0)
+    for a in range(3):
+        klo, khi = edges[a], edges[a + 1]
+        ref = 3 / (khi ** 3 - klo ** 3) * integrate.quad(lambda k: k * k * Wk(k), klo, khi,
+                                                       epsabs=1e-13, epsrel=1e-12, limit=200)[0]
+        assert got[a] == pytest.approx(ref, rel=1e-9, abs=1e-9 * abs(got[0]))
+
+
+# ------------------------------------------------------- power spectrum -----
+def _tiny_catalog(N, L, seed, spread):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0, L, size=3)
+    return np.mod(c + rng.normal(0, spread, size=(N, 3)), L)
+
+
+def test_power_pair_sum_equals_plane_wave_definition():
+    # Eq. discrete-xy with the window, projected on L_l(khat.z) and averaged
+    # over the k shell (Eq. pk-binned), equals (-i)^l (2l+1) DD^a_l: this pins the
+    # Bessel/Legendre expansion of Eq. general-XY-counts, its sign and the binning.
+    L, R0 = 60.0, 20.0
+    pos = _tiny_catalog(8, L, 11, 6.0)
+    edges = np.array([0.05, 0.2, 0.35])
+    DD, npairs = oracle.power_pair_sum(pos, None, L, R0, edges, ell_max=4)
+    assert npairs > 20
+    d = _minimage(pos[:, None, :] - pos[None, :, :], L)
+    r = np.linalg.norm(d, axis=-1)
+    mask = (r > 0) & (r < R0)
+    dv = d[mask]
+    Wv = np.array([oracle.window(x / R0) for x in r[mask]])
+    ct, wct = np.polynomial.legendre.leggauss(40)
+    nphi = 80
+    phi = np.arange(nphi) * 2 * np.pi / nphi
+    C, PH = np.meshgrid(ct, phi, indexing="ij")
+    S = np.sqrt(1 - C * C)
+    khat = np.stack([S * np.cos(PH), S * np.sin(PH), C], axis=-1).reshape(-1, 3)
+    wang = (np.outer(wct, np.full(nphi, 2 * np.pi / nphi)) / (4 * np.pi)).ravel()
+    xk, wk = np.polynomial.legendre.leggauss(24)
+    for a in range(2):
+        klo, khi = edges[a], edges[a + 1]
+        ks = 0.5 * (khi - klo) * xk + 0.5 * (khi + klo)
+        wks = 0.5 * (khi - klo) * wk * 3 * ks * ks / (khi ** 3 - klo ** 3)
+        for l in (0, 2, 4):
+            Ll = eval_legendre(l, khat[:, 2])
+            tot = 0.0 + 0.0j
+            for k, wkk in zip(ks, wks):
+                phase = np.exp(-1j * k * (khat @ dv.T))  # [ndir, npairs]
+                tot += wkk * (2 * l + 1) * np.sum(wang * Ll * (phase @ Wv))
+            expect = ((-1) ** (l // 2)) * (2 * l + 1) * DD[l // 2, a]
+            assert abs(tot.imag) < 1e-10 * max(1.0, abs(expect))
+            assert tot.real == pytest.approx(expect, rel=1e-9, abs=1e-9 * np.max(np.abs(DD)))
+
+
+def test_power_two_particle_ordered_pair():
+    # two particles across the periodic boundary: one pair in each order, the
+    # minimum-image separation 3 along x (mu = 0) and weights w_i w_j.
+    L, R0 = 50.0, 10.0
+    pos = np.array([[0.5, 10.0, 10.0], [47.5, 10.0, 10.0]])
+    w = np.array([2.0, 0.5])
+    edges = np.array([0.1, 0.4, 1.2])
+    DD, npairs = oracle.power_pair_sum(pos, w, L, R0, edges, ell_max=4)
+    assert npairs == 2
+    for a in range(2):
+        for l in (0, 2, 4):
+            jb = oracle.jbar(l, 3.0, edges[a], edges[a + 1])
+            assert DD[l // 2, a] == pytest.approx(2 * 1.0 * oracle.window(0.3) * jb * eval_legendre(l, 0.0),
+                                                  rel=1e-14, abs=1e-16)
+
+
+def test_power_poisson_null_and_rr_term():
+    # Fixed-N uniform catalogs: E[DD_0^a] / (n^2 V) = W~^a (N-1)/N, so
+    # E[P_0^a] = -W~^a / N and E[P_2], E[P_4] = 0 (RR term of Sec. 3 and the
+    # translation-invariance argument DR = RR).
+    N, L, R0 = 300, 100.0, 20.0
+    edges = np.linspace(0.1, 0.5, 5)
+    Wt = oracle.window_transform_binned(edges, R0)
+    Ps = []
+    rng = np.random.default_rng(123)
+    for s in range(60):
+        pos = rng.uniform(0, L, size=(N, 3))
+        DD, _ = oracle.power_pair_sum(pos, None, L, R0, edges, ell_max=4)
+        Ps.append(oracle.power_from_pairs(DD, N, L, Wt))
+    Ps = np.array(Ps)
+    mean = Ps.mean(axis=0)
+    se = Ps.std(axis=0, ddof=1) / np.sqrt(len(Ps))
+    assert np.all(np.abs(mean[0] + Wt / N) < 4 * se[0] + 1e-12)
+    assert np.all(np.abs(mean[1:]) < 4 * se[1:] + 1e-12)
+    # and the signal is not trivially zero: the spread is resolved
+    assert np.all(se[0] > 0)
+
+
+def test_power_invariances():
+    L, R0 = 200.0, 20.0
+    rng = np.random.default_rng(7)
+    parents = rng.uniform(0, L, size=(60, 3))
+    pos = np.mod(parents[rng.integers(0, 60, 1500)] + rng.normal(0, 3.0, size=(1500, 3)), L)
+    w = rng.uniform(0.5, 1.5, 1500)
+    edges = np.linspace(0.2, 1.2, 6)
+    base, _ = oracle.power_pair_sum(pos, w, L, R0, edges, ell_max=4)
+    scale = np.max(np.abs(base))
+    shift = np.mod(pos + rng.uniform(0, L, 3), L)
+    perm = rng.permutation(len(pos))
+    swap = pos[:, [1, 0, 2]]
+    flip = np.mod(-pos * np.array([1, 1, -1]) + np.array([0, 0, L]), L)
+    for p2, w2 in ((shift, w), (pos[perm], w[perm]), (swap, w), (flip, w)):
+        got, _ = oracle.power_pair_sum(p2, w2, L, R0, edges, ell_max=4)
+        assert np.max(np.abs(got - base)) < 1e-10 * scale
+
+
+# ------------------------------------------------------------- bispectrum ---
+def test_bispectrum_primary_sum_equals_triple_sum():
+    # Sec. 4.2: sum_i w_i [4pi/(2l+1) sum_m A^a_lm A^b*_lm - C^ab_l](x_i) equals the
+    # triple sum over i, j != i, k != i, k != j of
+    # w_i w_j w_k jbar^a_l(r_ij) jbar^b_l(r_ik) W W L_l(rhat_ij . rhat_ik).
+    L, R0 = 40.0, 15.0
+    rng = np.random.default_rng(3)
+    pos = _tiny_catalog(25, L, 5, 5.0)
+    w = rng.uniform(0.5, 1.5, 25)
+    edges = np.array([0.1, 0.3, 0.5, 0.7])
+    T, _ = oracle.bispectrum_primary_sum(pos, w, np.arange(25), pos, w, L, R0, edges, lmax=4)
+    nk = 3
+    ref = np.zeros((5, nk, nk))
+    for i in range(25):
+        d = _minimage(pos[i] - pos, L)
+        r = np.linalg.norm(d, axis=1)
+        sel = np.where((r > 0) & (r < R0))[0]
+        if len(sel) < 2:
+            continue
+        rh = d[sel] / r[sel, None]
+        Wv = np.array([oracle.window(x / R0) for x in r[sel]])
+        cosm = rh @ rh.T
+        for l in range(5):
+            jb = np.array([[oracle.jbar(l, x, edges[a], edges[a + 1]) for x in r[sel]] for a in range(nk)])
+            Lm = eval_legendre(l, np.clip(cosm, -1, 1))
+            np.fill_diagonal(Lm, 0.0)  # k != j
+            y = jb * (w[sel] * Wv)[None, :]
+            ref[l] += w[i] * (y @ Lm @ y.T)
+    assert np.max(np.abs(T - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+def test_bispectrum_plane_wave_definition():
+    # Eq. general-XYZ-counts / general-Bkl-exp: averaging
+    # e^{-i k1.x_ij} e^{-i k2.x_ik} against (2l+1) L_l(k1hat.k2hat) over both k
+    # directions and both k shells gives (-1)^l (2l+1) times the triple sum,
+    # i.e. the oracle's primary sum T.  This pins the (-1)^l (2l+1) convention.
+    L, R0 = 60.0, 20.0
+    pos = _tiny_catalog(6, L, 17, 5.0)
+    edges = np.array([0.05, 0.2, 0.35])
+    T, _ = oracle.bispectrum_primary_sum(pos, np.ones(6), np.arange(6), pos, None, L, R0, edges, lmax=4)
+    ct, wct = np.polynomial.legendre.leggauss(20)
+    nphi = 40
+    phi = np.arange(nphi) * 2 * np.pi / nphi
+    C, PH = np.meshgrid(ct, phi, indexing="ij")
+    S = np.sqrt(1 - C * C)
+    khat = np.stack([S * np.cos(PH), S * np.sin(PH), C], axis=-1).reshape(-1, 3)
+    wang = (np.outer(wct, np.full(nphi, 2 * np.pi / nphi)) / (4 * np.pi)).ravel()
+    cosk = np.clip(khat @ khat.T, -1, 1)
+    xk, wk = np.polynomial.legendre.leggauss(8)
+    N = 6
+    dvec, Wm = {}, {}
+    for i in range(N):
+        d = _minimage(pos[i] - pos, L)
+        r = np.linalg.norm(d, axis=1)
+        sel = np.where((r > 0) & (r < R0))[0]
+        dvec[i] = d[sel]
+        Wm[i] = np.array([oracle.window(x / R0) for x in r[sel]])
+    for l in range(5):
+        Lmat = eval_legendre(l, cosk) * wang[:, None] * wang[None, :]
+        for a in range(2):
+            for b in range(2):
+                ka = 0.5 * (edges[a + 1] - edges[a]) * xk + 0.5 * (edges[a + 1] + edges[a])
+                wa = 0.5 * (edges[a + 1] - edges[a]) * wk * 3 * ka ** 2 / (edges[a + 1] ** 3 - edges[a] ** 3)
+                kb = 0.5 * (edges[b + 1] - edges[b]) * xk + 0.5 * (edges[b + 1] + edges[b])
+                wb = 0.5 * (edges[b + 1] - edges[b]) * wk * 3 * kb ** 2 / (edges[b + 1] ** 3 - edges[b] ** 3)
+                tot = 0.0 + 0.0j
+                for i in range(N):
+                    dv, Wv = dvec[i], Wm[i]
+                    if len(Wv) == 0:
+                        continue
+                    proj = khat @ dv.T  # [ndir, nnb]
+                    E1 = np.einsum("q,qdn->dn", wa, np.exp(-1j * ka[:, None, None] * proj[None]) * Wv)
+                    E2 = np.einsum("q,qdn->dn", wb, np.exp(-1j * kb[:, None, None] * proj[None]) * Wv)
+                    full = np.sum(E1.sum(1) * (Lmat @ E2.sum(1)))
+                    diag = np.sum(E1 * (Lmat @ E2))  # j == k terms
+                    tot += (2 * l + 1) * (full - diag)
+                expect = ((-1) ** l) * (2 * l + 1) * T[l, a, b]
+                assert abs(tot.imag) < 1e-8 * max(1.0, np.max(np.abs(T)))
+                assert tot.real == pytest.approx(expect, rel=1e-8, abs=1e-8 * np.max(np.abs(T)))
+
+
+def _cluster(N, L, seed):
+    rng = np.random.default_rng(seed)
+    parents = rng.uniform(0, L, size=(N // 10, 3))
+    return np.mod(parents[rng.integers(0, len(parents), N)] + rng.normal(0, 2.0, size=(N, 3)), L)
+
+
+def test_bispectrum_symmetries():
+    # B^ab_l = B^ba_l; invariance under translations, relabelling and the
+    # rotations/reflections of the cube (the isotropic bispectrum, Sec. 2).
+    L, R0 = 100.0, 20.0
+    pos = _cluster(200, L, 9)
+    rnd = np.random.default_rng(10).uniform(0, L, size=(600, 3))
+    edges = np.linspace(0.2, 0.8, 4)
+    B, _ = oracle.bispectrum(pos, None, rnd, L, R0, edges, lmax=4)
+    scale = np.max(np.abs(B))
+    assert np.max(np.abs(B - np.transpose(B, (0, 2, 1)))) < 1e-12 * scale
+    rng = np.random.default_rng(1)
+    sh = rng.uniform(0, L, 3)
+    perm = rng.permutation(200)
+    rot = lambda p: np.mod(np.stack([p[:, 1], -p[:, 0], p[:, 2]], 1) + np.array([0, L, 0]), L)
+    refl = lambda p: np.mod(np.stack([p[:, 2], p[:, 1], -p[:, 0]], 1) + np.array([0, 0, L]), L)
+    for p2, r2 in ((np.mod(pos + sh, L), np.mod(rnd + sh, L)), (pos[perm], rnd),
+                   (rot(pos), rot(rnd)), (refl(pos), refl(rnd))):
+        B2, _ = oracle.bispectrum(p2, None, r2, L, R0, edges, lmax=4)
+        assert np.max(np.abs(B2 - B)) < 1e-10 * scale
+
+
+def test_bispectrum_null_mean():
+    # Unclustered data: the four l = 0 terms of the summary (Sec. 4.5) cancel in
+    # expectation, so the seed-mean of B_0 (and of the l > 0 multipoles) is zero
+    # up to O(1/N) and the Monte Carlo noise of the random catalog.
+    N, L, R0 = 250, 80.0, 20.0
+    edges = np.linspace(0.15, 0.45, 3)
+    rng = np.random.default_rng(77)
+    Bs = []
+    for s in range(16):
+        pos = rng.uniform(0, L, size=(N, 3))
+        rnd = rng.uniform(0, L, size=(3 * N, 3))
+        B, info = oracle.bispectrum(pos, None, rnd, L, R0, edges, lmax=2)
+        Bs.append(B)
+    Bs = np.array(Bs)
+    mean = Bs.mean(0)
+    se = Bs.std(0, ddof=1) / np.sqrt(len(Bs))
+    Wt = info["Wt"]
+    # O(1/N) bias bound: a few W~^a W~^b / N
+    bias = 5.0 * np.abs(np.outer(Wt, Wt)) / N
+    assert np.all(np.abs(mean[0]) < 4 * se[0] + bias)
+    assert np.all(np.abs(mean[1:]) < 4 * se[1:] + 1e-12 * np.max(np.abs(Bs)))
