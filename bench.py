@@ -1,0 +1,311 @@
+"""Benchmark of the GB300 small-scale power-spectrum path (arXiv:2005.01739, Sec. 3).
+
+One step = one complete hip_power call on a device-resident catalog: cell-list
+build, FP32 pair kernel, FP64 finalize (W~^a, reduction, normalisation) and the
+download of P and DD.  Metric: unordered pairs with 0 < r < R0, times the number
+of k bins, per second (pairs x k-bins / s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank measures its own catalog of
+the same size (different seed): weak scaling, no data-path collective; only the
+step times are max-reduced.  ``--impl reference`` times the FP64 CPU oracle on
+the host cores over a bounded primary sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairs×k-bins/s for P_ℓ(k), B_ℓ; mixed-prec batched vs FP64 GPU at stated err"
+UNIT = "pairs*kbins/s"
+WORKLOAD = "pk_mixed_n2e6"
+FLOPS_PER_PAIR_BIN = 12.0  # nominal algorithmic FP32 flops per (unordered pair, k bin)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_peak_tflops(pk) -> float:
+    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(rank: int):
+    from paper_2005_01739_gb300 import catalogs
+    wl = catalogs.workload(WORKLOAD)
+    if rank > 0:  # weak scaling: same size and settings, another seed
+        pos, w = catalogs.thomas(2_000_000, 1000.0, 50_000, 1.5, 1001 + 97 * rank, weights="u05_15")
+        wl = dict(wl, pos=pos, w=w)
+    return wl
+
+
+def _config(wl, nranks):
+    return {"workload": WORKLOAD, "N": int(len(wl["pos"])), "L": wl["L"], "R0": wl["R0"],
+            "n_k": int(len(wl["edges"]) - 1), "k_range": [float(wl["edges"][0]), float(wl["edges"][-1])],
+            "ell": [0, 2, 4], "weights": "U(0.5,1.5)", "catalog": "Thomas process, 5e4 parents, sigma 1.5",
+            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas{nranks}"}
+
+
+def oracle_sample(wl, seconds: float):
+    """Time the FP64 oracle on a primary subset sized for ~`seconds` of work."""
+    import oracle
+    pos = wl["pos"].astype(np.float64)
+    w = wl["w"].astype(np.float64)
+    m = 64
+    while True:
+        t0 = time.perf_counter()
+        _, npairs = oracle.power_pair_sum(pos, w, wl["L"], wl["R0"], wl["edges"], 4, 2, primaries=np.arange(m))
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * seconds or m >= len(pos):
+            break
+        m = min(len(pos), int(m * max(2.0, 0.5 * seconds / max(dt, 1e-3))))
+    nk = len(wl["edges"]) - 1
+    return {"value": npairs * nk / dt, "seconds": dt, "primaries": m, "ordered_pairs": npairs,
+            "cores": oracle.num_threads()}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    wl = _workload(0)
+    for _ in range(args.warmup):
+        oracle_sample(wl, 2.0)
+    times, rates, last = [], [], None
+    for _ in range(args.steps):
+        last = oracle_sample(wl, args.ref_seconds)
+        rates.append(last["value"])
+        times.append(last["seconds"])
+    v = float(np.mean(rates))
+    sample = (f"ordered pair sums of the first {last['primaries']} primaries against all "
+              f"{len(wl['pos'])} particles, all {len(wl['edges']) - 1} bins, l=0,2,4 (FP64 brute force)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(wl, 1),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2005_01739_gb300 import binding, build
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    binding.load()
+    wl = _workload(rank)
+    L, R0, edges = wl["L"], wl["R0"], wl["edges"]
+    nk = len(edges) - 1
+    stream = torch.cuda.Stream()
+    dpos = torch.from_numpy(wl["pos"]).cuda()
+    dw = torch.from_numpy(wl["w"]).cuda()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    binding.set_profiling(True)
+
+    def step():
+        with torch.cuda.stream(stream):
+            return binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed", stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    step_ms, pair_ms = [], []
+    npairs = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[i][0].record(stream)
+            _, _, npairs = step()
+            ev[i][1].record(stream)
+            pair_ms.append(float(binding.stage_times()[2]))
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(step_ms))
+    pairs = npairs // 2  # unordered pairs with 0 < r < R0
+    work = float(pairs) * nk
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    wsum = torch.tensor([work], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(wsum, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    value = float(wsum.item()) / (ms_max / 1e3)
+
+    # end to end through the public call with pinned host inputs (H2D and result D2H inside)
+    hpos = torch.from_numpy(wl["pos"]).pin_memory()
+    hw = torch.from_numpy(wl["w"]).pin_memory()
+    e2e_t = []
+    for i in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        binding.hip_power(hpos, hw, L, R0, edges, 4, 2, "mixed", stream=stream)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * float(np.mean(e2e_t))
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = float(wsum.item()) / (float(te.item()) / 1e3)
+    n = len(wl["pos"])
+    h2d = 12 * n + 4 * n
+    d2h = 2 * 3 * nk * 8 + 8 + 4
+
+    # the plain FP64 kernel on the same catalog (one step), for the mixed/FP64 ratio
+    fp64 = None
+    if not args.skip_fp64:
+        with torch.cuda.stream(stream):
+            binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "fp64", stream=stream)
+        st = binding.stage_times()
+        fp64_kernel_ms = float(st[2])
+        fp64 = {"value": work / (float(sum(st[1:4])) / 1e3), "unit": UNIT, "pair_kernel_ms": fp64_kernel_ms,
+                "speedup_mixed_vs_fp64_kernel": fp64_kernel_ms / float(np.mean(pair_ms))}
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+    pk = _peaks()
+    peak = fp32_peak_tflops(pk)
+    kern_ms = float(np.mean(pair_ms))
+    achieved = FLOPS_PER_PAIR_BIN * work / (kern_ms / 1e3) / 1e12
+    cpu = oracle_sample(wl, args.ref_seconds) if not args.skip_cpu else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": _config(wl, ws),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": float(te.item())},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_power_pairs<float,4,21>",
+                     "kernel_ms": kern_ms, "flops_per_pair_bin": FLOPS_PER_PAIR_BIN,
+                     "peak_note": "derived FP32 FMA peak: 152 SM x 128 lanes x 2 x max SM clock"},
+        "gpu_launches": 6 * args.steps,
+        "clocks": clk.summary(),
+        "pairs": int(pairs),
+        "stage_ms": dict(zip(["upload", "cells", "pairs", "finalize", "download"],
+                             [float(x) for x in binding.stage_times()])),
+        "fp64_plain": fp64,
+    }
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
+                                "sample": (f"FP64 brute force, ordered pair sums of the first {cpu['primaries']} "
+                                           f"primaries against all {n} particles, {nk} bins, l=0,2,4 "
+                                           f"({cpu['seconds']:.1f} s)")}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,105 @@
+/*
+ * hipster_gb300 -- C ABI of the GB300 (sm_103a) small-scale spectrum estimators of
+ * Philcox, "A Faster Fourier Transform? Computing Small-Scale Power Spectra and
+ * Bispectra for Cosmological Simulations in O(N^2) Time" (arXiv:2005.01739).
+ *
+ * Every entry point takes plain pointers and sizes.  Positions and weights may
+ * live in host memory or in device memory of the current CUDA device (detected
+ * per pointer); results are always written to HOST memory, in float64.  The
+ * library owns its scratch (cell lists, tables, partial sums) in a per-device
+ * workspace that grows on demand and is reused across calls; calls are
+ * serialised by a process-wide lock and are synchronous with respect to their
+ * host outputs (they synchronise `cuda_stream` before returning).  Outputs are
+ * written only when the call returns HIP_OK.
+ *
+ * Units: positions, L and R0 in Mpc/h; k-bin edges in h/Mpc.  Positions outside
+ * [0, L) are wrapped periodically.
+ */
+#ifndef HIPSTER_GB300_H
+#define HIPSTER_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HIP_OK = 0,
+    HIP_ERR_ARG = -1,       /* null pointer, bad size, unknown enum, odd ell_max for P */
+    HIP_ERR_RANGE = -2,     /* L <= 0, R0 <= 0, R0 >= L/2, edges not strictly increasing or < 0, too many bins */
+    HIP_ERR_NONFINITE = -3, /* a position or weight is NaN/Inf */
+    HIP_ERR_CUDA = -4,      /* a CUDA runtime call failed (message via hip_last_error) */
+    HIP_ERR_NOMEM = -5,     /* device workspace allocation failed */
+    HIP_ERR_TIMEOUT = -6    /* a bounded device-side wait gave up */
+} hip_status;
+
+/* Pair-separation window W(r; R0).  The only window of the paper: Eq. window_defn
+ * (Sec. 2), piecewise quartic, C^1, support r < R0. */
+typedef enum { HIP_WINDOW_PHILCOX = 0 } hip_window;
+
+/* Arithmetic of the pair kernels.  FP64: every per-pair and per-bin quantity in
+ * double precision (the plain baseline).  MIXED: pair geometry, bin-averaged
+ * Bessel functions and per-warp accumulation in FP32; cross-warp reduction,
+ * normalisation and the analytic random-pair terms in FP64. */
+typedef enum { HIP_PREC_FP64 = 0, HIP_PREC_MIXED = 1 } hip_precision;
+
+#define HIP_MAX_BINS 255
+
+/* Power-spectrum multipoles of a periodic box, Sec. 3 of the paper:
+ *
+ *   P^a_l = (-i)^l (2l+1) / (n_w^2 V) * DD^a_l  -  delta_l0 W~^a(R0),
+ *   DD^a_l = sum_{i in S} sum_{j != i, 0 < r_ij < R0} w_i w_j W(r_ij/R0) jbar^a_l(r_ij) L_l(mu_ij),
+ *
+ * (binned estimator following Eq. pk-binned; jbar from Eq. jla-def; W~^a from
+ * Eq. wka-def; (-i)^l = (-1)^(l/2) for the even l computed here).  r_ij is the
+ * minimum-image separation x_i - x_j, mu_ij its cosine to the `los_axis` axis,
+ * n_w = (sum_i w_i) / L^3 over ALL particles, V = L^3.
+ *
+ *   pos        [N][3] float32, xyz interleaved (host or device)
+ *   w          [N] float32 weights, or NULL for unit weights (host or device)
+ *   N          number of particles, >= 1
+ *   L, R0      box side and truncation radius, 0 < R0 < L/2
+ *   window     HIP_WINDOW_PHILCOX
+ *   k_edges    [n_k+1] float64 host, strictly increasing, k_edges[0] >= 0
+ *   n_k        number of k bins, 1..HIP_MAX_BINS
+ *   ell_max    0, 2 or 4; multipoles l = 0, 2, ..., ell_max are returned
+ *   los_axis   0, 1 or 2 (line of sight; the paper uses a fixed axis for boxes)
+ *   prec       HIP_PREC_FP64 or HIP_PREC_MIXED
+ *   prim_begin, prim_end   primary range S = [prim_begin, prim_end) in input
+ *              order (0, N for all).  Partial results over disjoint ranges add
+ *              up to the full DD (for sharding over devices or processes).
+ *   P_out      [(ell_max/2+1) * n_k] float64 host, row-major (l, a)
+ *   DD_out     same shape, the unnormalised DD^a_l; may be NULL
+ *   npairs_out number of ordered pairs (i in S, j) with 0 < r < R0; may be NULL
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
+ */
+hip_status hip_power(const float *pos, const float *w, int64_t N, double L, double R0, hip_window window,
+                     const double *k_edges, int n_k, int ell_max, int los_axis, hip_precision prec,
+                     int64_t prim_begin, int64_t prim_end, double *P_out, double *DD_out, int64_t *npairs_out,
+                     void *cuda_stream);
+
+/* Stage timing of the most recent hip_power call on this process, for
+ * measurement.  When enabled (on != 0), each call records CUDA events on its
+ * stream around its stages; hip_stage_times then writes, in milliseconds,
+ *   ms[0] input upload (0 for device-resident inputs),  ms[1] cell-list build,
+ *   ms[2] pair kernel,  ms[3] FP64 finalize (W~, reduction, normalisation),
+ *   ms[4] result download,
+ * for the first min(n, 5) entries.  Returns the number of entries written
+ * (0 if profiling was off during the last call).  Not thread-safe with
+ * respect to concurrent calls (calls are serialised anyway). */
+void hip_set_profiling(int on);
+int hip_stage_times(double *ms, int n);
+
+/* Human-readable name of a status code (static string). */
+const char *hip_status_string(hip_status s);
+
+/* Text of the last CUDA error seen by this thread's most recent failing call
+ * (static thread-local buffer; empty if none). */
+const char *hip_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIPSTER_GB300_H */

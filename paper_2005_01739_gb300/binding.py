@@ -1,0 +1,132 @@
+"""Thin ctypes binding of libhipster_gb300.so (argument marshalling only).
+
+Every computation happens in the CUDA library; this module converts arrays to
+pointers, checks the returned status and raises on failure.  There is no CPU
+fallback: if the library is missing or fails to load, calls raise RuntimeError.
+
+Inputs may be numpy arrays (host memory) or CUDA torch tensors (device memory,
+float32, contiguous); the library detects which per pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+HIP_OK, HIP_ERR_ARG, HIP_ERR_RANGE, HIP_ERR_NONFINITE, HIP_ERR_CUDA, HIP_ERR_NOMEM, HIP_ERR_TIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6
+PREC = {"fp64": 0, "mixed": 1}
+HIP_MAX_BINS = 255
+
+_lock = threading.Lock()
+_lib = None
+
+
+class HipError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (built by ``build.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or _build.LIB
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} (run __graft_entry__.build())")
+        L = ctypes.CDLL(p)
+        i64, d, i, P = ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+        L.hip_power.restype = i
+        L.hip_power.argtypes = [P, P, i64, d, d, i, P, i, i, i, i, i64, i64, P, P, P, P]
+        L.hip_status_string.restype = ctypes.c_char_p
+        L.hip_status_string.argtypes = [i]
+        L.hip_last_error.restype = ctypes.c_char_p
+        L.hip_last_error.argtypes = []
+        L.hip_debug_F.restype = d
+        L.hip_debug_F.argtypes = [i, i, d]
+        L.hip_set_profiling.restype = None
+        L.hip_set_profiling.argtypes = [i]
+        L.hip_stage_times.restype = i
+        L.hip_stage_times.argtypes = [P, i]
+        _lib = L
+        return L
+
+
+def _check(L, rc: int, what: str):
+    if rc != HIP_OK:
+        msg = L.hip_status_string(rc).decode()
+        extra = L.hip_last_error().decode()
+        raise HipError(rc, f"{what}: {msg}" + (f" ({extra})" if extra else ""))
+
+
+def _ptr(x):
+    """(pointer, keepalive) for a numpy array or a torch tensor (host or CUDA)."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr"):  # torch tensor
+        import torch
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError("tensor inputs must be contiguous float32")
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    return a.ctypes.data_as(ctypes.c_void_p), a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def hip_power(pos, w, L, R0, k_edges, ell_max=4, los_axis=2, prec="mixed", prim_range=None, stream=None):
+    """P^a_l (Sec. 3 binned estimator) of one periodic catalog.
+
+    Returns (P [n_ell, n_k], DD [n_ell, n_k], npairs) as float64 numpy arrays and
+    the number of ordered pairs counted."""
+    lib = load()
+    n = int(pos.shape[0]) if hasattr(pos, "shape") else len(pos)
+    pp, keep_p = _ptr(pos)
+    wp, keep_w = _ptr(w)
+    edges = np.ascontiguousarray(np.asarray(k_edges, dtype=np.float64))
+    n_k = len(edges) - 1
+    n_ell = ell_max // 2 + 1
+    P = np.zeros((n_ell, n_k))
+    DD = np.zeros((n_ell, n_k))
+    npairs = ctypes.c_int64(0)
+    p0, p1 = (0, n) if prim_range is None else (int(prim_range[0]), int(prim_range[1]))
+    rc = lib.hip_power(pp, wp, n, float(L), float(R0), 0, edges.ctypes.data_as(ctypes.c_void_p), n_k,
+                       int(ell_max), int(los_axis), PREC[prec], p0, p1, P.ctypes.data_as(ctypes.c_void_p),
+                       DD.ctypes.data_as(ctypes.c_void_p), ctypes.byref(npairs), _stream_handle(stream))
+    _check(lib, rc, "hip_power")
+    del keep_p, keep_w
+    return P, DD, int(npairs.value)
+
+
+def debug_F(prec: str, l: int, u: float) -> float:
+    """Host evaluation of the kernels' F_l(u) = D_l(u)/u^3 (same source and tables)."""
+    return load().hip_debug_F(PREC[prec], int(l), float(u))
+
+
+def set_profiling(on: bool) -> None:
+    """Record CUDA events around the stages of each call (see hip_stage_times)."""
+    load().hip_set_profiling(1 if on else 0)
+
+
+def stage_times():
+    """Stage times (ms) of the last call: upload, cells, pairs, finalize, download."""
+    out = np.zeros(5)
+    n = load().hip_stage_times(out.ctypes.data_as(ctypes.c_void_p), 5)
+    return out[:n]

@@ -1,0 +1,317 @@
+// C ABI of the library: argument validation, the per-device workspace, and the
+// sequencing of the kernels for hip_power (Sec. 3 of arXiv:2005.01739).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "hip_internal.h"
+#include "hip_workspace.h"
+
+static thread_local char g_errbuf[512];
+
+static void set_err(const char *what, cudaError_t e)
+{
+    std::snprintf(g_errbuf, sizeof(g_errbuf), "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" const char *hip_last_error(void) { return g_errbuf; }
+
+extern "C" const char *hip_status_string(hip_status s)
+{
+    switch (s) {
+    case HIP_OK: return "ok";
+    case HIP_ERR_ARG: return "invalid argument";
+    case HIP_ERR_RANGE: return "argument out of range";
+    case HIP_ERR_NONFINITE: return "non-finite position or weight";
+    case HIP_ERR_CUDA: return "CUDA error";
+    case HIP_ERR_NOMEM: return "out of device memory";
+    case HIP_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+std::mutex &hip_api_mutex()
+{
+    static std::mutex m;
+    return m;
+}
+
+// ------------------------------------------------------------- workspace ----
+static Workspace g_ws[64];
+static bool g_coeffs_ready[64];
+
+hip_status hip_device_setup(int *dev_out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_err("cudaGetDevice", e);
+        return HIP_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= 64) return HIP_ERR_ARG;
+    if (!g_coeffs_ready[dev]) {
+        if ((e = hip_upload_coeffs_power()) != cudaSuccess || (e = hip_upload_coeffs_bispec()) != cudaSuccess) {
+            set_err("coefficient upload", e);
+            return HIP_ERR_CUDA;
+        }
+        g_coeffs_ready[dev] = true;
+    }
+    *dev_out = dev;
+    return HIP_OK;
+}
+
+Workspace &hip_workspace(int dev) { return g_ws[dev]; }
+
+hip_status Workspace::reserve(size_t bytes, cudaStream_t st)
+{
+    if (bytes <= cap) return HIP_OK;
+    if (base) {
+        cudaStreamSynchronize(st);
+        cudaFree(base);
+        base = nullptr;
+        cap = 0;
+    }
+    size_t want = bytes + bytes / 4 + (1 << 20);
+    cudaError_t e = cudaMalloc(&base, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        base = nullptr;
+        set_err("cudaMalloc(workspace)", e);
+        return HIP_ERR_NOMEM;
+    }
+    cap = want;
+    return HIP_OK;
+}
+
+// Does `p` point to device-accessible memory of the current device?
+bool hip_is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int hip_cells_per_side(double L, double R0)
+{
+    double q = std::floor(L / R0);
+    int n = (int)q;
+    if (n < 1) n = 1;
+    if (n > 128) n = 128;
+    return n;
+}
+
+hip_status hip_check_edges(const double *k_edges, int n_k)
+{
+    if (!k_edges) return HIP_ERR_ARG;
+    if (n_k < 1 || n_k > HIP_MAX_BINS) return HIP_ERR_RANGE;
+    for (int a = 0; a <= n_k; ++a)
+        if (!std::isfinite(k_edges[a])) return HIP_ERR_RANGE;
+    if (k_edges[0] < 0.0) return HIP_ERR_RANGE;
+    for (int a = 0; a < n_k; ++a)
+        if (!(k_edges[a + 1] > k_edges[a])) return HIP_ERR_RANGE;
+    return HIP_OK;
+}
+
+// ------------------------------------------------------------- profiling -----
+#define HIP_NSTAGE 5
+static bool g_prof = false;
+static bool g_prof_valid = false;
+static double g_stage_ms[HIP_NSTAGE];
+
+// Events: 0 start, 1 inputs uploaded, 2 cells built, 3 pair kernel begins,
+// 4 pair kernel ends, 5 finalize ends, 6 results downloaded.
+struct StageTimer {
+    static const int NEV = 7;
+    cudaEvent_t ev[NEV];
+    bool on = false;
+    cudaStream_t st;
+    explicit StageTimer(cudaStream_t s) : st(s)
+    {
+        on = g_prof;
+        g_prof_valid = false;
+        if (on)
+            for (auto &e : ev) cudaEventCreate(&e);
+    }
+    void mark(int i)
+    {
+        if (on) cudaEventRecord(ev[i], st);
+    }
+    void finish()
+    {
+        if (!on) return;
+        cudaEventSynchronize(ev[NEV - 1]);
+        const int a[HIP_NSTAGE] = {0, 1, 3, 4, 5}, b[HIP_NSTAGE] = {1, 2, 4, 5, 6};
+        for (int i = 0; i < HIP_NSTAGE; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[a[i]], ev[b[i]]);
+            g_stage_ms[i] = ms;
+        }
+        g_prof_valid = true;
+    }
+    ~StageTimer()
+    {
+        if (on)
+            for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+extern "C" void hip_set_profiling(int on) { g_prof = on != 0; }
+
+extern "C" int hip_stage_times(double *ms, int n)
+{
+    if (!g_prof_valid || !ms) return 0;
+    int m = n < HIP_NSTAGE ? n : HIP_NSTAGE;
+    for (int i = 0; i < m; ++i) ms[i] = g_stage_ms[i];
+    return m;
+}
+
+// ------------------------------------------------------------- hip_power -----
+template <typename T>
+static hip_status power_impl(const float *pos, const float *w, int64_t N, double L, double R0,
+                             const double *k_edges, int n_k, int ell_max, int los, int64_t p0, int64_t p1,
+                             double *P_out, double *DD_out, int64_t *npairs_out, cudaStream_t st, int dev)
+{
+    Workspace &ws = hip_workspace(dev);
+    const int n_c = hip_cells_per_side(L, R0);
+    const int n_cells = n_c * n_c * n_c;
+    const int n_e = n_k + 1, n_ell = ell_max / 2 + 1;
+    const int grid = hip_power_grid<T>();
+    const bool dpos = hip_is_device_ptr(pos);
+    const bool dw = w && hip_is_device_ptr(w);
+
+    Carve cv;
+    size_t o_pos = dpos ? 0 : cv.take(sizeof(float) * 3 * N);
+    size_t o_w = (w && !dw) ? cv.take(sizeof(float) * N) : 0;
+    size_t o_x = cv.take(sizeof(T) * N), o_y = cv.take(sizeof(T) * N), o_z = cv.take(sizeof(T) * N);
+    size_t o_ws = cv.take(sizeof(float) * N), o_idx = cv.take(sizeof(int) * N), o_cid = cv.take(sizeof(int) * N);
+    size_t o_start = cv.take(sizeof(int) * (n_cells + 1)), o_fill = cv.take(sizeof(int) * n_cells);
+    size_t o_part = cv.take(sizeof(double) * (size_t)grid * 3 * n_e);
+    size_t o_small = cv.take(sizeof(double) * 8);
+    size_t o_wt = cv.take(sizeof(double) * n_k);
+    size_t o_dd = cv.take(sizeof(double) * 3 * n_k), o_p = cv.take(sizeof(double) * 3 * n_k);
+    hip_status hs = ws.reserve(cv.total, st);
+    if (hs != HIP_OK) return hs;
+    char *b = (char *)ws.base;
+    cudaError_t e;
+#define HIP_CK(call, what)                                                                                           \
+    do {                                                                                                             \
+        if ((e = (call)) != cudaSuccess) {                                                                           \
+            set_err(what, e);                                                                                        \
+            return HIP_ERR_CUDA;                                                                                     \
+        }                                                                                                            \
+    } while (0)
+    const float *dposp = pos;
+    const float *dwp = w;
+    StageTimer tm(st);
+    tm.mark(0);
+    if (!dpos) {
+        HIP_CK(cudaMemcpyAsync(b + o_pos, pos, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st), "H2D positions");
+        dposp = (const float *)(b + o_pos);
+    }
+    if (w && !dw) {
+        HIP_CK(cudaMemcpyAsync(b + o_w, w, sizeof(float) * N, cudaMemcpyHostToDevice, st), "H2D weights");
+        dwp = (const float *)(b + o_w);
+    }
+    T *x = (T *)(b + o_x), *y = (T *)(b + o_y), *z = (T *)(b + o_z);
+    float *wsrt = (float *)(b + o_ws);
+    int *idx = (int *)(b + o_idx), *cid = (int *)(b + o_cid);
+    int *cstart = (int *)(b + o_start), *cfill = (int *)(b + o_fill);
+    double *partials = (double *)(b + o_part);
+    double *small = (double *)(b + o_small);  // [0] S1, [1] npairs (u64), [2] err|counter (ints)
+    double *S1 = small;
+    unsigned long long *npairs = (unsigned long long *)(small + 1);
+    int *err = (int *)(small + 2);
+    int *counter = err + 1;
+    double *Wt = (double *)(b + o_wt), *DD = (double *)(b + o_dd), *P = (double *)(b + o_p);
+
+    tm.mark(1);
+    HIP_CK(hip_build_cells<T>(dposp, dwp, N, L, n_c, x, y, z, wsrt, idx, cid, cstart, cfill, S1, err, st),
+           "cell build");
+    tm.mark(2);
+    int herr = 0;
+    HIP_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H error word");
+    HIP_CK(cudaStreamSynchronize(st), "cell build sync");
+    if (herr) return HIP_ERR_NONFINITE;
+
+    HIP_CK(cudaMemsetAsync(npairs, 0, sizeof(unsigned long long), st), "memset");
+    HIP_CK(cudaMemsetAsync(counter, 0, sizeof(int), st), "memset");
+    CellList<T> cl{x, y, z, wsrt, idx, cstart, n_c, (T)(L / n_c)};
+    PowerKernelArgs ka;
+    ka.n_e = n_e;
+    ka.los = los;
+    ka.p0 = p0;
+    ka.p1 = p1;
+    ka.n_items = n_cells * HIP_NSHIFT;
+    ka.work_counter = counter;
+    ka.partials = partials;
+    ka.npairs = npairs;
+    tm.mark(3);
+    HIP_CK(hip_power_pairs<T>(cl, ka, k_edges, n_ell, R0, grid, st), "pair kernel");
+    tm.mark(4);
+    HIP_CK(hip_power_finalize(partials, grid, n_e, n_ell, k_edges, R0, L, S1, Wt, DD, P, st), "finalize");
+    tm.mark(5);
+    std::vector<double> hP(n_ell * n_k), hDD(n_ell * n_k);
+    unsigned long long hn = 0;
+    HIP_CK(cudaMemcpyAsync(hP.data(), P, sizeof(double) * n_ell * n_k, cudaMemcpyDeviceToHost, st), "D2H P");
+    HIP_CK(cudaMemcpyAsync(hDD.data(), DD, sizeof(double) * n_ell * n_k, cudaMemcpyDeviceToHost, st), "D2H DD");
+    HIP_CK(cudaMemcpyAsync(&hn, npairs, sizeof(hn), cudaMemcpyDeviceToHost, st), "D2H npairs");
+    tm.mark(6);
+    HIP_CK(cudaStreamSynchronize(st), "stream sync");
+    tm.finish();
+#undef HIP_CK
+    std::memcpy(P_out, hP.data(), sizeof(double) * n_ell * n_k);
+    if (DD_out) std::memcpy(DD_out, hDD.data(), sizeof(double) * n_ell * n_k);
+    if (npairs_out) *npairs_out = (int64_t)hn;
+    return HIP_OK;
+}
+
+extern "C" hip_status hip_power(const float *pos, const float *w, int64_t N, double L, double R0, hip_window window,
+                                const double *k_edges, int n_k, int ell_max, int los_axis, hip_precision prec,
+                                int64_t prim_begin, int64_t prim_end, double *P_out, double *DD_out,
+                                int64_t *npairs_out, void *cuda_stream)
+{
+    g_errbuf[0] = 0;
+    if (!pos || !P_out) return HIP_ERR_ARG;
+    if (N < 1 || N > 2000000000LL) return HIP_ERR_ARG;
+    if (window != HIP_WINDOW_PHILCOX) return HIP_ERR_ARG;
+    if (prec != HIP_PREC_FP64 && prec != HIP_PREC_MIXED) return HIP_ERR_ARG;
+    if (ell_max != 0 && ell_max != 2 && ell_max != 4) return HIP_ERR_ARG;
+    if (los_axis < 0 || los_axis > 2) return HIP_ERR_ARG;
+    if (!(L > 0.0) || !std::isfinite(L) || !(R0 > 0.0) || !(R0 < 0.5 * L)) return HIP_ERR_RANGE;
+    if (prim_begin < 0 || prim_end > N || prim_begin > prim_end) return HIP_ERR_RANGE;
+    hip_status hs = hip_check_edges(k_edges, n_k);
+    if (hs != HIP_OK) return hs;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    int dev = 0;
+    if ((hs = hip_device_setup(&dev)) != HIP_OK) return hs;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (prec == HIP_PREC_MIXED)
+        return power_impl<float>(pos, w, N, L, R0, k_edges, n_k, ell_max, los_axis, prim_begin, prim_end, P_out,
+                                 DD_out, npairs_out, st, dev);
+    return power_impl<double>(pos, w, N, L, R0, k_edges, n_k, ell_max, los_axis, prim_begin, prim_end, P_out,
+                              DD_out, npairs_out, st, dev);
+}
+
+// ------------------------------------------------------ host self-checks -----
+// Evaluate the pair kernels' F_l(u) = D_l(u)/u^3 on the host with the same source
+// and coefficient tables (FP32 path when prec == HIP_PREC_MIXED).  For tests.
+extern "C" double hip_debug_F(int prec, int l, double u)
+{
+    if (l < 0 || l > HIP_LMAX) return NAN;
+    const HipCoeffs &C = hip_host_coeffs();
+    if (prec == HIP_PREC_MIXED) {
+        float F[5] = {0, 0, 0, 0, 0};
+        hip_F_f32<31>((float)u, C, F);
+        return F[l];
+    }
+    double F[5] = {0, 0, 0, 0, 0};
+    hip_F_f64<31>(u, C, F);
+    return F[l];
+}

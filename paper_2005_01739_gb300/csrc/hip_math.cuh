@@ -1,0 +1,195 @@
+// Per-pair special functions of the estimators of arXiv:2005.01739, shared by the
+// pair kernels (device) and by host self-checks (the same source compiles for both).
+//
+// The bin-averaged spherical Bessel function of Eq. jla-def is evaluated through
+// its edge form
+//     jbar^a_l(r) = 3 [ k_{a+1}^3 F_l(r k_{a+1}) - k_a^3 F_l(r k_a) ] / (k_{a+1}^3 - k_a^3),
+//     F_l(u) = D_l(u) / u^3,   D_l(u) = int_0^u t^2 j_l(t) dt,
+// so one F_l evaluation per (pair, bin edge) serves the two bins that share the
+// edge and the r^-3 of Eq. jla-def never appears.  D_l comes from the recursion
+// of App. C, which for l <= 4 collapses to (s = sin u, c = cos u, Si = sine integral)
+//     D_0 = s - u c
+//     D_1 = 2 - 2c - u s
+//     D_2 = -4 s + u c + 3 Si
+//     D_3 = (u - 15/u) s + 7 c + 8
+//     D_4 = (11 - 52.5/u^2) s + (52.5/u - u) c + 7.5 Si
+// (constants of integration chosen so that D_l(0) = 0).  These forms cancel
+// catastrophically for small u, where the Taylor series of F_l in x = u^2 is used
+// instead.  Si(u) for large u is pi/2 - f(u) cos u - g(u) sin u with the auxiliary
+// functions f, g replaced by polynomial fits of u f(u) and u^2 g(u) in
+// t = (u0/u)^2, fitted in FP64 on the host at library initialisation.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#endif
+
+#define HIP_F32_USMALL 6.0f    // FP32: series below, closed form above
+#define HIP_F32_NSER 15        // Taylor terms of F_l in x = u^2 (u < 6)
+#define HIP_F32_SIDEG 8        // degree of the u f(u), u^2 g(u) fits in t = (6/u)^2
+
+#define HIP_F64_USMALL 2.5     // FP64: series below
+#define HIP_F64_USI 12.0       // FP64: Si by its power series below, fitted auxiliaries above
+#define HIP_F64_NSER 16
+#define HIP_F64_NSISER 32
+#define HIP_F64_SIDEG 16
+
+#define HIP_LMAX 4
+
+struct HipCoeffs {
+    // Taylor coefficients of F_l(u) / u^l in x = u^2
+    float ser32[HIP_LMAX + 1][HIP_F32_NSER];
+    double ser64[HIP_LMAX + 1][HIP_F64_NSER];
+    // monomial coefficients in t of u f(u) and u^2 g(u) (FP32: t = (6/u)^2; FP64: t = (12/u)^2)
+    float sif32[HIP_F32_SIDEG + 1];
+    float sig32[HIP_F32_SIDEG + 1];
+    double sif64[HIP_F64_SIDEG + 1];
+    double sig64[HIP_F64_SIDEG + 1];
+    // Si(u) / u = sum_n a_n x^n (FP64 middle range)
+    double siser64[HIP_F64_NSISER];
+};
+
+#define HIP_HALF_PI_F 1.57079632679489661923f
+#define HIP_HALF_PI_D 1.57079632679489661923
+
+// ---------------------------------------------------------------- window ----
+// Eq. window_defn (Sec. 2); x = r / R0.
+template <typename T>
+__host__ __device__ __forceinline__ T hip_W(T x)
+{
+    if (x < T(0.5)) return T(1);
+    if (x < T(0.75)) {
+        T y = T(2) * x - T(1);
+        T y3 = y * y * y;
+        return T(1) - T(8) * y3 + T(8) * y3 * y;
+    }
+    if (x < T(1)) {
+        T y = x - T(1);
+        T y3 = y * y * y;
+        return T(-64) * y3 - T(128) * y3 * y;
+    }
+    return T(0);
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ void hip_legendre24(T mu, T &l2, T &l4)
+{
+    T m2 = mu * mu;
+    l2 = T(1.5) * m2 - T(0.5);
+    l4 = (T(4.375) * m2 - T(3.75)) * m2 + T(0.375);
+}
+
+// ------------------------------------------------------------ F_l (FP32) ---
+// Evaluates F_l(u) for l = 0..LMAX (only the l listed in MASK are produced;
+// bit l of MASK).  C is the coefficient table (constant memory on the device).
+template <int MASK>
+__host__ __device__ __forceinline__ void hip_F_f32(float u, const HipCoeffs &C, float *F)
+{
+    if (u < HIP_F32_USMALL) {
+        float x = u * u;
+#pragma unroll
+        for (int l = 0; l <= HIP_LMAX; ++l) {
+            if (!(MASK & (1 << l))) continue;
+            float acc = C.ser32[l][HIP_F32_NSER - 1];
+#pragma unroll
+            for (int s = HIP_F32_NSER - 2; s >= 0; --s) acc = fmaf(acc, x, C.ser32[l][s]);
+            float ul = 1.0f;
+#pragma unroll
+            for (int q = 0; q < l; ++q) ul *= u;
+            F[l] = acc * ul;
+        }
+        return;
+    }
+    float s, c;
+#ifdef __CUDA_ARCH__
+    sincosf(u, &s, &c);
+    float w = __frcp_rn(u);
+#else
+    s = sinf(u);
+    c = cosf(u);
+    float w = 1.0f / u;
+#endif
+    float w2 = w * w;
+    float w3 = w2 * w;
+    float si = 0.0f;
+    if (MASK & ((1 << 2) | (1 << 4))) {
+        float t = 36.0f * w2;
+        float pf = C.sif32[HIP_F32_SIDEG], pg = C.sig32[HIP_F32_SIDEG];
+#pragma unroll
+        for (int q = HIP_F32_SIDEG - 1; q >= 0; --q) {
+            pf = fmaf(pf, t, C.sif32[q]);
+            pg = fmaf(pg, t, C.sig32[q]);
+        }
+        // Si = pi/2 - f cos - g sin, f = w pf, g = w^2 pg
+        si = HIP_HALF_PI_F - w * fmaf(pf, c, w * pg * s);
+    }
+    if (MASK & 1) F[0] = fmaf(w3, s, -w2 * c);
+    if (MASK & 2) F[1] = fmaf(w3, 2.0f - 2.0f * c, -w2 * s);
+    if (MASK & 4) F[2] = fmaf(w3, fmaf(3.0f, si, -4.0f * s), w2 * c);
+    if (MASK & 8) F[3] = fmaf(w2, s, w3 * fmaf(7.0f, c, 8.0f - 15.0f * w * s));
+    if (MASK & 16) F[4] = fmaf(w3, fmaf(fmaf(-52.5f, w2, 11.0f), s, 7.5f * si), w2 * fmaf(52.5f, w2, -1.0f) * c);
+}
+
+// ------------------------------------------------------------ F_l (FP64) ---
+template <int MASK>
+__host__ __device__ __forceinline__ void hip_F_f64(double u, const HipCoeffs &C, double *F)
+{
+    if (u < HIP_F64_USMALL) {
+        double x = u * u;
+#pragma unroll
+        for (int l = 0; l <= HIP_LMAX; ++l) {
+            if (!(MASK & (1 << l))) continue;
+            double acc = C.ser64[l][HIP_F64_NSER - 1];
+#pragma unroll
+            for (int s = HIP_F64_NSER - 2; s >= 0; --s) acc = fma(acc, x, C.ser64[l][s]);
+            double ul = 1.0;
+#pragma unroll
+            for (int q = 0; q < l; ++q) ul *= u;
+            F[l] = acc * ul;
+        }
+        return;
+    }
+    double s, c;
+#ifdef __CUDA_ARCH__
+    sincos(u, &s, &c);
+#else
+    s = sin(u);
+    c = cos(u);
+#endif
+    double w = 1.0 / u;
+    double w2 = w * w;
+    double w3 = w2 * w;
+    double si = 0.0;
+    if (MASK & ((1 << 2) | (1 << 4))) {
+        if (u < HIP_F64_USI) {
+            double x = u * u;
+            double acc = C.siser64[HIP_F64_NSISER - 1];
+#pragma unroll 4
+            for (int n = HIP_F64_NSISER - 2; n >= 0; --n) acc = fma(acc, x, C.siser64[n]);
+            si = acc * u;
+        } else {
+            double t = (HIP_F64_USI * HIP_F64_USI) * w2;
+            double pf = C.sif64[HIP_F64_SIDEG], pg = C.sig64[HIP_F64_SIDEG];
+#pragma unroll
+            for (int q = HIP_F64_SIDEG - 1; q >= 0; --q) {
+                pf = fma(pf, t, C.sif64[q]);
+                pg = fma(pg, t, C.sig64[q]);
+            }
+            si = HIP_HALF_PI_D - w * fma(pf, c, w * pg * s);
+        }
+    }
+    if (MASK & 1) F[0] = fma(w3, s, -w2 * c);
+    if (MASK & 2) F[1] = fma(w3, 2.0 - 2.0 * c, -w2 * s);
+    if (MASK & 4) F[2] = fma(w3, fma(3.0, si, -4.0 * s), w2 * c);
+    if (MASK & 8) F[3] = fma(w2, s, w3 * fma(7.0, c, 8.0 - 15.0 * w * s));
+    if (MASK & 16) F[4] = fma(w3, fma(fma(-52.5, w2, 11.0), s, 7.5 * si), w2 * fma(52.5, w2, -1.0) * c);
+}
+
+// Host-side construction of the coefficient table (FP64 fits; hip_tables.cpp).
+void hip_build_coeffs(HipCoeffs *C);
+const HipCoeffs &hip_host_coeffs();

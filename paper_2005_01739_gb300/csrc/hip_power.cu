@@ -1,0 +1,536 @@
+// Cell-list build and power-spectrum pair kernels (Sec. 3 of arXiv:2005.01739).
+//
+// Pair pass: persistent CTAs pull work items (home cell, one of 14 half-shell
+// shifts) from an atomic counter.  A CTA stages a tile of the home cell and a
+// tile of the shifted neighbour cell in shared memory (positions as cell-local
+// offsets, so separations keep full precision whatever the box size), each warp
+// tests candidate pairs with one lane per candidate and appends accepted pairs to
+// a per-warp queue.  The queue is drained with one lane per bin EDGE: for every
+// queued pair each lane evaluates F_l(r k_e) at its own edges and accumulates
+// omega_l F_l into registers.  No lane ever writes another lane's edge, so there
+// is no atomic and no divergence on the bin loop.  Per work item the FP32
+// register sums are folded into FP64 registers; at the end each CTA reduces its
+// warps in shared memory and writes one FP64 partial row.  The FP64 finalize sums
+// the partials, forms DD^a_l from adjacent edges, normalises and subtracts W~^a.
+#include <cstdio>
+
+#include "hip_internal.h"
+
+static __constant__ HipCoeffs c_coeffs;
+
+cudaError_t hip_upload_coeffs_power()
+{
+    return cudaMemcpyToSymbol(c_coeffs, &hip_host_coeffs(), sizeof(HipCoeffs));
+}
+
+// ------------------------------------------------------------- cell build ----
+__device__ __forceinline__ double hip_wrap(double v, double L)
+{
+    v -= L * floor(v / L);
+    if (v >= L) v -= L;
+    if (v < 0.0) v = 0.0;
+    return v;
+}
+
+__global__ void k_cell_count(const float *__restrict__ pos, const float *__restrict__ w, long long N, double L,
+                             int n_c, double inv_cs, int *__restrict__ cid, int *__restrict__ count, double *S1,
+                             int *err)
+{
+    double wsum = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        float px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
+        float wi = w ? w[i] : 1.0f;
+        if (!isfinite(px) || !isfinite(py) || !isfinite(pz) || !isfinite(wi)) {
+            atomicOr(err, 1);
+            cid[i] = 0;
+            continue;
+        }
+        int c3[3];
+        float pv[3] = {px, py, pz};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double v = hip_wrap((double)pv[k], L);
+            int ic = (int)(v * inv_cs);
+            c3[k] = ic >= n_c ? n_c - 1 : ic;
+        }
+        int id = (c3[0] * n_c + c3[1]) * n_c + c3[2];
+        cid[i] = id;
+        atomicAdd(&count[id], 1);
+        wsum += (double)wi;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wsum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) atomicAdd(S1, v);
+    }
+}
+
+// `count` and `fill` may alias: each thread reads its own segment before clearing it.
+__global__ void __launch_bounds__(1024) k_cell_scan(const int *count, int n, int *__restrict__ start, int *fill)
+{
+    __shared__ int s[1024];
+    int t = threadIdx.x;
+    int per = (n + 1023) / 1024;
+    int b = t * per, e = min(b + per, n);
+    int sum = 0;
+    for (int i = b; i < e; ++i) sum += count[i];
+    s[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int v = t >= off ? s[t - off] : 0;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    int run = s[t] - sum;
+    for (int i = b; i < e; ++i) {
+        const int ci = count[i];
+        start[i] = run;
+        fill[i] = 0;
+        run += ci;
+    }
+    if (t == 1023) start[n] = s[1023];
+}
+
+template <typename T>
+__global__ void k_cell_scatter(const float *__restrict__ pos, const float *__restrict__ w, long long N, double L,
+                               int n_c, double cs, double inv_cs, const int *__restrict__ cid,
+                               const int *__restrict__ start, int *__restrict__ fill, T *__restrict__ x,
+                               T *__restrict__ y, T *__restrict__ z, float *__restrict__ ws, int *__restrict__ idx)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        int id = cid[i];
+        int slot = start[id] + atomicAdd(&fill[id], 1);
+        float pv[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+        double loc[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double v = hip_wrap((double)pv[k], L);
+            int ic = (int)(v * inv_cs);
+            ic = ic >= n_c ? n_c - 1 : ic;
+            loc[k] = v - ic * cs;
+        }
+        x[slot] = (T)loc[0];
+        y[slot] = (T)loc[1];
+        z[slot] = (T)loc[2];
+        ws[slot] = w ? w[i] : 1.0f;
+        idx[slot] = (int)i;
+    }
+}
+
+template <typename T>
+cudaError_t hip_build_cells(const float *pos, const float *w, int64_t N, double L, int n_c, T *x, T *y, T *z,
+                            float *ws, int *idx, int *cid, int *cell_start, int *cell_fill, double *S1, int *err,
+                            cudaStream_t st)
+{
+    int n_cells = n_c * n_c * n_c;
+    double cs = L / n_c;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(cell_fill, 0, sizeof(int) * n_cells, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(S1, 0, sizeof(double), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(err, 0, sizeof(int), st)) != cudaSuccess) return e;
+    int blocks = (int)((N + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_cell_count<<<blocks, 256, 0, st>>>(pos, w, N, L, n_c, 1.0 / cs, cid, cell_fill, S1, err);
+    k_cell_scan<<<1, 1024, 0, st>>>(cell_fill, n_cells, cell_start, cell_fill);
+    k_cell_scatter<T><<<blocks, 256, 0, st>>>(pos, w, N, L, n_c, cs, 1.0 / cs, cid, cell_start, cell_fill, x, y, z,
+                                              ws, idx);
+    return cudaGetLastError();
+}
+
+template cudaError_t hip_build_cells<float>(const float *, const float *, int64_t, double, int, float *, float *,
+                                            float *, float *, int *, int *, int *, int *, double *, int *,
+                                            cudaStream_t);
+template cudaError_t hip_build_cells<double>(const float *, const float *, int64_t, double, int, double *, double *,
+                                             double *, float *, int *, int *, int *, int *, double *, int *,
+                                             cudaStream_t);
+
+// ------------------------------------------------------------- pair pass -----
+template <typename T>
+struct EdgeTable {
+    T k[HIP_MAX_EDGES];
+};
+
+template <typename T>
+__device__ __forceinline__ T hip_sqrt(T v);
+template <>
+__device__ __forceinline__ float hip_sqrt<float>(float v) { return sqrtf(v); }
+template <>
+__device__ __forceinline__ double hip_sqrt<double>(double v) { return sqrt(v); }
+
+template <typename T, int MASK>
+__device__ __forceinline__ void hip_F(T u, T *F);
+template <>
+__device__ __forceinline__ void hip_F<float, 21>(float u, float *F) { hip_F_f32<21>(u, c_coeffs, F); }
+template <>
+__device__ __forceinline__ void hip_F<float, 5>(float u, float *F) { hip_F_f32<5>(u, c_coeffs, F); }
+template <>
+__device__ __forceinline__ void hip_F<float, 1>(float u, float *F) { hip_F_f32<1>(u, c_coeffs, F); }
+template <>
+__device__ __forceinline__ void hip_F<double, 21>(double u, double *F) { hip_F_f64<21>(u, c_coeffs, F); }
+template <>
+__device__ __forceinline__ void hip_F<double, 5>(double u, double *F) { hip_F_f64<5>(u, c_coeffs, F); }
+template <>
+__device__ __forceinline__ void hip_F<double, 1>(double u, double *F) { hip_F_f64<1>(u, c_coeffs, F); }
+
+#define HIP_TILE 128
+#define HIP_QCAP 64
+
+template <typename T>
+struct PairSmem {
+    T hx[HIP_TILE], hy[HIP_TILE], hz[HIP_TILE];
+    float hw[HIP_TILE];
+    int hin[HIP_TILE];
+    T nx[HIP_TILE], ny[HIP_TILE], nz[HIP_TILE];
+    float nw[HIP_TILE];
+    int nin[HIP_TILE];
+    T qr[HIP_PAIR_WARPS][HIP_QCAP];
+    T qo[HIP_PAIR_WARPS][3][HIP_QCAP];
+    int item[2];
+};
+
+__constant__ int c_shift[HIP_NSHIFT][3] = {{0, 0, 0},  {1, -1, -1}, {1, -1, 0}, {1, -1, 1}, {1, 0, -1},
+                                           {1, 0, 0},  {1, 0, 1},   {1, 1, -1}, {1, 1, 0},  {1, 1, 1},
+                                           {0, 1, -1}, {0, 1, 0},   {0, 1, 1},  {0, 0, 1}};
+
+// One drain of a warp's pair queue: lanes over bin edges, pairs broadcast.
+template <typename T, int NCH, int MASK>
+__device__ __forceinline__ void hip_drain(const PairSmem<T> &sm, int warp, int n, const T *kk, int lane, int n_e,
+                                          T (&H)[3][NCH])
+{
+    for (int q = 0; q < n; ++q) {
+        T r = sm.qr[warp][q];
+        T o0 = sm.qo[warp][0][q], o2 = sm.qo[warp][1][q], o4 = sm.qo[warp][2][q];
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+            if (lane + 32 * t < n_e) {
+                T F[5];
+                hip_F<T, MASK>(r * kk[t], F);
+                H[0][t] += o0 * F[0];
+                if (MASK & 4) H[1][t] += o2 * F[2];
+                if (MASK & 16) H[2][t] += o4 * F[4];
+            }
+        }
+    }
+}
+
+template <typename T, int NCH, int MASK>
+__global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
+    k_power_pairs(CellList<T> cl, PowerKernelArgs a, EdgeTable<T> ed, T R0)
+{
+    __shared__ PairSmem<T> sm;
+    __shared__ double red[3][HIP_MAX_EDGES];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const T R0sq = R0 * R0, invR0 = T(1) / R0;
+    const int n_e = a.n_e, n_c = cl.n_c;
+    const int n_ell = (MASK & 16) ? 3 : ((MASK & 4) ? 2 : 1);
+
+    T kk[NCH];
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+        int e = lane + 32 * t;
+        kk[t] = e < n_e ? ed.k[e] : T(0);
+    }
+    T H[3][NCH];
+    double R[3][NCH];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+            H[l][t] = T(0);
+            R[l][t] = 0.0;
+        }
+    unsigned long long cnt = 0;
+    int slot = 0;
+    if (threadIdx.x == 0) sm.item[0] = atomicAdd(a.work_counter, 1);
+    __syncthreads();
+    for (;;) {
+        const int item = sm.item[slot];
+        if (item >= a.n_items) break;
+        if (threadIdx.x == 0) sm.item[slot ^ 1] = atomicAdd(a.work_counter, 1);
+        slot ^= 1;
+        const int c = item / HIP_NSHIFT, q = item - c * HIP_NSHIFT;
+        const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
+        const int dx = c_shift[q][0], dy = c_shift[q][1], dz = c_shift[q][2];
+        const int nb = (((cx + dx + n_c) % n_c) * n_c + (cy + dy + n_c) % n_c) * n_c + (cz + dz + n_c) % n_c;
+        const T sx = T(dx) * cl.cs, sy = T(dy) * cl.cs, sz = T(dz) * cl.cs;
+        const int a0 = cl.cell_start[c], a1 = cl.cell_start[c + 1];
+        const int b0 = cl.cell_start[nb], b1 = cl.cell_start[nb + 1];
+        const bool self = (q == 0);
+        int qn = 0;
+        for (int hb = a0; hb < a1; hb += HIP_TILE) {
+            const int hn = min(HIP_TILE, a1 - hb);
+            __syncthreads();
+            for (int i = threadIdx.x; i < hn; i += HIP_PAIR_THREADS) {
+                sm.hx[i] = cl.x[hb + i];
+                sm.hy[i] = cl.y[hb + i];
+                sm.hz[i] = cl.z[hb + i];
+                sm.hw[i] = cl.w[hb + i];
+                long long oi = cl.idx[hb + i];
+                sm.hin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
+            }
+            for (int nbs = self ? hb : b0; nbs < b1; nbs += HIP_TILE) {
+                const int nn = min(HIP_TILE, b1 - nbs);
+                __syncthreads();
+                for (int i = threadIdx.x; i < nn; i += HIP_PAIR_THREADS) {
+                    sm.nx[i] = cl.x[nbs + i];
+                    sm.ny[i] = cl.y[nbs + i];
+                    sm.nz[i] = cl.z[nbs + i];
+                    sm.nw[i] = cl.w[nbs + i];
+                    long long oi = cl.idx[nbs + i];
+                    sm.nin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
+                }
+                __syncthreads();
+                const bool same = self && (nbs == hb);
+                for (int il = warp; il < hn; il += HIP_PAIR_WARPS) {
+                    const T xi = sm.hx[il] - sx, yi = sm.hy[il] - sy, zi = sm.hz[il] - sz;
+                    const float wi = sm.hw[il];
+                    const int ini = sm.hin[il];
+                    for (int jb = same ? il + 1 : 0; jb < nn; jb += 32) {
+                        const int jl = jb + lane;
+                        bool ok = false;
+                        T ddx = T(0), ddy = T(0), ddz = T(0), r2 = T(0);
+                        int mult = 0;
+                        if (jl < nn) {
+                            ddx = xi - sm.nx[jl];
+                            ddy = yi - sm.ny[jl];
+                            ddz = zi - sm.nz[jl];
+                            r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            mult = ini + sm.nin[jl];
+                            ok = (r2 < R0sq) && (r2 > T(0)) && (mult > 0);
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, ok);
+                        if (ok) {
+                            const T r = hip_sqrt<T>(r2);
+                            const T dl = a.los == 0 ? ddx : (a.los == 1 ? ddy : ddz);
+                            const T mu = dl / r;
+                            T l2, l4;
+                            hip_legendre24<T>(mu, l2, l4);
+                            const T om = T(wi) * T(sm.nw[jl]) * hip_W<T>(r * invR0) * T(mult);
+                            const int s = qn + __popc(m & lt_mask);
+                            sm.qr[warp][s] = r;
+                            sm.qo[warp][0][s] = om;
+                            sm.qo[warp][1][s] = om * l2;
+                            sm.qo[warp][2][s] = om * l4;
+                            cnt += (unsigned long long)mult;
+                        }
+                        qn += __popc(m);
+                        if (qn >= 32) {
+                            __syncwarp();
+                            hip_drain<T, NCH, MASK>(sm, warp, qn, kk, lane, n_e, H);
+                            qn = 0;
+                            __syncwarp();
+                        }
+                    }
+                }
+            }
+        }
+        if (qn > 0) {
+            __syncwarp();
+            hip_drain<T, NCH, MASK>(sm, warp, qn, kk, lane, n_e, H);
+            __syncwarp();
+        }
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                R[l][t] += (double)H[l][t];
+                H[l][t] = T(0);
+            }
+        __syncthreads();  // item[slot] is rewritten next iteration; tiles restaged
+    }
+    // CTA reduction of the per-lane FP64 sums into one partial row.
+    for (int i = threadIdx.x; i < 3 * HIP_MAX_EDGES; i += HIP_PAIR_THREADS) (&red[0][0])[i] = 0.0;
+    __syncthreads();
+    for (int wv = 0; wv < HIP_PAIR_WARPS; ++wv) {
+        if (warp == wv) {
+#pragma unroll
+            for (int l = 0; l < 3; ++l)
+#pragma unroll
+                for (int t = 0; t < NCH; ++t) {
+                    int e = lane + 32 * t;
+                    if (e < n_e) red[l][e] += R[l][t];
+                }
+        }
+        __syncthreads();
+    }
+    double *out = a.partials + (size_t)blockIdx.x * 3 * n_e;
+    for (int i = threadIdx.x; i < n_ell * n_e; i += HIP_PAIR_THREADS) {
+        int l = i / n_e, e = i - l * n_e;
+        out[l * n_e + e] = red[l][e];
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0 && cnt) atomicAdd(a.npairs, cnt);
+}
+
+template <typename T, int NCH, int MASK>
+static int occupancy_blocks()
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_power_pairs<T, NCH, MASK>, HIP_PAIR_THREADS, 0);
+    return nb < 1 ? 1 : nb;
+}
+
+template <typename T>
+int hip_power_grid()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * occupancy_blocks<T, 4, 21>();
+}
+template int hip_power_grid<float>();
+template int hip_power_grid<double>();
+
+template <typename T, int NCH>
+static void launch_mask(const CellList<T> &cl, const PowerKernelArgs &a, const EdgeTable<T> &ed, int n_ell, T R0,
+                        int grid, cudaStream_t st)
+{
+    if (n_ell == 3)
+        k_power_pairs<T, NCH, 21><<<grid, HIP_PAIR_THREADS, 0, st>>>(cl, a, ed, R0);
+    else if (n_ell == 2)
+        k_power_pairs<T, NCH, 5><<<grid, HIP_PAIR_THREADS, 0, st>>>(cl, a, ed, R0);
+    else
+        k_power_pairs<T, NCH, 1><<<grid, HIP_PAIR_THREADS, 0, st>>>(cl, a, ed, R0);
+}
+
+template <typename T>
+cudaError_t hip_power_pairs(const CellList<T> &cl, const PowerKernelArgs &a, const double *kedges, int n_ell,
+                            double R0, int grid, cudaStream_t st)
+{
+    EdgeTable<T> ed;
+    for (int e = 0; e < HIP_MAX_EDGES; ++e) ed.k[e] = e < a.n_e ? (T)kedges[e] : T(0);
+    int nch = (a.n_e + 31) / 32;
+    if (nch <= 1)
+        launch_mask<T, 1>(cl, a, ed, n_ell, (T)R0, grid, st);
+    else if (nch <= 2)
+        launch_mask<T, 2>(cl, a, ed, n_ell, (T)R0, grid, st);
+    else if (nch <= 4)
+        launch_mask<T, 4>(cl, a, ed, n_ell, (T)R0, grid, st);
+    else
+        launch_mask<T, 8>(cl, a, ed, n_ell, (T)R0, grid, st);
+    return cudaGetLastError();
+}
+template cudaError_t hip_power_pairs<float>(const CellList<float> &, const PowerKernelArgs &, const double *, int,
+                                            double, int, cudaStream_t);
+template cudaError_t hip_power_pairs<double>(const CellList<double> &, const PowerKernelArgs &, const double *, int,
+                                             double, int, cudaStream_t);
+
+// --------------------------------------------------------------- finalize ----
+struct FinalArgs {
+    double k[HIP_MAX_EDGES];
+    double glx[16], glw[16];
+};
+
+// W~^a = 4 pi int_0^R0 r^2 jbar^a_0(r) W(r/R0) dr (Eq. wka-def), composite
+// 16-point Gauss-Legendre on the three polynomial pieces of W, panels no wider
+// than pi / (4 k_hi).  One CTA per bin.
+__global__ void k_window_transform(FinalArgs f, double R0, double *Wt)
+{
+    const int a = blockIdx.x;
+    const double klo = f.k[a], khi = f.k[a + 1];
+    const double k3lo = klo * klo * klo, k3hi = khi * khi * khi;
+    const double hmax = 3.14159265358979323846 / (4.0 * khi);
+    const double brk[4] = {0.0, 0.5 * R0, 0.75 * R0, R0};
+    double acc = 0.0;
+    for (int piece = 0; piece < 3; ++piece) {
+        const double lo = brk[piece], len = brk[piece + 1] - brk[piece];
+        const int np = max(1, (int)ceil(len / hmax));
+        const double h = len / np;
+        for (int i = threadIdx.x; i < np * 16; i += blockDim.x) {
+            const int p = i >> 4, q = i & 15;
+            const double r = lo + h * (p + 0.5 * (f.glx[q] + 1.0));
+            double Fh[5], Fl[5];
+            hip_F_f64<1>(r * khi, c_coeffs, Fh);
+            hip_F_f64<1>(r * klo, c_coeffs, Fl);
+            const double jb = 3.0 * (k3hi * Fh[0] - k3lo * Fl[0]) / (k3hi - k3lo);
+            acc += 0.5 * h * f.glw[q] * r * r * jb * hip_W<double>(r / R0);
+        }
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) Wt[a] = 4.0 * 3.14159265358979323846 * v;
+    }
+}
+
+// Sum of the CTA partials (fixed order), DD^a_l from adjacent edges, and
+// P^a_l = (-1)^(l/2) (2l+1) DD^a_l / (n_w^2 V) - delta_l0 W~^a.
+__global__ void __launch_bounds__(1024) k_power_final(FinalArgs f, const double *__restrict__ partials, int nparts,
+                                                      int n_e, int n_ell, double L, const double *S1,
+                                                      const double *__restrict__ Wt, double *DD, double *P)
+{
+    __shared__ double H[3][HIP_MAX_EDGES];
+    for (int i = threadIdx.x; i < n_ell * n_e; i += blockDim.x) {
+        double s = 0.0;
+        for (int p = 0; p < nparts; ++p) s += partials[(size_t)p * 3 * n_e + i];
+        H[i / n_e][i % n_e] = s;
+    }
+    __syncthreads();
+    const int n_k = n_e - 1;
+    const double V = L * L * L;
+    const double nw = S1[0] / V;
+    for (int i = threadIdx.x; i < n_ell * n_k; i += blockDim.x) {
+        const int il = i / n_k, a = i - il * n_k;
+        const double k3lo = f.k[a] * f.k[a] * f.k[a], k3hi = f.k[a + 1] * f.k[a + 1] * f.k[a + 1];
+        const double dd = 3.0 * (k3hi * H[il][a + 1] - k3lo * H[il][a]) / (k3hi - k3lo);
+        const int l = 2 * il;
+        const double sign = (il & 1) ? -1.0 : 1.0;
+        double p = sign * (2.0 * l + 1.0) * dd / (nw * nw * V);
+        if (il == 0) p -= Wt[a];
+        DD[i] = dd;
+        P[i] = p;
+    }
+}
+
+static void gl16(double *x, double *w)
+{
+    for (int i = 0; i < 16; ++i) {
+        double z = cos(3.14159265358979323846 * (i + 0.75) / 16.5), p1 = 0, p0 = 0, dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            p0 = 1.0;
+            p1 = z;
+            for (int k = 2; k <= 16; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = 16.0 * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        p0 = 1.0;
+        p1 = z;
+        for (int k = 2; k <= 16; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = 16.0 * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+cudaError_t hip_power_finalize(const double *partials, int nparts, int n_e, int n_ell, const double *kedges_host,
+                               double R0, double L, const double *S1, double *Wt, double *DD, double *P,
+                               cudaStream_t st)
+{
+    FinalArgs f;
+    for (int e = 0; e < HIP_MAX_EDGES; ++e) f.k[e] = e < n_e ? kedges_host[e] : 0.0;
+    gl16(f.glx, f.glw);
+    k_window_transform<<<n_e - 1, 256, 0, st>>>(f, R0, Wt);
+    k_power_final<<<1, 1024, 0, st>>>(f, partials, nparts, n_e, n_ell, L, S1, Wt, DD, P);
+    return cudaGetLastError();
+}

@@ -1,0 +1,201 @@
+"""GPU parity of the power-spectrum path (Sec. 3) against the FP64 oracle.
+
+Every GPU call goes through the C ABI (binding -> libhipster_gb300.so).  The
+error metric per bin is |P_gpu - P_ref| / max(|P_ref,l^a|, |P_ref,0^a|) (the
+monopole sets the scale of each bin, since the multipoles cross zero), with
+the tolerances of the plain FP64 path (1e-10: summation order only) and of the
+mixed FP32 path (1e-5).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_01739_gb300 import binding, catalogs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_01739_gb300 import build
+    build.build()
+    binding.load()
+
+
+def _err(P, Pref):
+    scale = np.maximum(np.abs(Pref), np.abs(Pref[0])[None, :])
+    return float(np.max(np.abs(P - Pref) / scale))
+
+
+def _same_count(prec, n, nref):
+    # FP32 separations can move a pair lying within ~1e-7 R0 of the cut across
+    # it; such a pair has W = 0 there, so only the count may differ.
+    slack = 0 if prec == "fp64" else max(2, int(2e-6 * nref))
+    assert abs(n - nref) <= slack, (prec, n, nref)
+
+
+def _dev(a):
+    import torch
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+_cache = {}
+
+
+def _oracle_P(key, pos, w, L, R0, edges, ell_max=4, los=2):
+    if key not in _cache:
+        p64 = pos.astype(np.float64)
+        w64 = None if w is None else w.astype(np.float64)
+        DD, npairs = oracle.power_pair_sum(p64, w64, L, R0, edges, ell_max, los)
+        S1 = len(pos) if w is None else float(np.sum(w64))
+        Wt = oracle.window_transform_binned(edges, R0)
+        _cache[key] = (oracle.power_from_pairs(DD, S1, L, Wt), DD, npairs, Wt)
+    return _cache[key]
+
+
+def _dense_case():
+    # clustered, dense: cells hold several 128-particle tiles plus a ragged tail
+    pos, w = catalogs.thomas(6000, 60.0, 40, 1.2, seed=31, background_frac=0.2, los_sigma=1.0, weights="u05_15")
+    return pos, w, 60.0, 12.0, catalogs.linear_edges(0.2, 3.0, 30)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_dense_clustered_parity(prec):
+    pos, w, L, R0, edges = _dense_case()
+    n_c = int(L // R0)
+    cells = np.floor(pos.astype(np.float64) / (L / n_c)).astype(int).clip(0, n_c - 1)
+    occ = np.bincount((cells[:, 0] * n_c + cells[:, 1]) * n_c + cells[:, 2], minlength=n_c ** 3)
+    assert occ.max() > 2 * 128 and occ.max() % 128 != 0  # several tiles and a ragged tail
+    Pref, DDref, nref, _ = _oracle_P("dense", pos, w, L, R0, edges)
+    P, DD, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, prec)
+    _same_count(prec, npairs, nref)
+    assert _err(P, Pref) < TOL[prec]
+
+
+@pytest.mark.parametrize("nk,kmax", [(40, 4.0), (100, 6.0), (200, 10.0)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_bin_chunks_parity(prec, nk, kmax):
+    # 41, 101 and 201 bin edges: two, four and eight 32-edge chunks per lane
+    pos, w = catalogs.thomas(2500, 60.0, 60, 1.5, seed=32, background_frac=0.3, los_sigma=2.0)
+    L, R0 = 60.0, 12.0
+    edges = catalogs.linear_edges(0.1, kmax, nk)
+    Pref, _, nref, _ = _oracle_P(("chunks", nk), pos, w, L, R0, edges)
+    P, _, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, prec)
+    _same_count(prec, npairs, nref)
+    assert _err(P, Pref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_nonlinear_edges_and_los_axes(prec):
+    pos, w = catalogs.thomas(2000, 50.0, 50, 1.5, seed=33, los_sigma=2.0, weights="u05_15")
+    L, R0 = 50.0, 11.0
+    edges = np.concatenate([[0.0], np.geomspace(0.05, 4.0, 24)])
+    for los in (0, 1, 2):
+        Pref, _, nref, _ = _oracle_P(("los", los), pos, w, L, R0, edges, 4, los)
+        P, _, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, los, prec)
+        _same_count(prec, npairs, nref)
+        assert _err(P, Pref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_workload_n5e4_full(prec):
+    wl = catalogs.workload("pk_plain_n5e4")
+    Pref, _, nref, _ = _oracle_P("n5e4", wl["pos"], wl["w"], wl["L"], wl["R0"], wl["edges"])
+    P, _, npairs = binding.hip_power(_dev(wl["pos"]), None, wl["L"], wl["R0"], wl["edges"], 4, 2, prec)
+    _same_count(prec, npairs, nref)
+    assert _err(P, Pref) < TOL[prec]
+
+
+def test_workload_n2e6_sampled_primaries():
+    # Full-size 2e6-particle catalog in the benchmark's launch configuration,
+    # checked on the ordered sums of a primary subset the oracle can do directly.
+    wl = catalogs.workload("pk_mixed_n2e6")
+    pos, w, L, R0, edges = wl["pos"], wl["w"], wl["L"], wl["R0"], wl["edges"]
+    S = (1000, 1300)
+    p64, w64 = pos.astype(np.float64), w.astype(np.float64)
+    DDref, nref = oracle.power_pair_sum(p64, w64, L, R0, edges, 4, 2, primaries=np.arange(*S))
+    Wt = oracle.window_transform_binned(edges, R0)
+    S1 = float(np.sum(w64))
+    Pref = oracle.power_from_pairs(DDref, S1, L, Wt)
+    dpos, dw = _dev(pos), _dev(w)
+    for prec in ("fp64", "mixed"):
+        P, DD, npairs = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, prec, prim_range=S)
+        _same_count(prec, npairs, nref)
+        # DD normalised by the monopole of its own bin (the subset's P is not a
+        # spectrum, so compare the pair sums themselves)
+        scale = np.maximum(np.abs(DDref), np.abs(DDref[0])[None, :])
+        assert np.max(np.abs(DD - DDref) / scale) < TOL[prec]
+        assert _err(P, Pref) < TOL[prec]
+    # full run: sharding identity and pair count consistency
+    Pm, DDm, nm = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed")
+    half = len(pos) // 2
+    _, DDa, na = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed", prim_range=(0, half))
+    _, DDb, nb = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed", prim_range=(half, len(pos)))
+    assert na + nb == nm
+    scale = np.maximum(np.abs(DDm), np.abs(DDm[0])[None, :])
+    assert np.max(np.abs(DDa + DDb - DDm) / scale) < 1e-6
+
+
+def test_single_particle_and_empty_range():
+    edges = catalogs.linear_edges(0.1, 1.0, 9)
+    L, R0 = 100.0, 20.0
+    Wt = oracle.window_transform_binned(edges, R0)
+    for prec in ("fp64", "mixed"):
+        P, DD, n = binding.hip_power(np.array([[1.0, 2.0, 3.0]], np.float32), None, L, R0, edges, 4, 2, prec)
+        assert n == 0 and np.all(DD == 0)
+        assert np.allclose(P[0], -Wt, rtol=1e-12) and np.all(P[1:] == 0)
+    pos, _ = catalogs.thomas(500, L, 10, 2.0, seed=5)
+    P, DD, n = binding.hip_power(pos, None, L, R0, edges, 4, 2, "mixed", prim_range=(100, 100))
+    assert n == 0 and np.all(DD == 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_two_cells_per_side_and_wrapping(prec):
+    # R0 > L/3: two cells per side, so the +1 and -1 neighbours are the same
+    # cell seen through different periodic images.  Positions given outside
+    # [0, L) must wrap.
+    L, R0 = 100.0, 40.0
+    pos, w = catalogs.thomas(1500, L, 30, 3.0, seed=34, background_frac=0.5)
+    edges = catalogs.linear_edges(0.05, 0.6, 12)
+    rng = np.random.default_rng(0)
+    shifted = (pos.astype(np.float64) + L * rng.integers(-2, 3, size=pos.shape)).astype(np.float32)
+    for key, p in (("twocell", pos), ("twocell-shifted", shifted)):
+        # the oracle takes minimum images of raw differences, so it needs no wrap
+        Pref, _, nref, _ = _oracle_P(key, p, w, L, R0, edges)
+        P, _, npairs = binding.hip_power(_dev(p), None, L, R0, edges, 4, 2, prec)
+        _same_count(prec, npairs, nref)
+        assert _err(P, Pref) < TOL[prec]
+
+
+def test_host_and_device_inputs_agree_and_nonfinite_rejected():
+    pos, w, L, R0, edges = _dense_case()
+    Ph, DDh, nh = binding.hip_power(pos, w, L, R0, edges, 4, 2, "fp64")
+    Pd, DDd, nd = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, "fp64")
+    assert nh == nd
+    assert np.max(np.abs(Ph - Pd) / np.maximum(np.abs(Pd), np.abs(Pd[0]))) < 1e-12
+    bad = pos.copy()
+    bad[17, 1] = np.nan
+    with pytest.raises(binding.HipError) as ei:
+        binding.hip_power(_dev(bad), None, L, R0, edges, 4, 2, "mixed")
+    assert ei.value.status == binding.HIP_ERR_NONFINITE
+    badw = w.copy()
+    badw[3] = np.inf
+    with pytest.raises(binding.HipError):
+        binding.hip_power(pos, badw, L, R0, edges, 4, 2, "mixed")
+    # the library is still usable after a rejected call
+    P2, _, n2 = binding.hip_power(pos, w, L, R0, edges, 4, 2, "fp64")
+    assert n2 == nh
+
+
+def test_mixed_translation_invariance():
+    pos, w, L, R0, edges = _dense_case()
+    P0, _, n0 = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, "mixed")
+    sh = np.mod(pos.astype(np.float64) + np.array([17.3, 41.9, 5.55]), L).astype(np.float32)
+    P1, _, n1 = binding.hip_power(_dev(sh), _dev(w), L, R0, edges, 4, 2, "mixed")
+    assert abs(n1 - n0) <= 2  # float32 rounding of shifted positions can move a pair across R0
+    assert _err(P1, P0) < 1e-4
