@@ -111,12 +111,16 @@ def _dist():
     return ws, rank, local
 
 
-def _workload(rank: int):
+def _workload(rank: int, scale: float = 1.0):
+    """The timed workload; `scale` < 1 shrinks the box volume (and N, parents)
+    by that factor at fixed density, R0 and bins, for profiler captures."""
     from paper_2005_01739_gb300 import catalogs
     wl = catalogs.workload(WORKLOAD)
-    if rank > 0:  # weak scaling: same size and settings, another seed
-        pos, w = catalogs.thomas(2_000_000, 1000.0, 50_000, 1.5, 1001 + 97 * rank, weights="u05_15")
-        wl = dict(wl, pos=pos, w=w)
+    if rank > 0 or scale != 1.0:  # weak scaling: same density and settings, another seed
+        L = 1000.0 * scale ** (1.0 / 3.0)
+        pos, w = catalogs.thomas(int(2_000_000 * scale), L, int(50_000 * scale), 1.5, 1001 + 97 * rank,
+                                 weights="u05_15")
+        wl = dict(wl, pos=pos, w=w, L=L)
     return wl
 
 
@@ -182,7 +186,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     binding.load()
-    wl = _workload(rank)
+    wl = _workload(rank, args.scale)
     L, R0, edges = wl["L"], wl["R0"], wl["edges"]
     nk = len(edges) - 1
     stream = torch.cuda.Stream()
@@ -301,6 +305,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the catalog volume at fixed density (profiler captures only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

