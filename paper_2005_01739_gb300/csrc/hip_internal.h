@@ -8,7 +8,7 @@
 #include "hip_math.cuh"
 
 #define HIP_MAX_EDGES (HIP_MAX_BINS + 1)
-#define HIP_PAIR_THREADS 256
+#define HIP_PAIR_THREADS 128
 #define HIP_PAIR_WARPS (HIP_PAIR_THREADS / 32)
 #define HIP_NSHIFT 14  // the home cell plus 13 forward neighbours (half shell)
 

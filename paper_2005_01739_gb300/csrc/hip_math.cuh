@@ -107,47 +107,44 @@ __host__ __device__ __forceinline__ void hip_legendre24(T mu, T &l2, T &l4)
 // is flat, so rounding 1/3 + small to a float gives the same rounding error for
 // every close pair, a bias that does not average out over many pairs.
 template <int MASK>
-__host__ __device__ __forceinline__ void hip_F_f32(float u, const HipCoeffs &C, float *Fm, float *Fc, bool &series)
+__host__ __device__ __forceinline__ void hip_F_f32_series(float u, const HipCoeffs &C, float *Fm, float *Fc)
 {
-    if (u < HIP_F32_USMALL) {
-        series = true;
-        const float x = u * u;
+    const float x = u * u;
 #pragma unroll
-        for (int l = 0; l <= HIP_LMAX; ++l) {
-            if (!(MASK & (1 << l))) continue;
-            float acc = C.ser32[l][HIP_F32_NSER - 1];
+    for (int l = 0; l <= HIP_LMAX; ++l) {
+        if (!(MASK & (1 << l))) continue;
+        float acc = C.ser32[l][HIP_F32_NSER - 1];
 #pragma unroll
-            for (int s = HIP_F32_NSER - 2; s >= 1; --s) acc = fmaf(acc, x, C.ser32[l][s]);
-            float cor = C.ser32lo[l][HIP_F32_NSERLO - 1];
+        for (int s = HIP_F32_NSER - 2; s >= 1; --s) acc = fmaf(acc, x, C.ser32[l][s]);
+        float cor = C.ser32lo[l][HIP_F32_NSERLO - 1];
 #pragma unroll
-            for (int s = HIP_F32_NSERLO - 2; s >= 0; --s) cor = fmaf(cor, x, C.ser32lo[l][s]);
-            float ul = 1.0f;
+        for (int s = HIP_F32_NSERLO - 2; s >= 0; --s) cor = fmaf(cor, x, C.ser32lo[l][s]);
+        float ul = 1.0f;
 #pragma unroll
-            for (int q = 0; q < l; ++q) ul *= u;
-            if (l == 0) {
-                Fm[0] = acc * x;
-            } else {
-                Fm[l] = fmaf(acc, x, C.ser32[l][0]) * ul;
-            }
-            Fc[l] = cor * ul;
+        for (int q = 0; q < l; ++q) ul *= u;
+        if (l == 0) {
+            Fm[0] = acc * x;
+        } else {
+            Fm[l] = fmaf(acc, x, C.ser32[l][0]) * ul;
         }
-        return;
+        Fc[l] = cor * ul;
     }
-    series = false;
-    float s, c;
+}
+
+// Closed forms of F_l = D_l / u^3 given s = sin u, c = cos u.
+template <int MASK>
+__host__ __device__ __forceinline__ void hip_F_f32_closed(float u, float s, float c, const HipCoeffs &C, float *Fm)
+{
 #ifdef __CUDA_ARCH__
-    sincosf(u, &s, &c);
-    float w = __frcp_rn(u);
+    const float w = __fdividef(1.0f, u);
 #else
-    s = sinf(u);
-    c = cosf(u);
-    float w = 1.0f / u;
+    const float w = 1.0f / u;
 #endif
-    float w2 = w * w;
-    float w3 = w2 * w;
+    const float w2 = w * w;
+    const float w3 = w2 * w;
     float si = 0.0f;
     if (MASK & ((1 << 2) | (1 << 4))) {
-        float t = 36.0f * w2;
+        const float t = 36.0f * w2;
         float pf = C.sif32[HIP_F32_SIDEG], pg = C.sig32[HIP_F32_SIDEG];
 #pragma unroll
         for (int q = HIP_F32_SIDEG - 1; q >= 0; --q) {
@@ -162,6 +159,25 @@ __host__ __device__ __forceinline__ void hip_F_f32(float u, const HipCoeffs &C, 
     if (MASK & 4) Fm[2] = fmaf(w3, fmaf(3.0f, si, -4.0f * s), w2 * c);
     if (MASK & 8) Fm[3] = fmaf(w2, s, w3 * fmaf(7.0f, c, 8.0f - 15.0f * w * s));
     if (MASK & 16) Fm[4] = fmaf(w3, fmaf(fmaf(-52.5f, w2, 11.0f), s, 7.5f * si), w2 * fmaf(52.5f, w2, -1.0f) * c);
+}
+
+template <int MASK>
+__host__ __device__ __forceinline__ void hip_F_f32(float u, const HipCoeffs &C, float *Fm, float *Fc, bool &series)
+{
+    if (u < HIP_F32_USMALL) {
+        series = true;
+        hip_F_f32_series<MASK>(u, C, Fm, Fc);
+        return;
+    }
+    series = false;
+    float s, c;
+#ifdef __CUDA_ARCH__
+    sincosf(u, &s, &c);
+#else
+    s = sinf(u);
+    c = cosf(u);
+#endif
+    hip_F_f32_closed<MASK>(u, s, c, C, Fm);
 #pragma unroll
     for (int l = 0; l <= HIP_LMAX; ++l) Fc[l] = 0.0f;
 }
@@ -179,43 +195,38 @@ __host__ __device__ __forceinline__ void hip_F_f32_total(float u, const HipCoeff
 
 // ------------------------------------------------------------ F_l (FP64) ---
 template <int MASK>
-__host__ __device__ __forceinline__ void hip_F_f64(double u, const HipCoeffs &C, double *F)
+__host__ __device__ __forceinline__ void hip_F_f64_series(double u, const HipCoeffs &C, double *F)
 {
-    if (u < HIP_F64_USMALL) {
-        double x = u * u;
+    const double x = u * u;
 #pragma unroll
-        for (int l = 0; l <= HIP_LMAX; ++l) {
-            if (!(MASK & (1 << l))) continue;
-            double acc = C.ser64[l][HIP_F64_NSER - 1];
+    for (int l = 0; l <= HIP_LMAX; ++l) {
+        if (!(MASK & (1 << l))) continue;
+        double acc = C.ser64[l][HIP_F64_NSER - 1];
 #pragma unroll
-            for (int s = HIP_F64_NSER - 2; s >= 0; --s) acc = fma(acc, x, C.ser64[l][s]);
-            double ul = 1.0;
+        for (int s = HIP_F64_NSER - 2; s >= 0; --s) acc = fma(acc, x, C.ser64[l][s]);
+        double ul = 1.0;
 #pragma unroll
-            for (int q = 0; q < l; ++q) ul *= u;
-            F[l] = acc * ul;
-        }
-        return;
+        for (int q = 0; q < l; ++q) ul *= u;
+        F[l] = acc * ul;
     }
-    double s, c;
-#ifdef __CUDA_ARCH__
-    sincos(u, &s, &c);
-#else
-    s = sin(u);
-    c = cos(u);
-#endif
-    double w = 1.0 / u;
-    double w2 = w * w;
-    double w3 = w2 * w;
+}
+
+template <int MASK>
+__host__ __device__ __forceinline__ void hip_F_f64_closed(double u, double s, double c, const HipCoeffs &C, double *F)
+{
+    const double w = 1.0 / u;
+    const double w2 = w * w;
+    const double w3 = w2 * w;
     double si = 0.0;
     if (MASK & ((1 << 2) | (1 << 4))) {
         if (u < HIP_F64_USI) {
-            double x = u * u;
+            const double x = u * u;
             double acc = C.siser64[HIP_F64_NSISER - 1];
 #pragma unroll 4
             for (int n = HIP_F64_NSISER - 2; n >= 0; --n) acc = fma(acc, x, C.siser64[n]);
             si = acc * u;
         } else {
-            double t = (HIP_F64_USI * HIP_F64_USI) * w2;
+            const double t = (HIP_F64_USI * HIP_F64_USI) * w2;
             double pf = C.sif64[HIP_F64_SIDEG], pg = C.sig64[HIP_F64_SIDEG];
 #pragma unroll
             for (int q = HIP_F64_SIDEG - 1; q >= 0; --q) {
@@ -230,6 +241,23 @@ __host__ __device__ __forceinline__ void hip_F_f64(double u, const HipCoeffs &C,
     if (MASK & 4) F[2] = fma(w3, fma(3.0, si, -4.0 * s), w2 * c);
     if (MASK & 8) F[3] = fma(w2, s, w3 * fma(7.0, c, 8.0 - 15.0 * w * s));
     if (MASK & 16) F[4] = fma(w3, fma(fma(-52.5, w2, 11.0), s, 7.5 * si), w2 * fma(52.5, w2, -1.0) * c);
+}
+
+template <int MASK>
+__host__ __device__ __forceinline__ void hip_F_f64(double u, const HipCoeffs &C, double *F)
+{
+    if (u < HIP_F64_USMALL) {
+        hip_F_f64_series<MASK>(u, C, F);
+        return;
+    }
+    double s, c;
+#ifdef __CUDA_ARCH__
+    sincos(u, &s, &c);
+#else
+    s = sin(u);
+    c = cos(u);
+#endif
+    hip_F_f64_closed<MASK>(u, s, c, C, F);
 }
 
 // Host-side construction of the coefficient table (FP64 fits; hip_tables.cpp).

@@ -12,6 +12,7 @@
 // register sums are folded into FP64 registers; at the end each CTA reduces its
 // warps in shared memory and writes one FP64 partial row.  The FP64 finalize sums
 // the partials, forms DD^a_l from adjacent edges, normalises and subtracts W~^a.
+#include <cmath>
 #include <cstdio>
 
 #include "hip_internal.h"
@@ -168,50 +169,69 @@ __device__ __forceinline__ float hip_sqrt<float>(float v) { return sqrtf(v); }
 template <>
 __device__ __forceinline__ double hip_sqrt<double>(double v) { return sqrt(v); }
 
-#define HIP_TILE 128
+#define HIP_WTILE 64
 #define HIP_QCAP 64
 
+// Shared memory of one warp: a tile of the home cell, a tile of the shifted
+// neighbour cell, and the queue of accepted pairs awaiting the bin pass.
 template <typename T>
-struct PairSmem {
-    T hx[HIP_TILE], hy[HIP_TILE], hz[HIP_TILE];
-    float hw[HIP_TILE];
-    int hin[HIP_TILE];
-    T nx[HIP_TILE], ny[HIP_TILE], nz[HIP_TILE];
-    float nw[HIP_TILE];
-    int nin[HIP_TILE];
-    T qr[HIP_PAIR_WARPS][HIP_QCAP];
-    T qo[HIP_PAIR_WARPS][3][HIP_QCAP];
-    int item[2];
+struct WarpSmem {
+    T hx[HIP_WTILE], hy[HIP_WTILE], hz[HIP_WTILE];
+    float hw[HIP_WTILE];
+    int hin[HIP_WTILE];
+    T nx[HIP_WTILE], ny[HIP_WTILE], nz[HIP_WTILE];
+    float nw[HIP_WTILE];
+    int nin[HIP_WTILE];
+    T qr[HIP_QCAP];                // separation r
+    T qo[3][HIP_QCAP];             // omega L_l(mu), l = 0, 2, 4
+    T qc[HIP_QCAP], qs[HIP_QCAP];  // cos, sin of 32 r dk: rotation between 32-edge chunks
 };
 
 __constant__ int c_shift[HIP_NSHIFT][3] = {{0, 0, 0},  {1, -1, -1}, {1, -1, 0}, {1, -1, 1}, {1, 0, -1},
                                            {1, 0, 0},  {1, 0, 1},   {1, 1, -1}, {1, 1, 0},  {1, 1, 1},
                                            {0, 1, -1}, {0, 1, 0},   {0, 1, 1},  {0, 0, 1}};
 
-// One drain of a warp's pair queue: lanes over bin edges, pairs broadcast.
-// FP32: H gets the main part of omega_l F_l (and, on the series branch, the
-// omega_0 / 3 constant as its own FMA); Hc gets the small coefficient-correction
-// part.  FP64: one accumulator.
-template <int NCH, int MASK>
-__device__ __forceinline__ void hip_drain(const PairSmem<float> &sm, int warp, int n, const float *kk,
-                                          const float *kl, int lane, int n_e, float (&H)[3][NCH],
-                                          float (&Hc)[3][NCH])
+__device__ __forceinline__ void hip_sincos(float u, float *s, float *c) { sincosf(u, s, c); }
+__device__ __forceinline__ void hip_sincos(double u, double *s, double *c) { sincos(u, s, c); }
+
+// Bin pass over the n queued pairs of a warp: lanes over bin edges (edge
+// lane + 32 t in chunk t), pairs broadcast.  sin/cos of u = r k_e come from one
+// accurate sincos in chunk 0 and, for uniformly spaced edges, a rotation by the
+// pair's 32 r dk for every later chunk.
+template <int NCH, int MASK, bool LIN>
+__device__ __forceinline__ void hip_drain(const WarpSmem<float> &sm, int n, const float *kk, const float *kl,
+                                          int lane, int n_e, float (&H)[3][NCH], float (&Hc)[3][NCH])
 {
     const float c0 = c_coeffs.ser32[0][0];
     for (int q = 0; q < n; ++q) {
-        const float r = sm.qr[warp][q];
-        const float o0 = sm.qo[warp][0][q], o2 = sm.qo[warp][1][q], o4 = sm.qo[warp][2][q];
+        const float r = sm.qr[q];
+        const float o0 = sm.qo[0][q], o2 = sm.qo[1][q], o4 = sm.qo[2][q];
+        const float rc = sm.qc[q], rs = sm.qs[q];
+        float s = 0.f, c = 1.f;
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
+            const float u = fmaf(r, kk[t], r * kl[t]);
+            if (LIN) {
+                if (t == 0) {
+                    sincosf(u, &s, &c);
+                } else {
+                    const float s2 = fmaf(s, rc, c * rs);
+                    c = fmaf(c, rc, -s * rs);
+                    s = s2;
+                }
+            }
             if (lane + 32 * t < n_e) {
                 float Fm[5], Fc[5];
-                bool series;
-                hip_F_f32<MASK>(fmaf(r, kk[t], r * kl[t]), c_coeffs, Fm, Fc, series);
-                if (series) {
+                if (u < HIP_F32_USMALL) {
+                    hip_F_f32_series<MASK>(u, c_coeffs, Fm, Fc);
                     H[0][t] = fmaf(o0, c0, H[0][t]);
                     Hc[0][t] = fmaf(o0, Fc[0], Hc[0][t]);
                     if (MASK & 4) Hc[1][t] = fmaf(o2, Fc[2], Hc[1][t]);
                     if (MASK & 16) Hc[2][t] = fmaf(o4, Fc[4], Hc[2][t]);
+                } else {
+                    float sc = s, cc = c;
+                    if (!LIN) sincosf(u, &sc, &cc);
+                    hip_F_f32_closed<MASK>(u, sc, cc, c_coeffs, Fm);
                 }
                 H[0][t] = fmaf(o0, Fm[0], H[0][t]);
                 if (MASK & 4) H[1][t] = fmaf(o2, Fm[2], H[1][t]);
@@ -221,19 +241,36 @@ __device__ __forceinline__ void hip_drain(const PairSmem<float> &sm, int warp, i
     }
 }
 
-template <int NCH, int MASK>
-__device__ __forceinline__ void hip_drain(const PairSmem<double> &sm, int warp, int n, const double *kk,
-                                          const double *, int lane, int n_e, double (&H)[3][NCH],
-                                          double (&)[3][NCH])
+template <int NCH, int MASK, bool LIN>
+__device__ __forceinline__ void hip_drain(const WarpSmem<double> &sm, int n, const double *kk, const double *,
+                                          int lane, int n_e, double (&H)[3][NCH], double (&)[3][NCH])
 {
     for (int q = 0; q < n; ++q) {
-        const double r = sm.qr[warp][q];
-        const double o0 = sm.qo[warp][0][q], o2 = sm.qo[warp][1][q], o4 = sm.qo[warp][2][q];
+        const double r = sm.qr[q];
+        const double o0 = sm.qo[0][q], o2 = sm.qo[1][q], o4 = sm.qo[2][q];
+        const double rc = sm.qc[q], rs = sm.qs[q];
+        double s = 0.0, c = 1.0;
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
+            const double u = r * kk[t];
+            if (LIN) {
+                if (t == 0) {
+                    sincos(u, &s, &c);
+                } else {
+                    const double s2 = fma(s, rc, c * rs);
+                    c = fma(c, rc, -s * rs);
+                    s = s2;
+                }
+            }
             if (lane + 32 * t < n_e) {
                 double F[5];
-                hip_F_f64<MASK>(r * kk[t], c_coeffs, F);
+                if (u < HIP_F64_USMALL) {
+                    hip_F_f64_series<MASK>(u, c_coeffs, F);
+                } else {
+                    double sc = s, cc = c;
+                    if (!LIN) sincos(u, &sc, &cc);
+                    hip_F_f64_closed<MASK>(u, sc, cc, c_coeffs, F);
+                }
                 H[0][t] = fma(o0, F[0], H[0][t]);
                 if (MASK & 4) H[1][t] = fma(o2, F[2], H[1][t]);
                 if (MASK & 16) H[2][t] = fma(o4, F[4], H[2][t]);
@@ -242,13 +279,23 @@ __device__ __forceinline__ void hip_drain(const PairSmem<double> &sm, int warp, 
     }
 }
 
-template <typename T, int NCH, int MASK>
-__global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
-    k_power_pairs(CellList<T> cl, PowerKernelArgs a, EdgeTable<T> ed, T R0)
+__device__ __forceinline__ float hip_rot_angle(float r, float dhi, float dlo) { return fmaf(r, dhi, r * dlo); }
+__device__ __forceinline__ double hip_rot_angle(double r, double dhi, double) { return r * dhi; }
+
+// Pair pass.  Each warp works on its own: it takes a work item (home cell,
+// half-shell shift) from the global counter, stages 64-particle tiles of both
+// cells in its own shared-memory slice, tests candidates one per lane, and
+// queues accepted pairs; the queue (which persists across work items) is
+// drained whenever it holds 32 pairs.  After each drain the FP32 register sums
+// are folded into FP64 registers, so an FP32 sum never spans more than 64 pairs.
+template <typename T, int NCH, int MASK, bool LIN>
+__global__ void __launch_bounds__(HIP_PAIR_THREADS)
+    k_power_pairs(CellList<T> cl, PowerKernelArgs a, EdgeTable<T> ed, T R0, T dk32hi, T dk32lo)
 {
-    __shared__ PairSmem<T> sm;
+    __shared__ WarpSmem<T> smem[HIP_PAIR_WARPS];
     __shared__ double red[3][HIP_MAX_EDGES];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem<T> &sm = smem[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
     const T R0sq = R0 * R0, invR0 = T(1) / R0;
     const int n_e = a.n_e, n_c = cl.n_c;
@@ -257,7 +304,7 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
     T kk[NCH], kl[NCH];
 #pragma unroll
     for (int t = 0; t < NCH; ++t) {
-        int e = lane + 32 * t;
+        const int e = lane + 32 * t;
         kk[t] = e < n_e ? ed.k[e] : T(0);
         kl[t] = e < n_e ? ed.klo[e] : T(0);
     }
@@ -272,14 +319,28 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
             R[l][t] = 0.0;
         }
     unsigned long long cnt = 0;
-    int slot = 0;
-    if (threadIdx.x == 0) sm.item[0] = atomicAdd(a.work_counter, 1);
-    __syncthreads();
+    int qn = 0;
+
+    auto drain = [&]() {
+        __syncwarp();
+        hip_drain<NCH, MASK, LIN>(sm, qn, kk, kl, lane, n_e, H, Hc);
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                R[l][t] += (double)H[l][t] + (double)Hc[l][t];
+                H[l][t] = T(0);
+                Hc[l][t] = T(0);
+            }
+        qn = 0;
+        __syncwarp();
+    };
+
     for (;;) {
-        const int item = sm.item[slot];
+        int item = 0;
+        if (lane == 0) item = atomicAdd(a.work_counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.n_items) break;
-        if (threadIdx.x == 0) sm.item[slot ^ 1] = atomicAdd(a.work_counter, 1);
-        slot ^= 1;
         const int c = item / HIP_NSHIFT, q = item - c * HIP_NSHIFT;
         const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
         const int dx = c_shift[q][0], dy = c_shift[q][1], dz = c_shift[q][2];
@@ -288,32 +349,31 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
         const int a0 = cl.cell_start[c], a1 = cl.cell_start[c + 1];
         const int b0 = cl.cell_start[nb], b1 = cl.cell_start[nb + 1];
         const bool self = (q == 0);
-        int qn = 0;
-        for (int hb = a0; hb < a1; hb += HIP_TILE) {
-            const int hn = min(HIP_TILE, a1 - hb);
-            __syncthreads();
-            for (int i = threadIdx.x; i < hn; i += HIP_PAIR_THREADS) {
+        for (int hb = a0; hb < a1; hb += HIP_WTILE) {
+            const int hn = min(HIP_WTILE, a1 - hb);
+            __syncwarp();
+            for (int i = lane; i < hn; i += 32) {
                 sm.hx[i] = cl.x[hb + i];
                 sm.hy[i] = cl.y[hb + i];
                 sm.hz[i] = cl.z[hb + i];
                 sm.hw[i] = cl.w[hb + i];
-                long long oi = cl.idx[hb + i];
+                const long long oi = cl.idx[hb + i];
                 sm.hin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
             }
-            for (int nbs = self ? hb : b0; nbs < b1; nbs += HIP_TILE) {
-                const int nn = min(HIP_TILE, b1 - nbs);
-                __syncthreads();
-                for (int i = threadIdx.x; i < nn; i += HIP_PAIR_THREADS) {
+            for (int nbs = self ? hb : b0; nbs < b1; nbs += HIP_WTILE) {
+                const int nn = min(HIP_WTILE, b1 - nbs);
+                __syncwarp();
+                for (int i = lane; i < nn; i += 32) {
                     sm.nx[i] = cl.x[nbs + i];
                     sm.ny[i] = cl.y[nbs + i];
                     sm.nz[i] = cl.z[nbs + i];
                     sm.nw[i] = cl.w[nbs + i];
-                    long long oi = cl.idx[nbs + i];
+                    const long long oi = cl.idx[nbs + i];
                     sm.nin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
                 }
-                __syncthreads();
+                __syncwarp();
                 const bool same = self && (nbs == hb);
-                for (int il = warp; il < hn; il += HIP_PAIR_WARPS) {
+                for (int il = 0; il < hn; ++il) {
                     const T xi = sm.hx[il] - sx, yi = sm.hy[il] - sy, zi = sm.hz[il] - sz;
                     const float wi = sm.hw[il];
                     const int ini = sm.hin[il];
@@ -338,39 +398,27 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
                             T l2, l4;
                             hip_legendre24<T>(mu, l2, l4);
                             const T om = T(wi) * T(sm.nw[jl]) * hip_W<T>(r * invR0) * T(mult);
-                            const int s = qn + __popc(m & lt_mask);
-                            sm.qr[warp][s] = r;
-                            sm.qo[warp][0][s] = om;
-                            sm.qo[warp][1][s] = om * l2;
-                            sm.qo[warp][2][s] = om * l4;
+                            const int slot = qn + __popc(m & lt_mask);
+                            sm.qr[slot] = r;
+                            sm.qo[0][slot] = om;
+                            sm.qo[1][slot] = om * l2;
+                            sm.qo[2][slot] = om * l4;
+                            if (LIN) {
+                                T rs, rc;
+                                hip_sincos(hip_rot_angle(r, dk32hi, dk32lo), &rs, &rc);
+                                sm.qc[slot] = rc;
+                                sm.qs[slot] = rs;
+                            }
                             cnt += (unsigned long long)mult;
                         }
                         qn += __popc(m);
-                        if (qn >= 32) {
-                            __syncwarp();
-                            hip_drain<NCH, MASK>(sm, warp, qn, kk, kl, lane, n_e, H, Hc);
-                            qn = 0;
-                            __syncwarp();
-                        }
+                        if (qn >= 32) drain();
                     }
                 }
             }
         }
-        if (qn > 0) {
-            __syncwarp();
-            hip_drain<NCH, MASK>(sm, warp, qn, kk, kl, lane, n_e, H, Hc);
-            __syncwarp();
-        }
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-#pragma unroll
-            for (int t = 0; t < NCH; ++t) {
-                R[l][t] += (double)H[l][t] + (double)Hc[l][t];
-                H[l][t] = T(0);
-                Hc[l][t] = T(0);
-            }
-        __syncthreads();  // item[slot] is rewritten next iteration; tiles restaged
     }
+    if (qn > 0) drain();
     // CTA reduction of the per-lane FP64 sums into one partial row.
     for (int i = threadIdx.x; i < 3 * HIP_MAX_EDGES; i += HIP_PAIR_THREADS) (&red[0][0])[i] = 0.0;
     __syncthreads();
@@ -380,7 +428,7 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
             for (int l = 0; l < 3; ++l)
 #pragma unroll
                 for (int t = 0; t < NCH; ++t) {
-                    int e = lane + 32 * t;
+                    const int e = lane + 32 * t;
                     if (e < n_e) red[l][e] += R[l][t];
                 }
         }
@@ -388,42 +436,61 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS, 2)
     }
     double *out = a.partials + (size_t)blockIdx.x * 3 * n_e;
     for (int i = threadIdx.x; i < n_ell * n_e; i += HIP_PAIR_THREADS) {
-        int l = i / n_e, e = i - l * n_e;
+        const int l = i / n_e, e = i - l * n_e;
         out[l * n_e + e] = red[l][e];
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if (lane == 0 && cnt) atomicAdd(a.npairs, cnt);
 }
 
-template <typename T, int NCH, int MASK>
-static int occupancy_blocks()
-{
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_power_pairs<T, NCH, MASK>, HIP_PAIR_THREADS, 0);
-    return nb < 1 ? 1 : nb;
-}
-
 template <typename T>
 int hip_power_grid()
 {
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, nb = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms * occupancy_blocks<T, 4, 21>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_power_pairs<T, 4, 21, true>, HIP_PAIR_THREADS, 0);
+    return sms * (nb < 1 ? 1 : nb);
 }
 template int hip_power_grid<float>();
 template int hip_power_grid<double>();
 
-template <typename T, int NCH>
+template <typename T, int NCH, bool LIN>
 static void launch_mask(const CellList<T> &cl, const PowerKernelArgs &a, const EdgeTable<T> &ed, int n_ell, T R0,
-                        int grid, cudaStream_t st)
+                        T dhi, T dlo, int grid, cudaStream_t st)
 {
     if (n_ell == 3)
-        k_power_pairs<T, NCH, 21><<<grid, HIP_PAIR_THREADS, 0, st>>>(cl, a, ed, R0);
+        k_power_pairs<T, NCH, 21, LIN><<<grid, HIP_PAIR_THREADS, 0, st>>>(cl, a, ed, R0, dhi, dlo);
     else if (n_ell == 2)
-        k_power_pairs<T, NCH, 5><<<grid, HIP_PAIR_THREADS, 0, st>>>(cl, a, ed, R0);
+        k_power_pairs<T, NCH, 5, LIN><<<grid, HIP_PAIR_THREADS, 0, st>>>(cl, a, ed, R0, dhi, dlo);
     else
-        k_power_pairs<T, NCH, 1><<<grid, HIP_PAIR_THREADS, 0, st>>>(cl, a, ed, R0);
+        k_power_pairs<T, NCH, 1, LIN><<<grid, HIP_PAIR_THREADS, 0, st>>>(cl, a, ed, R0, dhi, dlo);
+}
+
+template <typename T, bool LIN>
+static void launch_nch(const CellList<T> &cl, const PowerKernelArgs &a, const EdgeTable<T> &ed, int n_ell, T R0,
+                       T dhi, T dlo, int grid, cudaStream_t st)
+{
+    const int nch = (a.n_e + 31) / 32;
+    if (nch <= 1)
+        launch_mask<T, 1, LIN>(cl, a, ed, n_ell, R0, dhi, dlo, grid, st);
+    else if (nch <= 2)
+        launch_mask<T, 2, LIN>(cl, a, ed, n_ell, R0, dhi, dlo, grid, st);
+    else if (nch <= 4)
+        launch_mask<T, 4, LIN>(cl, a, ed, n_ell, R0, dhi, dlo, grid, st);
+    else
+        launch_mask<T, 8, LIN>(cl, a, ed, n_ell, R0, dhi, dlo, grid, st);
+}
+
+// Are the edges uniformly spaced (to 1e-12 of their magnitude)?
+static bool edges_linear(const double *k, int n_e, double *dk)
+{
+    if (n_e < 2) return false;
+    const double d = (k[n_e - 1] - k[0]) / (n_e - 1);
+    for (int e = 0; e < n_e; ++e)
+        if (std::fabs(k[e] - (k[0] + e * d)) > 1e-12 * (std::fabs(k[n_e - 1]) + std::fabs(k[0]))) return false;
+    *dk = d;
+    return true;
 }
 
 template <typename T>
@@ -431,20 +498,19 @@ cudaError_t hip_power_pairs(const CellList<T> &cl, const PowerKernelArgs &a, con
                             double R0, int grid, cudaStream_t st)
 {
     EdgeTable<T> ed;
+    double dk = 0.0;
+    const bool lin = edges_linear(kedges, a.n_e, &dk);
     for (int e = 0; e < HIP_MAX_EDGES; ++e) {
-        double k = e < a.n_e ? kedges[e] : 0.0;
+        const double k = e < a.n_e ? kedges[e] : 0.0;
         ed.k[e] = (T)k;
         ed.klo[e] = (T)(k - (double)ed.k[e]);
     }
-    int nch = (a.n_e + 31) / 32;
-    if (nch <= 1)
-        launch_mask<T, 1>(cl, a, ed, n_ell, (T)R0, grid, st);
-    else if (nch <= 2)
-        launch_mask<T, 2>(cl, a, ed, n_ell, (T)R0, grid, st);
-    else if (nch <= 4)
-        launch_mask<T, 4>(cl, a, ed, n_ell, (T)R0, grid, st);
+    const double d32 = 32.0 * dk;
+    const T dhi = (T)d32, dlo = (T)(d32 - (double)dhi);
+    if (lin)
+        launch_nch<T, true>(cl, a, ed, n_ell, (T)R0, dhi, dlo, grid, st);
     else
-        launch_mask<T, 8>(cl, a, ed, n_ell, (T)R0, grid, st);
+        launch_nch<T, false>(cl, a, ed, n_ell, (T)R0, dhi, dlo, grid, st);
     return cudaGetLastError();
 }
 template cudaError_t hip_power_pairs<float>(const CellList<float> &, const PowerKernelArgs &, const double *, int,

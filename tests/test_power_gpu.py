@@ -142,7 +142,7 @@ def test_workload_n2e6_sampled_primaries():
     _, DDa, na = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed", prim_range=(0, half))
     _, DDb, nb = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed", prim_range=(half, len(pos)))
     assert na + nb == nm
-    assert np.max(np.abs(DDa + DDb - DDm) / _scale(DDm)) < 1e-6
+    assert np.max(np.abs(DDa + DDb - DDm) / _scale(DDm)) < TOL["mixed"]
 
 
 def test_single_particle_and_empty_range():
