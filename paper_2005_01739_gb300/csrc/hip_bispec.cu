@@ -1,9 +1,405 @@
 // Bispectrum kernels (Sec. 4 of arXiv:2005.01739).
+//
+// For every primary p (data particles, then the random catalog) the kernel
+// forms, over data neighbours j with 0 < |x_p - x_j| < R0,
+//     A^a_lm(p) = sum_j w_j W(r/R0) jbar^a_l(r) R_lm(rhat)        (Eq. AC-def, binned)
+//     C^ab_l(p) = sum_j w_j^2 W^2 jbar^a_l(r) jbar^b_l(r)
+// with real spherical harmonics R_lm scaled so that sum_m R_lm(u) R_lm(v) =
+// L_l(u.v) (the addition theorem with the 4 pi / (2l+1) absorbed; real and
+// complex harmonics give the same sum over m), and accumulates
+//     T^ab_l += s_p [ sum_m A^a_lm A^b_lm - C^ab_l ](p),
+// s_p = w_p for data primaries and -S1/N_r for random ones (the DDR^II term
+// of Sec. 4.3 estimated with a random catalog).
+//
+// One warp owns one primary at a time.  Accepted neighbours go to a per-warp
+// queue holding r, w_j W, w_j^2 W^2 and the 25 R_lm; the queue is drained with
+// one lane per bin edge e, each lane evaluating F_l(r k_e), l = 0..4 (see
+// hip_math.cuh) and accumulating w W F_l R_lm into its 25 registers.  The same
+// drain forms jbar^a_l from adjacent edges and stages it for the C term.  At
+// the end of a primary the edge sums are differenced into A^a_lm and contracted.
+#include <cmath>
+#include <cstdio>
+
 #include "hip_internal.h"
+#include "hip_bispec.h"
 
 static __constant__ HipCoeffs c_coeffs;
+// normalisation of the real harmonics: sqrt((l-m)!/(l+m)!) (times sqrt 2 for m > 0)
+static __constant__ float c_ylm_norm_f[HIP_LMAX + 1][HIP_LMAX + 1];
+static __constant__ double c_ylm_norm_d[HIP_LMAX + 1][HIP_LMAX + 1];
 
 cudaError_t hip_upload_coeffs_bispec()
 {
-    return cudaMemcpyToSymbol(c_coeffs, &hip_host_coeffs(), sizeof(HipCoeffs));
+    cudaError_t e = cudaMemcpyToSymbol(c_coeffs, &hip_host_coeffs(), sizeof(HipCoeffs));
+    if (e != cudaSuccess) return e;
+    float nf[HIP_LMAX + 1][HIP_LMAX + 1];
+    double nd[HIP_LMAX + 1][HIP_LMAX + 1];
+    for (int l = 0; l <= HIP_LMAX; ++l)
+        for (int m = 0; m <= HIP_LMAX; ++m) {
+            double v = 0.0;
+            if (m <= l) {
+                double r = 1.0;
+                for (int k = l - m + 1; k <= l + m; ++k) r /= k;
+                v = std::sqrt(r) * (m > 0 ? std::sqrt(2.0) : 1.0);
+            }
+            nd[l][m] = v;
+            nf[l][m] = (float)v;
+        }
+    if ((e = cudaMemcpyToSymbol(c_ylm_norm_f, nf, sizeof(nf))) != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_ylm_norm_d, nd, sizeof(nd));
+}
+
+template <typename T>
+__device__ __forceinline__ T ylm_norm(int l, int m);
+template <>
+__device__ __forceinline__ float ylm_norm<float>(int l, int m) { return c_ylm_norm_f[l][m]; }
+template <>
+__device__ __forceinline__ double ylm_norm<double>(int l, int m) { return c_ylm_norm_d[l][m]; }
+
+// Real harmonics R_lm(u) for l <= 4 at unit vector (x, y, z), index l*l + l + m:
+// R_l0 = P_l(z); R_l,+m = n_lm Ptilde_l^m(z) Re (x + i y)^m; R_l,-m = same with Im,
+// Ptilde_l^m(z) = P_l^m(z) / (1 - z^2)^(m/2) by the usual three-term recurrence.
+template <typename T>
+__device__ __forceinline__ void hip_real_ylm(T x, T y, T z, T *R)
+{
+    T P[HIP_LMAX + 1][HIP_LMAX + 1];
+#pragma unroll
+    for (int m = 0; m <= HIP_LMAX; ++m) {
+        T pmm = T(1);
+#pragma unroll
+        for (int k = 1; k <= m; ++k) pmm *= T(2 * k - 1);
+        P[m][m] = pmm;
+        if (m + 1 <= HIP_LMAX) P[m + 1][m] = T(2 * m + 1) * z * pmm;
+#pragma unroll
+        for (int l = m + 2; l <= HIP_LMAX; ++l)
+            P[l][m] = (T(2 * l - 1) * z * P[l - 1][m] - T(l + m - 1) * P[l - 2][m]) * (T(1) / T(l - m));
+    }
+    T cm[HIP_LMAX + 1], sm[HIP_LMAX + 1];
+    cm[0] = T(1);
+    sm[0] = T(0);
+#pragma unroll
+    for (int m = 1; m <= HIP_LMAX; ++m) {
+        cm[m] = cm[m - 1] * x - sm[m - 1] * y;
+        sm[m] = sm[m - 1] * x + cm[m - 1] * y;
+    }
+#pragma unroll
+    for (int l = 0; l <= HIP_LMAX; ++l) {
+        R[l * l + l] = P[l][0];
+#pragma unroll
+        for (int m = 1; m <= l; ++m) {
+            const T b = ylm_norm<T>(l, m) * P[l][m];
+            R[l * l + l + m] = b * cm[m];
+            R[l * l + l - m] = b * sm[m];
+        }
+    }
+}
+
+#define HIP_BQ 16                       // neighbours per drain
+#define HIP_BQCAP (HIP_BQ + 32)         // queue capacity (a ballot adds up to 32)
+#define HIP_BWARPS 4
+#define HIP_BTHREADS (HIP_BWARPS * 32)
+#define HIP_NLM 25
+
+template <typename T, int NKMAX>
+struct BWarpSmem {
+    T qr[HIP_BQCAP], qw[HIP_BQCAP], qpsi[HIP_BQCAP];
+    T qy[HIP_NLM][HIP_BQCAP];
+    T J[HIP_LMAX + 1][HIP_BQ][NKMAX];  // jbar^a_l of each drained neighbour
+    T X[NKMAX + 1][HIP_NLM];           // k_e^3 * (edge sums), then A^a_lm
+};
+
+__device__ __forceinline__ float hip_sqrt_b(float v) { return sqrtf(v); }
+__device__ __forceinline__ double hip_sqrt_b(double v) { return sqrt(v); }
+
+// F_l(u), l = 0..4, as one number per l.
+__device__ __forceinline__ void hip_F_all(float u, float *F)
+{
+    float Fm[5], Fc[5];
+    bool series;
+    hip_F_f32<31>(u, c_coeffs, Fm, Fc, series);
+#pragma unroll
+    for (int l = 0; l <= HIP_LMAX; ++l) F[l] = Fm[l] + Fc[l];
+    if (series) F[0] += c_coeffs.ser32[0][0];
+}
+__device__ __forceinline__ void hip_F_all(double u, double *F) { hip_F_f64<31>(u, c_coeffs, F); }
+
+__device__ __forceinline__ float hip_arg(float r, float khi, float klo) { return fmaf(r, khi, r * klo); }
+__device__ __forceinline__ double hip_arg(double r, double khi, double) { return r * khi; }
+
+// Drain n queued neighbours of one primary: lanes over edges.  Accumulates the
+// edge sums E[t][lm] += w W F_l(r k_e) R_lm and stages jbar^a_l for the C term.
+template <typename T, int NCH, int NKMAX>
+__device__ __forceinline__ void hip_bdrain(BWarpSmem<T, NKMAX> &sm, int n, const T *kk, const T *kl, const T *k3,
+                                           const T *k3n, const T *jfac, int lane, int n_e, T (&E)[NCH][HIP_NLM])
+{
+    for (int q = 0; q < n; ++q) {
+        const T r = sm.qr[q], ww = sm.qw[q];
+        T F[NCH][HIP_LMAX + 1];
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+            hip_F_all(hip_arg(r, kk[t], kl[t]), F[t]);
+            if (lane + 32 * t < n_e) {
+#pragma unroll
+                for (int l = 0; l <= HIP_LMAX; ++l) {
+                    const T f = ww * F[t][l];
+#pragma unroll
+                    for (int m = -l; m <= l; ++m) E[t][l * l + l + m] += f * sm.qy[l * l + l + m][q];
+                }
+            }
+        }
+        // jbar^a_l = jfac_a (k_{a+1}^3 F_l(u_{a+1}) - k_a^3 F_l(u_a)), a = lane + 32 t
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+#pragma unroll
+            for (int l = 0; l <= HIP_LMAX; ++l) {
+                T nxt = __shfl_down_sync(0xffffffffu, F[t][l], 1);
+                const T wrap = __shfl_sync(0xffffffffu, F[(t + 1 < NCH) ? t + 1 : t][l], 0);
+                if (lane == 31 && t + 1 < NCH) nxt = wrap;
+                const int a = lane + 32 * t;
+                if (a < n_e - 1) sm.J[l][q][a] = jfac[t] * (k3n[t] * nxt - k3[t] * F[t][l]);
+            }
+        }
+    }
+}
+
+// Tc[l][a][b] -= s_p sum_q psi_q J[l][q][a] J[l][q][b]  (the C term).
+template <typename T, int NKMAX>
+__device__ __forceinline__ void hip_cterm(const BWarpSmem<T, NKMAX> &sm, int n, int nk, T sp, int lane, float *Tc)
+{
+    const int per_l = nk * nk;
+    for (int i = lane; i < (HIP_LMAX + 1) * per_l; i += 32) {
+        const int l = i / per_l, ab = i - l * per_l, a = ab / nk, b = ab - a * nk;
+        T acc = T(0);
+        for (int q = 0; q < n; ++q) acc += sm.qpsi[q] * sm.J[l][q][a] * sm.J[l][q][b];
+        atomicAdd(&Tc[i], (float)(-sp * acc));
+    }
+}
+
+template <typename T, int NCH, int NKMAX>
+__global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
+{
+    __shared__ BWarpSmem<T, NKMAX> smem[HIP_BWARPS];
+    extern __shared__ float Tc[];  // [5][nk][nk] CTA accumulator
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    BWarpSmem<T, NKMAX> &sm = smem[warp];
+    const int n_e = a.n_e, nk = n_e - 1, n_c = a.data.n_c;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const T R0sq = a.R0 * a.R0, invR0 = T(1) / a.R0;
+    for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) Tc[i] = 0.f;
+    __syncthreads();
+
+    T kk[NCH], kl[NCH], k3[NCH], k3n[NCH], jfac[NCH];
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+        const int e = lane + 32 * t;
+        kk[t] = e < n_e ? a.k[e] : T(0);
+        kl[t] = e < n_e ? a.klo[e] : T(0);
+        k3[t] = e < n_e ? a.k3[e] : T(0);
+        k3n[t] = e + 1 < n_e ? a.k3[e + 1] : T(0);
+        jfac[t] = e + 1 < n_e ? a.jfac[e] : T(0);
+    }
+    unsigned long long cnt_d = 0, cnt_r = 0;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(a.work_counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= 2 * a.n_cells) break;
+        const bool is_rand = item >= a.n_cells;
+        const CellList<T> &pl = is_rand ? a.rand : a.data;
+        const int c = is_rand ? item - a.n_cells : item;
+        const int p0 = pl.cell_start[c], p1 = pl.cell_start[c + 1];
+        const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
+        for (int p = p0; p < p1; ++p) {
+            const T px = pl.x[p], py = pl.y[p], pz = pl.z[p];
+            const T sp = is_rand ? a.rand_weight : T(pl.w[p]);
+            const int self = is_rand ? -1 : p;
+            T E[NCH][HIP_NLM];
+#pragma unroll
+            for (int t = 0; t < NCH; ++t)
+#pragma unroll
+                for (int i = 0; i < HIP_NLM; ++i) E[t][i] = T(0);
+            int qn = 0;
+            for (int s = 0; s < 27; ++s) {
+                const int dx = s / 9 - 1, dy = (s / 3) % 3 - 1, dz = s % 3 - 1;
+                const int nb = (((cx + dx + n_c) % n_c) * n_c + (cy + dy + n_c) % n_c) * n_c + (cz + dz + n_c) % n_c;
+                const int b0 = a.data.cell_start[nb], b1 = a.data.cell_start[nb + 1];
+                const T ox = px - T(dx) * a.data.cs, oy = py - T(dy) * a.data.cs, oz = pz - T(dz) * a.data.cs;
+                for (int jb = b0; jb < b1; jb += 32) {
+                    const int j = jb + lane;
+                    bool ok = false;
+                    T ddx = T(0), ddy = T(0), ddz = T(0), r2 = T(0);
+                    if (j < b1) {
+                        ddx = ox - a.data.x[j];
+                        ddy = oy - a.data.y[j];
+                        ddz = oz - a.data.z[j];
+                        r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        ok = (r2 < R0sq) && (r2 > T(0)) && (j != self);
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, ok);
+                    if (ok) {
+                        const T r = hip_sqrt_b(r2);
+                        const T ir = T(1) / r;
+                        const T W = hip_W<T>(r * invR0);
+                        const T wj = T(a.data.w[j]);
+                        const int slot = qn + __popc(m & lt_mask);
+                        T R[HIP_NLM];
+                        hip_real_ylm<T>(ddx * ir, ddy * ir, ddz * ir, R);
+                        sm.qr[slot] = r;
+                        sm.qw[slot] = wj * W;
+                        sm.qpsi[slot] = wj * wj * W * W;
+#pragma unroll
+                        for (int i = 0; i < HIP_NLM; ++i) sm.qy[i][slot] = R[i];
+                    }
+                    const int nq = __popc(m);
+                    if (is_rand)
+                        cnt_r += nq;
+                    else
+                        cnt_d += nq;
+                    qn += nq;
+                    if (qn >= HIP_BQ) {
+                        // drain the first HIP_BQ entries, move the rest (< 32) down
+                        __syncwarp();
+                        hip_bdrain<T, NCH, NKMAX>(sm, HIP_BQ, kk, kl, k3, k3n, jfac, lane, n_e, E);
+                        __syncwarp();
+                        hip_cterm<T, NKMAX>(sm, HIP_BQ, nk, sp, lane, Tc);
+                        const int rest = qn - HIP_BQ;
+                        T mv[3] = {T(0), T(0), T(0)};
+                        if (lane < rest) {
+                            mv[0] = sm.qr[HIP_BQ + lane];
+                            mv[1] = sm.qw[HIP_BQ + lane];
+                            mv[2] = sm.qpsi[HIP_BQ + lane];
+                        }
+                        T my[HIP_NLM];
+#pragma unroll
+                        for (int i = 0; i < HIP_NLM; ++i) my[i] = lane < rest ? sm.qy[i][HIP_BQ + lane] : T(0);
+                        __syncwarp();
+                        if (lane < rest) {
+                            sm.qr[lane] = mv[0];
+                            sm.qw[lane] = mv[1];
+                            sm.qpsi[lane] = mv[2];
+#pragma unroll
+                            for (int i = 0; i < HIP_NLM; ++i) sm.qy[i][lane] = my[i];
+                        }
+                        qn = rest;
+                        __syncwarp();
+                    }
+                }
+            }
+            if (qn > 0) {
+                __syncwarp();
+                hip_bdrain<T, NCH, NKMAX>(sm, qn, kk, kl, k3, k3n, jfac, lane, n_e, E);
+                __syncwarp();
+                hip_cterm<T, NKMAX>(sm, qn, nk, sp, lane, Tc);
+                qn = 0;
+            }
+            // edge sums -> A^a_lm = jfac_a (k_{a+1}^3 E_{a+1} - k_a^3 E_a)
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                const int e = lane + 32 * t;
+                if (e < n_e)
+#pragma unroll
+                    for (int i = 0; i < HIP_NLM; ++i) sm.X[e][i] = k3[t] * E[t][i];
+            }
+            __syncwarp();
+            T Aa[NCH][HIP_NLM];
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                const int e = lane + 32 * t;
+#pragma unroll
+                for (int i = 0; i < HIP_NLM; ++i) Aa[t][i] = e < nk ? jfac[t] * (sm.X[e + 1][i] - sm.X[e][i]) : T(0);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                const int e = lane + 32 * t;
+                if (e < nk)
+#pragma unroll
+                    for (int i = 0; i < HIP_NLM; ++i) sm.X[e][i] = Aa[t][i];
+            }
+            __syncwarp();
+            // contraction: Tc[l][a][b] += s_p sum_m A^a_lm A^b_lm  (lane owns rows a)
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                const int aa = lane + 32 * t;
+                if (aa < nk) {
+                    for (int b = 0; b < nk; ++b) {
+#pragma unroll
+                        for (int l = 0; l <= HIP_LMAX; ++l) {
+                            T d = T(0);
+#pragma unroll
+                            for (int mm = -l; mm <= l; ++mm) d += Aa[t][l * l + l + mm] * sm.X[b][l * l + l + mm];
+                            atomicAdd(&Tc[(l * nk + aa) * nk + b], (float)(sp * d));
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    double *out = a.partials + (size_t)blockIdx.x * (HIP_LMAX + 1) * nk * nk;
+    for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) out[i] = (double)Tc[i];
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt_d += __shfl_xor_sync(0xffffffffu, cnt_d, o);
+        cnt_r += __shfl_xor_sync(0xffffffffu, cnt_r, o);
+    }
+    if (lane == 0) {
+        if (cnt_d) atomicAdd(a.npairs, cnt_d);
+        if (cnt_r) atomicAdd(a.npairs + 1, cnt_r);
+    }
+}
+
+template <typename T, int NCH, int NKMAX>
+static cudaError_t launch_bispec(const BispecArgs<T> &a, int *grid_out, cudaStream_t st)
+{
+    const int nk = a.n_e - 1;
+    const size_t dyn = sizeof(float) * (HIP_LMAX + 1) * nk * nk;
+    cudaError_t e = cudaFuncSetAttribute(k_bispec<T, NCH, NKMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dyn);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bispec<T, NCH, NKMAX>, HIP_BTHREADS, dyn);
+    const int grid = sms * (nb < 1 ? 1 : nb);
+    *grid_out = grid;
+    k_bispec<T, NCH, NKMAX><<<grid, HIP_BTHREADS, dyn, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t hip_bispec_pairs(const BispecArgs<T> &a, int *grid_out, cudaStream_t st)
+{
+    const int nk = a.n_e - 1;
+    if (nk <= 31) return launch_bispec<T, 1, 32>(a, grid_out, st);
+    if (sizeof(T) == 4 && nk <= 63) return launch_bispec<T, 2, 64>(a, grid_out, st);
+    return cudaErrorInvalidValue;
+}
+template cudaError_t hip_bispec_pairs<float>(const BispecArgs<float> &, int *, cudaStream_t);
+template cudaError_t hip_bispec_pairs<double>(const BispecArgs<double> &, int *, cudaStream_t);
+
+// B^ab_l = (-1)^l (2l+1) T^ab_l / (V n_w^3)
+//          - delta_l0 (W~^a S^b + W~^b S^a) / (V n_w^2) + 2 delta_l0 W~^a W~^b   (Sec. 4.5)
+__global__ void k_bispec_final(const double *__restrict__ partials, int nparts, int nk, int lmax, double L,
+                               const double *S1, const double *S, const double *Wt, double *B)
+{
+    const int tot = (lmax + 1) * nk * nk;
+    const double V = L * L * L, nw = S1[0] / V;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int p = 0; p < nparts; ++p) t += partials[(size_t)p * (HIP_LMAX + 1) * nk * nk + i];
+        const int l = i / (nk * nk), ab = i - l * nk * nk, aa = ab / nk, bb = ab - aa * nk;
+        double b = ((l & 1) ? -1.0 : 1.0) * (2.0 * l + 1.0) * t / (V * nw * nw * nw);
+        if (l == 0) b += -(Wt[aa] * S[bb] + Wt[bb] * S[aa]) / (V * nw * nw) + 2.0 * Wt[aa] * Wt[bb];
+        B[i] = b;
+    }
+}
+
+cudaError_t hip_bispec_finalize(const double *partials, int nparts, int nk, int lmax, double L, const double *S1,
+                                const double *S, const double *Wt, double *B, cudaStream_t st)
+{
+    const int tot = (lmax + 1) * nk * nk;
+    k_bispec_final<<<(tot + 255) / 256, 256, 0, st>>>(partials, nparts, nk, lmax, L, S1, S, Wt, B);
+    return cudaGetLastError();
 }

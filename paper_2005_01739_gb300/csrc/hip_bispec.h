@@ -1,0 +1,28 @@
+// Internal interface of the bispectrum kernels (hip_bispec.cu).
+#pragma once
+
+#include "hip_internal.h"
+
+#define HIP_BMAXE 65  // bin edges supported by the bispectrum kernels (64 bins)
+
+template <typename T>
+struct BispecArgs {
+    CellList<T> data;        // neighbours (and data primaries)
+    CellList<T> rand;        // random primaries (same cell grid)
+    int n_cells;             // cells per catalog (n_c^3)
+    int n_e;                 // bin edges = n_k + 1
+    T R0;
+    T rand_weight;           // -S1 / N_r
+    int *work_counter;
+    double *partials;        // [gridDim.x][5][n_k][n_k]
+    unsigned long long *npairs;  // [0] data-primary pairs, [1] random-primary pairs
+    T k[HIP_BMAXE], klo[HIP_BMAXE], k3[HIP_BMAXE], jfac[HIP_BMAXE];
+};
+
+template <typename T>
+cudaError_t hip_bispec_pairs(const BispecArgs<T> &a, int *grid_out, cudaStream_t st);
+
+// B^ab_l from the summed T partials, S^a (ordered DD_0 sum of the power kernel)
+// and W~^a (Sec. 4.5 summary), all in FP64 on the device.
+cudaError_t hip_bispec_finalize(const double *partials, int nparts, int nk, int lmax, double L, const double *S1,
+                                const double *S, const double *Wt, double *B, cudaStream_t st);
