@@ -79,6 +79,35 @@ hip_status hip_power(const float *pos, const float *w, int64_t N, double L, doub
                      int64_t prim_begin, int64_t prim_end, double *P_out, double *DD_out, int64_t *npairs_out,
                      void *cuda_stream);
 
+/* Isotropic bispectrum multipoles of a periodic box, Sec. 4 of the paper (the
+ * summary estimator of Sec. 4.5):
+ *
+ *   B^ab_l = (-1)^l (2l+1) / (V n_w^3) * T^ab_l
+ *            - delta_l0 (W~^a S^b + W~^b S^a) / (V n_w^2) + 2 delta_l0 W~^a W~^b,
+ *   T^ab_l = sum_{i data} w_i G^ab_l(x_i) - (S1/N_r) sum_{r random} G^ab_l(x_r),
+ *   G^ab_l(x) = 4pi/(2l+1) sum_m A^a_lm(x) A^b*_lm(x) - C^ab_l(x),
+ *   A^a_lm(x) = sum_j w_j jbar^a_l(r) W(r/R0) Y_lm(rhat),  C^ab_l(x) = sum_j w_j^2 jbar^a_l jbar^b_l W^2,
+ *
+ * over data j with 0 < r = |x - x_j| < R0 (minimum image; j != i for a data
+ * primary), Eq. AC-def binned as in Sec. 4.4; S^a = the ordered DD_0 pair sum of
+ * hip_power (the DDR^I term, Sec. 4.3); the DDR^II term uses the random
+ * catalog (f_rand = N_r / N); S1 = sum of data weights, n_w = S1 / L^3.
+ *
+ *   pos, w, N        data as in hip_power (w NULL = unit weights)
+ *   rand_pos, N_r    [N_r][3] float32 uniform random positions (host or device), N_r >= 1
+ *   L, R0, window    as in hip_power
+ *   k_edges, n_k     as in hip_power, n_k <= 63 (MIXED) or <= 31 (FP64)
+ *   lmax             0..4; multipoles l = 0..lmax are returned
+ *   prec             HIP_PREC_FP64 or HIP_PREC_MIXED
+ *   B_out            [(lmax+1) * n_k * n_k] float64 host, row-major (l, a, b); symmetric in a, b
+ *   npairs_out       [2] or NULL: ordered (primary, data) pairs counted for data and
+ *                    for random primaries
+ *   cuda_stream      as in hip_power
+ */
+hip_status hip_bispectrum(const float *pos, const float *w, int64_t N, const float *rand_pos, int64_t N_r, double L,
+                          double R0, hip_window window, const double *k_edges, int n_k, int lmax, hip_precision prec,
+                          double *B_out, int64_t *npairs_out, void *cuda_stream);
+
 /* Stage timing of the most recent hip_power call on this process, for
  * measurement.  When enabled (on != 0), each call records CUDA events on its
  * stream around its stages; hip_stage_times then writes, in milliseconds,

@@ -49,6 +49,8 @@ def load(path: str | None = None):
         i64, d, i, P = ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p
         L.hip_power.restype = i
         L.hip_power.argtypes = [P, P, i64, d, d, i, P, i, i, i, i, i64, i64, P, P, P, P]
+        L.hip_bispectrum.restype = i
+        L.hip_bispectrum.argtypes = [P, P, i64, P, i64, d, d, i, P, i, i, i, P, P, P]
         L.hip_status_string.restype = ctypes.c_char_p
         L.hip_status_string.argtypes = [i]
         L.hip_last_error.restype = ctypes.c_char_p
@@ -115,6 +117,28 @@ def hip_power(pos, w, L, R0, k_edges, ell_max=4, los_axis=2, prec="mixed", prim_
     _check(lib, rc, "hip_power")
     del keep_p, keep_w
     return P, DD, int(npairs.value)
+
+
+def hip_bispectrum(pos, w, rand_pos, L, R0, k_edges, lmax=4, prec="mixed", stream=None):
+    """B^ab_l (Sec. 4.5 summary estimator) of one periodic catalog with a random
+    catalog for the DDR^II term.  Returns (B [lmax+1, n_k, n_k], (pairs from data
+    primaries, pairs from random primaries))."""
+    lib = load()
+    n = int(pos.shape[0]) if hasattr(pos, "shape") else len(pos)
+    nr = int(rand_pos.shape[0]) if hasattr(rand_pos, "shape") else len(rand_pos)
+    pp, keep_p = _ptr(pos)
+    wp, keep_w = _ptr(w)
+    rp, keep_r = _ptr(rand_pos)
+    edges = np.ascontiguousarray(np.asarray(k_edges, dtype=np.float64))
+    n_k = len(edges) - 1
+    B = np.zeros((lmax + 1, n_k, n_k))
+    npairs = (ctypes.c_int64 * 2)()
+    rc = lib.hip_bispectrum(pp, wp, n, rp, nr, float(L), float(R0), 0, edges.ctypes.data_as(ctypes.c_void_p), n_k,
+                            int(lmax), PREC[prec], B.ctypes.data_as(ctypes.c_void_p), npairs,
+                            _stream_handle(stream))
+    _check(lib, rc, "hip_bispectrum")
+    del keep_p, keep_w, keep_r
+    return B, (int(npairs[0]), int(npairs[1]))
 
 
 def debug_F(prec: str, l: int, u: float) -> float:

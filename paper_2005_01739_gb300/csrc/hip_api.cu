@@ -6,6 +6,7 @@
 #include <mutex>
 #include <vector>
 
+#include "hip_bispec.h"
 #include "hip_internal.h"
 #include "hip_workspace.h"
 
@@ -297,6 +298,160 @@ extern "C" hip_status hip_power(const float *pos, const float *w, int64_t N, dou
                                  DD_out, npairs_out, st, dev);
     return power_impl<double>(pos, w, N, L, R0, k_edges, n_k, ell_max, los_axis, prim_begin, prim_end, P_out,
                               DD_out, npairs_out, st, dev);
+}
+
+// --------------------------------------------------------- hip_bispectrum ----
+template <typename T>
+static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const float *rpos, int64_t N_r, double L,
+                              double R0, const double *k_edges, int n_k, int lmax, double *B_out,
+                              int64_t *npairs_out, cudaStream_t st, int dev)
+{
+    Workspace &ws = hip_workspace(dev);
+    const int n_c = hip_cells_per_side(L, R0);
+    const int n_cells = n_c * n_c * n_c;
+    const int n_e = n_k + 1;
+    const int pgrid = hip_power_grid<T>();
+    const bool dpos = hip_is_device_ptr(pos), dw = w && hip_is_device_ptr(w), drp = hip_is_device_ptr(rpos);
+    const int bparts_max = 152 * 8;  // upper bound on the bispectrum grid
+    const size_t tsz = (size_t)(HIP_LMAX + 1) * n_k * n_k;
+
+    Carve cv;
+    const size_t o_pos = dpos ? 0 : cv.take(sizeof(float) * 3 * N);
+    const size_t o_w = (w && !dw) ? cv.take(sizeof(float) * N) : 0;
+    const size_t o_rp = drp ? 0 : cv.take(sizeof(float) * 3 * N_r);
+    const size_t o_dx = cv.take(sizeof(T) * N), o_dy = cv.take(sizeof(T) * N), o_dz = cv.take(sizeof(T) * N);
+    const size_t o_dw = cv.take(sizeof(float) * N), o_didx = cv.take(sizeof(int) * N), o_dcid = cv.take(sizeof(int) * N);
+    const size_t o_rx = cv.take(sizeof(T) * N_r), o_ry = cv.take(sizeof(T) * N_r), o_rz = cv.take(sizeof(T) * N_r);
+    const size_t o_rw = cv.take(sizeof(float) * N_r), o_ridx = cv.take(sizeof(int) * N_r);
+    const size_t o_rcid = cv.take(sizeof(int) * N_r);
+    const size_t o_ds = cv.take(sizeof(int) * (n_cells + 1)), o_df = cv.take(sizeof(int) * n_cells);
+    const size_t o_rs = cv.take(sizeof(int) * (n_cells + 1)), o_rf = cv.take(sizeof(int) * n_cells);
+    const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * n_e);
+    const size_t o_bp = cv.take(sizeof(double) * bparts_max * tsz);
+    const size_t o_small = cv.take(sizeof(double) * 16);
+    const size_t o_wt = cv.take(sizeof(double) * n_k), o_dd = cv.take(sizeof(double) * 3 * n_k);
+    const size_t o_p = cv.take(sizeof(double) * 3 * n_k), o_b = cv.take(sizeof(double) * tsz);
+    hip_status hs = ws.reserve(cv.total, st);
+    if (hs != HIP_OK) return hs;
+    char *b = (char *)ws.base;
+    cudaError_t e;
+#define HIP_CK(call, what)                                                                                           \
+    do {                                                                                                             \
+        if ((e = (call)) != cudaSuccess) {                                                                           \
+            set_err(what, e);                                                                                        \
+            return HIP_ERR_CUDA;                                                                                     \
+        }                                                                                                            \
+    } while (0)
+    const float *dposp = pos, *dwp = w, *drpp = rpos;
+    if (!dpos) {
+        HIP_CK(cudaMemcpyAsync(b + o_pos, pos, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st), "H2D positions");
+        dposp = (const float *)(b + o_pos);
+    }
+    if (w && !dw) {
+        HIP_CK(cudaMemcpyAsync(b + o_w, w, sizeof(float) * N, cudaMemcpyHostToDevice, st), "H2D weights");
+        dwp = (const float *)(b + o_w);
+    }
+    if (!drp) {
+        HIP_CK(cudaMemcpyAsync(b + o_rp, rpos, sizeof(float) * 3 * N_r, cudaMemcpyHostToDevice, st), "H2D randoms");
+        drpp = (const float *)(b + o_rp);
+    }
+    double *small = (double *)(b + o_small);
+    double *S1 = small, *S1r = small + 1;
+    unsigned long long *npairs = (unsigned long long *)(small + 2);  // [2]: P pass; [3], [4]: B pass
+    int *err = (int *)(small + 5), *errr = err + 1;
+    int *counter = (int *)(small + 6), *bcounter = counter + 1;
+    T *dx = (T *)(b + o_dx), *dy = (T *)(b + o_dy), *dz = (T *)(b + o_dz);
+    T *rx = (T *)(b + o_rx), *ry = (T *)(b + o_ry), *rz = (T *)(b + o_rz);
+    int *dstart = (int *)(b + o_ds), *rstart = (int *)(b + o_rs);
+    HIP_CK(hip_build_cells<T>(dposp, dwp, N, L, n_c, dx, dy, dz, (float *)(b + o_dw), (int *)(b + o_didx),
+                              (int *)(b + o_dcid), dstart, (int *)(b + o_df), S1, err, st),
+           "cell build (data)");
+    HIP_CK(hip_build_cells<T>(drpp, nullptr, N_r, L, n_c, rx, ry, rz, (float *)(b + o_rw), (int *)(b + o_ridx),
+                              (int *)(b + o_rcid), rstart, (int *)(b + o_rf), S1r, errr, st),
+           "cell build (randoms)");
+    int herr[2] = {0, 0};
+    double hS1 = 0.0;
+    HIP_CK(cudaMemcpyAsync(herr, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "D2H error word");
+    HIP_CK(cudaMemcpyAsync(&hS1, S1, sizeof(double), cudaMemcpyDeviceToHost, st), "D2H S1");
+    HIP_CK(cudaStreamSynchronize(st), "cell build sync");
+    if (herr[0] || herr[1]) return HIP_ERR_NONFINITE;
+
+    // S^a: ordered DD_0 pair sum over all data (the power pass with l = 0 only)
+    CellList<T> dcl{dx, dy, dz, (const float *)(b + o_dw), (const int *)(b + o_didx), dstart, n_c, (T)(L / n_c)};
+    CellList<T> rcl{rx, ry, rz, (const float *)(b + o_rw), (const int *)(b + o_ridx), rstart, n_c, (T)(L / n_c)};
+    HIP_CK(cudaMemsetAsync(npairs, 0, 3 * sizeof(unsigned long long), st), "memset");
+    HIP_CK(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st), "memset");
+    PowerKernelArgs ka;
+    ka.n_e = n_e;
+    ka.los = 2;
+    ka.p0 = 0;
+    ka.p1 = N;
+    ka.n_items = n_cells * HIP_NSHIFT;
+    ka.work_counter = counter;
+    ka.partials = (double *)(b + o_pp);
+    ka.npairs = npairs;
+    HIP_CK(hip_power_pairs<T>(dcl, ka, k_edges, 1, R0, pgrid, st), "pair kernel (S)");
+    double *Wt = (double *)(b + o_wt), *DD = (double *)(b + o_dd), *P = (double *)(b + o_p);
+    HIP_CK(hip_power_finalize(ka.partials, pgrid, n_e, 1, k_edges, R0, L, S1, Wt, DD, P, st), "finalize (S)");
+
+    BispecArgs<T> ba;
+    ba.data = dcl;
+    ba.rand = rcl;
+    ba.n_cells = n_cells;
+    ba.n_e = n_e;
+    ba.R0 = (T)R0;
+    ba.rand_weight = (T)(-hS1 / (double)N_r);
+    ba.work_counter = bcounter;
+    ba.partials = (double *)(b + o_bp);
+    ba.npairs = npairs + 1;
+    for (int q = 0; q < HIP_BMAXE; ++q) {
+        const double k = q < n_e ? k_edges[q] : 0.0;
+        ba.k[q] = (T)k;
+        ba.klo[q] = (T)(k - (double)ba.k[q]);
+        ba.k3[q] = (T)(k * k * k);
+        ba.jfac[q] = q + 1 < n_e ? (T)(3.0 / (k_edges[q + 1] * k_edges[q + 1] * k_edges[q + 1] - k * k * k)) : T(0);
+    }
+    int bgrid = 0;
+    HIP_CK(hip_bispec_pairs<T>(ba, bparts_max, &bgrid, st), "bispectrum kernel");
+    double *B = (double *)(b + o_b);
+    HIP_CK(hip_bispec_finalize(ba.partials, bgrid, n_k, lmax, L, S1, DD, Wt, B, st), "bispectrum finalize");
+    const size_t nout = (size_t)(lmax + 1) * n_k * n_k;
+    std::vector<double> hB(nout);
+    unsigned long long hn[3] = {0, 0, 0};
+    HIP_CK(cudaMemcpyAsync(hB.data(), B, sizeof(double) * nout, cudaMemcpyDeviceToHost, st), "D2H B");
+    HIP_CK(cudaMemcpyAsync(hn, npairs, sizeof(hn), cudaMemcpyDeviceToHost, st), "D2H npairs");
+    HIP_CK(cudaStreamSynchronize(st), "stream sync");
+#undef HIP_CK
+    std::memcpy(B_out, hB.data(), sizeof(double) * nout);
+    if (npairs_out) {
+        npairs_out[0] = (int64_t)hn[1];
+        npairs_out[1] = (int64_t)hn[2];
+    }
+    return HIP_OK;
+}
+
+extern "C" hip_status hip_bispectrum(const float *pos, const float *w, int64_t N, const float *rand_pos, int64_t N_r,
+                                     double L, double R0, hip_window window, const double *k_edges, int n_k,
+                                     int lmax, hip_precision prec, double *B_out, int64_t *npairs_out,
+                                     void *cuda_stream)
+{
+    g_errbuf[0] = 0;
+    if (!pos || !rand_pos || !B_out) return HIP_ERR_ARG;
+    if (N < 1 || N > 2000000000LL || N_r < 1 || N_r > 2000000000LL) return HIP_ERR_ARG;
+    if (window != HIP_WINDOW_PHILCOX) return HIP_ERR_ARG;
+    if (prec != HIP_PREC_FP64 && prec != HIP_PREC_MIXED) return HIP_ERR_ARG;
+    if (lmax < 0 || lmax > HIP_LMAX) return HIP_ERR_ARG;
+    if (!(L > 0.0) || !std::isfinite(L) || !(R0 > 0.0) || !(R0 < 0.5 * L)) return HIP_ERR_RANGE;
+    hip_status hs = hip_check_edges(k_edges, n_k);
+    if (hs != HIP_OK) return hs;
+    if (n_k > (prec == HIP_PREC_MIXED ? HIP_BMAXE - 2 : 31)) return HIP_ERR_RANGE;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    int dev = 0;
+    if ((hs = hip_device_setup(&dev)) != HIP_OK) return hs;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (prec == HIP_PREC_MIXED)
+        return bispec_impl<float>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, lmax, B_out, npairs_out, st, dev);
+    return bispec_impl<double>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, lmax, B_out, npairs_out, st, dev);
 }
 
 // ------------------------------------------------------ host self-checks -----

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
 }
 
 template <typename T, int NCH, int NKMAX>
-static cudaError_t launch_bispec(const BispecArgs<T> &a, int *grid_out, cudaStream_t st)
+static cudaError_t launch_bispec(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st)
 {
     const int nk = a.n_e - 1;
     const size_t dyn = sizeof(float) * (HIP_LMAX + 1) * nk * nk;
@@ -362,22 +362,25 @@ static cudaError_t launch_bispec(const BispecArgs<T> &a, int *grid_out, cudaStre
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bispec<T, NCH, NKMAX>, HIP_BTHREADS, dyn);
-    const int grid = sms * (nb < 1 ? 1 : nb);
+    int grid = sms * (nb < 1 ? 1 : nb);
+    if (grid > max_grid) grid = max_grid;
     *grid_out = grid;
     k_bispec<T, NCH, NKMAX><<<grid, HIP_BTHREADS, dyn, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t hip_bispec_pairs(const BispecArgs<T> &a, int *grid_out, cudaStream_t st)
+cudaError_t hip_bispec_pairs(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st)
 {
     const int nk = a.n_e - 1;
-    if (nk <= 31) return launch_bispec<T, 1, 32>(a, grid_out, st);
-    if (sizeof(T) == 4 && nk <= 63) return launch_bispec<T, 2, 64>(a, grid_out, st);
+    if (nk <= 31) return launch_bispec<T, 1, 32>(a, max_grid, grid_out, st);
+    if constexpr (sizeof(T) == 4) {
+        if (nk <= 63) return launch_bispec<T, 2, 64>(a, max_grid, grid_out, st);
+    }
     return cudaErrorInvalidValue;
 }
-template cudaError_t hip_bispec_pairs<float>(const BispecArgs<float> &, int *, cudaStream_t);
-template cudaError_t hip_bispec_pairs<double>(const BispecArgs<double> &, int *, cudaStream_t);
+template cudaError_t hip_bispec_pairs<float>(const BispecArgs<float> &, int, int *, cudaStream_t);
+template cudaError_t hip_bispec_pairs<double>(const BispecArgs<double> &, int, int *, cudaStream_t);
 
 // B^ab_l = (-1)^l (2l+1) T^ab_l / (V n_w^3)
 //          - delta_l0 (W~^a S^b + W~^b S^a) / (V n_w^2) + 2 delta_l0 W~^a W~^b   (Sec. 4.5)

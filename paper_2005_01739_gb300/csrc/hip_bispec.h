@@ -20,7 +20,7 @@ struct BispecArgs {
 };
 
 template <typename T>
-cudaError_t hip_bispec_pairs(const BispecArgs<T> &a, int *grid_out, cudaStream_t st);
+cudaError_t hip_bispec_pairs(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st);
 
 // B^ab_l from the summed T partials, S^a (ordered DD_0 sum of the power kernel)
 // and W~^a (Sec. 4.5 summary), all in FP64 on the device.
