@@ -164,14 +164,14 @@ __device__ __forceinline__ void hip_bdrain(BWarpSmem<T, NKMAX> &sm, int n, const
 
 // Tc[l][a][b] -= s_p sum_q psi_q J[l][q][a] J[l][q][b]  (the C term).
 template <typename T, int NKMAX>
-__device__ __forceinline__ void hip_cterm(const BWarpSmem<T, NKMAX> &sm, int n, int nk, T sp, int lane, float *Tc)
+__device__ __forceinline__ void hip_cterm(const BWarpSmem<T, NKMAX> &sm, int n, int nk, T sp, int lane, T *Tc)
 {
     const int per_l = nk * nk;
     for (int i = lane; i < (HIP_LMAX + 1) * per_l; i += 32) {
         const int l = i / per_l, ab = i - l * per_l, a = ab / nk, b = ab - a * nk;
         T acc = T(0);
         for (int q = 0; q < n; ++q) acc += sm.qpsi[q] * sm.J[l][q][a] * sm.J[l][q][b];
-        atomicAdd(&Tc[i], (float)(-sp * acc));
+        atomicAdd(&Tc[i], -sp * acc);
     }
 }
 
@@ -179,13 +179,14 @@ template <typename T, int NCH, int NKMAX>
 __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
 {
     __shared__ BWarpSmem<T, NKMAX> smem[HIP_BWARPS];
-    extern __shared__ float Tc[];  // [5][nk][nk] CTA accumulator
+    extern __shared__ __align__(16) unsigned char tc_raw[];
+    T *Tc = reinterpret_cast<T *>(tc_raw);  // [5][nk][nk] CTA accumulator
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BWarpSmem<T, NKMAX> &sm = smem[warp];
     const int n_e = a.n_e, nk = n_e - 1, n_c = a.data.n_c;
     const unsigned lt_mask = (1u << lane) - 1u;
     const T R0sq = a.R0 * a.R0, invR0 = T(1) / a.R0;
-    for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) Tc[i] = 0.f;
+    for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) Tc[i] = T(0);
     __syncthreads();
 
     T kk[NCH], kl[NCH], k3[NCH], k3n[NCH], jfac[NCH];
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
                     else
                         cnt_d += nq;
                     qn += nq;
-                    if (qn >= HIP_BQ) {
+                    while (qn >= HIP_BQ) {
                         // drain the first HIP_BQ entries, move the rest (< 32) down
                         __syncwarp();
                         hip_bdrain<T, NCH, NKMAX>(sm, HIP_BQ, kk, kl, k3, k3n, jfac, lane, n_e, E);
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
                             T d = T(0);
 #pragma unroll
                             for (int mm = -l; mm <= l; ++mm) d += Aa[t][l * l + l + mm] * sm.X[b][l * l + l + mm];
-                            atomicAdd(&Tc[(l * nk + aa) * nk + b], (float)(sp * d));
+                            atomicAdd(&Tc[(l * nk + aa) * nk + b], sp * d);
                         }
                     }
                 }
@@ -340,10 +341,7 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
     __syncthreads();
     double *out = a.partials + (size_t)blockIdx.x * (HIP_LMAX + 1) * nk * nk;
     for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) out[i] = (double)Tc[i];
-    for (int o = 16; o > 0; o >>= 1) {
-        cnt_d += __shfl_xor_sync(0xffffffffu, cnt_d, o);
-        cnt_r += __shfl_xor_sync(0xffffffffu, cnt_r, o);
-    }
+    // cnt_d, cnt_r are warp-uniform (every lane added each ballot's count)
     if (lane == 0) {
         if (cnt_d) atomicAdd(a.npairs, cnt_d);
         if (cnt_r) atomicAdd(a.npairs + 1, cnt_r);
@@ -354,7 +352,7 @@ template <typename T, int NCH, int NKMAX>
 static cudaError_t launch_bispec(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st)
 {
     const int nk = a.n_e - 1;
-    const size_t dyn = sizeof(float) * (HIP_LMAX + 1) * nk * nk;
+    const size_t dyn = sizeof(T) * (HIP_LMAX + 1) * nk * nk;
     cudaError_t e = cudaFuncSetAttribute(k_bispec<T, NCH, NKMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)dyn);
     if (e != cudaSuccess) return e;
