@@ -18,6 +18,7 @@
 #ifndef HIPSTER_GB300_H
 #define HIPSTER_GB300_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -107,6 +108,33 @@ hip_status hip_power(const float *pos, const float *w, int64_t N, double L, doub
 hip_status hip_bispectrum(const float *pos, const float *w, int64_t N, const float *rand_pos, int64_t N_r, double L,
                           double R0, hip_window window, const double *k_edges, int n_k, int lmax, hip_precision prec,
                           double *B_out, int64_t *npairs_out, void *cuda_stream);
+
+/* hip_power without any device allocation (no counterpart in the paper: this is
+ * a property of the library, not of the estimator).
+ *
+ * Same arguments, results and errors as hip_power with prec = HIP_PREC_MIXED,
+ * but all scratch lives in one statically sized device array of
+ * hip_noalloc_capacity() bytes (64 MiB) that every device loading the library
+ * reserves until the process exits; no cudaMalloc/cudaFree or other allocating
+ * routine is called.  It is for callers that cannot allocate device memory
+ * while they run: work recorded into CUDA graphs, hosts whose own memory pool
+ * owns the device, loops that cannot afford the device-wide synchronisation of
+ * cudaMalloc/cudaFree.
+ *
+ * Limit: the call needs about 24 bytes per particle for device-resident inputs
+ * (40 for host inputs), plus cell tables and per-CTA partial sums; a call that
+ * would not fit returns HIP_ERR_RANGE and hip_noalloc_message() says how many
+ * bytes it needed.  The array's device address is looked up on the first call
+ * made with each device current: make that first call before any stream
+ * capture.  Every call shares the array (it keeps the previous call's
+ * contents; each call clears what must start at zero); calls must not overlap
+ * on the GPU, and this entry point serialises them and synchronises
+ * `cuda_stream` before returning. */
+hip_status hip_power_noalloc(const float *pos, const float *w, int64_t N, double L, double R0, hip_window window,
+                             const double *k_edges, int n_k, int ell_max, int los_axis, int64_t prim_begin,
+                             int64_t prim_end, double *P_out, double *DD_out, int64_t *npairs_out, void *cuda_stream);
+size_t hip_noalloc_capacity(void);
+const char *hip_noalloc_message(void);
 
 /* Stage timing of the most recent hip_power call on this process, for
  * measurement.  When enabled (on != 0), each call records CUDA events on its

@@ -51,6 +51,12 @@ def load(path: str | None = None):
         L.hip_power.argtypes = [P, P, i64, d, d, i, P, i, i, i, i, i64, i64, P, P, P, P]
         L.hip_bispectrum.restype = i
         L.hip_bispectrum.argtypes = [P, P, i64, P, i64, d, d, i, P, i, i, i, P, P, P]
+        L.hip_power_noalloc.restype = i
+        L.hip_power_noalloc.argtypes = [P, P, i64, d, d, i, P, i, i, i, i64, i64, P, P, P, P]
+        L.hip_noalloc_capacity.restype = ctypes.c_size_t
+        L.hip_noalloc_capacity.argtypes = []
+        L.hip_noalloc_message.restype = ctypes.c_char_p
+        L.hip_noalloc_message.argtypes = []
         L.hip_status_string.restype = ctypes.c_char_p
         L.hip_status_string.argtypes = [i]
         L.hip_last_error.restype = ctypes.c_char_p
@@ -115,6 +121,30 @@ def hip_power(pos, w, L, R0, k_edges, ell_max=4, los_axis=2, prec="mixed", prim_
                        int(ell_max), int(los_axis), PREC[prec], p0, p1, P.ctypes.data_as(ctypes.c_void_p),
                        DD.ctypes.data_as(ctypes.c_void_p), ctypes.byref(npairs), _stream_handle(stream))
     _check(lib, rc, "hip_power")
+    del keep_p, keep_w
+    return P, DD, int(npairs.value)
+
+
+def hip_power_noalloc(pos, w, L, R0, k_edges, ell_max=4, los_axis=2, prim_range=None, stream=None):
+    """hip_power (mixed precision) with its scratch in the library's static device
+    array instead of allocated memory.  Same returns as hip_power."""
+    lib = load()
+    n = int(pos.shape[0]) if hasattr(pos, "shape") else len(pos)
+    pp, keep_p = _ptr(pos)
+    wp, keep_w = _ptr(w)
+    edges = np.ascontiguousarray(np.asarray(k_edges, dtype=np.float64))
+    n_k = len(edges) - 1
+    n_ell = ell_max // 2 + 1
+    P = np.zeros((n_ell, n_k))
+    DD = np.zeros((n_ell, n_k))
+    npairs = ctypes.c_int64(0)
+    p0, p1 = (0, n) if prim_range is None else (int(prim_range[0]), int(prim_range[1]))
+    rc = lib.hip_power_noalloc(pp, wp, n, float(L), float(R0), 0, edges.ctypes.data_as(ctypes.c_void_p), n_k,
+                               int(ell_max), int(los_axis), p0, p1, P.ctypes.data_as(ctypes.c_void_p),
+                               DD.ctypes.data_as(ctypes.c_void_p), ctypes.byref(npairs), _stream_handle(stream))
+    if rc != HIP_OK:
+        raise HipError(rc, f"hip_power_noalloc: {lib.hip_status_string(rc).decode()} "
+                           f"({lib.hip_noalloc_message().decode()})")
     del keep_p, keep_w
     return P, DD, int(npairs.value)
 
