@@ -131,22 +131,62 @@ def _config(wl, nranks):
             "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas{nranks}"}
 
 
+def combine_ranks(ms: float, work: float, device: str):
+    """Whole-job timing over ranks: the slowest rank's time and the sum of the
+    work all ranks did (no data-path collective; one scalar each)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(work)
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    w = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def oracle_sample(wl, seconds: float):
     """Time the FP64 oracle on a primary subset sized for ~`seconds` of work."""
     import oracle
     pos = wl["pos"].astype(np.float64)
     w = wl["w"].astype(np.float64)
-    m = 64
+    m = 32
     while True:
         t0 = time.perf_counter()
         _, npairs = oracle.power_pair_sum(pos, w, wl["L"], wl["R0"], wl["edges"], 4, 2, primaries=np.arange(m))
         dt = time.perf_counter() - t0
-        if dt > 0.25 * seconds or m >= len(pos):
+        if dt > 0.5 * seconds or m >= len(pos):
             break
-        m = min(len(pos), int(m * max(2.0, 0.5 * seconds / max(dt, 1e-3))))
+        m = min(len(pos), max(2 * m, int(m * seconds / max(dt, 1e-3))))
     nk = len(wl["edges"]) - 1
     return {"value": npairs * nk / dt, "seconds": dt, "primaries": m, "ordered_pairs": npairs,
             "cores": oracle.num_threads()}
+
+
+def bispectrum_rate(binding, stream, reps: int = 2):
+    """B_l (l = 0..4) of the 5e5-particle workload with 1.5e6 randoms: ordered
+    (primary, data) pairs, random primaries included, times bins, per second."""
+    import torch
+    from paper_2005_01739_gb300 import catalogs
+    wl = catalogs.workload("bk_n5e5")
+    dpos = torch.from_numpy(wl["pos"]).cuda()
+    drnd = torch.from_numpy(wl["rand"]).cuda()
+    nk = len(wl["edges"]) - 1
+    with torch.cuda.stream(stream):
+        binding.hip_bispectrum(dpos, None, drnd, wl["L"], wl["R0"], wl["edges"], 4, "mixed", stream=stream)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            _, (nd, nr) = binding.hip_bispectrum(dpos, None, drnd, wl["L"], wl["R0"], wl["edges"], 4, "mixed",
+                                                 stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.mean(ts))
+    return {"workload": "bk_n5e5", "value": (nd + nr) * nk / (ms / 1e3), "unit": UNIT, "ms_per_call": ms,
+            "pairs_data_primaries": nd, "pairs_random_primaries": nr, "n_k": nk, "ell": [0, 1, 2, 3, 4]}
 
 
 def run_reference(args):
@@ -223,13 +263,8 @@ def run_ours(args):
     ms = float(np.mean(step_ms))
     pairs = npairs // 2  # unordered pairs with 0 < r < R0
     work = float(pairs) * nk
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    wsum = torch.tensor([work], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(wsum, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    value = float(wsum.item()) / (ms_max / 1e3)
+    ms_max, work_sum = combine_ranks(ms, work, "cuda")
+    value = work_sum / (ms_max / 1e3)
 
     # end to end through the public call with pinned host inputs (H2D and result D2H inside)
     hpos = torch.from_numpy(wl["pos"]).pin_memory()
@@ -241,10 +276,8 @@ def run_ours(args):
         binding.hip_power(hpos, hw, L, R0, edges, 4, 2, "mixed", stream=stream)
         e2e_t.append(time.perf_counter() - t0)
     e2e_ms = 1e3 * float(np.mean(e2e_t))
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = float(wsum.item()) / (float(te.item()) / 1e3)
+    e2e_max, _ = combine_ranks(e2e_ms, 0.0, "cuda")
+    e2e_value = work_sum / (e2e_max / 1e3)
     n = len(wl["pos"])
     h2d = 12 * n + 4 * n
     d2h = 2 * 3 * nk * 8 + 8 + 4
@@ -258,6 +291,10 @@ def run_ours(args):
         fp64_kernel_ms = float(st[2])
         fp64 = {"value": work / (float(sum(st[1:4])) / 1e3), "unit": UNIT, "pair_kernel_ms": fp64_kernel_ms,
                 "speedup_mixed_vs_fp64_kernel": fp64_kernel_ms / float(np.mean(pair_ms))}
+
+    bisp = None
+    if not args.skip_bispectrum:
+        bisp = bispectrum_rate(binding, stream)
 
     if rank != 0:
         if ws > 1:
@@ -273,7 +310,7 @@ def run_ours(args):
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": _config(wl, ws),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": float(te.item())},
+                "ms_per_step": e2e_max},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_power_pairs<float,4,21>",
                      "kernel_ms": kern_ms, "flops_per_pair_bin": FLOPS_PER_PAIR_BIN,
@@ -284,6 +321,7 @@ def run_ours(args):
         "stage_ms": dict(zip(["upload", "cells", "pairs", "finalize", "download"],
                              [float(x) for x in binding.stage_times()])),
         "fp64_plain": fp64,
+        "bispectrum": bisp,
     }
     if cpu:
         line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
@@ -302,9 +340,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-bispectrum", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the catalog volume at fixed density (profiler captures only)")
     args = ap.parse_args()
