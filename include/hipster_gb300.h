@@ -109,6 +109,49 @@ hip_status hip_bispectrum(const float *pos, const float *w, int64_t N, const flo
                           double R0, hip_window window, const double *k_edges, int n_k, int lmax, hip_precision prec,
                           double *B_out, int64_t *npairs_out, void *cuda_stream);
 
+/* One catalog of a batched power-spectrum computation: the arguments of
+ * hip_power for that catalog (host or device inputs; host outputs). */
+typedef struct {
+    const float *pos;    /* [N][3] float32 */
+    const float *w;      /* [N] float32 or NULL */
+    int64_t N;
+    double L, R0;
+    const double *k_edges; /* [n_k+1] host */
+    int n_k;
+    int ell_max, los_axis;
+    int64_t prim_begin, prim_end;
+    double *P_out;       /* [(ell_max/2+1) * n_k] host */
+    double *DD_out;      /* same shape or NULL */
+    int64_t *npairs_out; /* or NULL */
+} hip_catalog;
+
+typedef struct hip_batch_plan hip_batch_plan;
+
+/* Batched power spectra (the estimator of hip_power, Sec. 3, for many catalogs):
+ * the catalogs' cell builds, ONE persistent pair-kernel launch over all of their
+ * work items, and the FP64 finalize are recorded into a CUDA graph at plan
+ * creation and replayed by hip_batch_plan_run.  Catalogs may differ in N, L, R0,
+ * bins, ell_max and line of sight.
+ *
+ * hip_batch_plan_create: validates every catalog (HIP_ERR_ARG/RANGE as in
+ *   hip_power; hip_batch_message() names the catalog), allocates the plan's
+ *   device memory and pinned output mirror, records and instantiates the graph
+ *   (capturing on `cuda_stream`).  The hip_catalog array is copied; the data and
+ *   output pointers it holds must stay valid for the plan's lifetime.
+ * hip_batch_plan_run: copies host-resident inputs into the plan, replays the
+ *   graph, synchronises `cuda_stream` and writes every catalog's outputs;
+ *   device-resident inputs are read in place (their current contents).
+ *   HIP_ERR_NONFINITE if a catalog has a non-finite position or weight.
+ * hip_power_batched: create + run + destroy in one call.
+ * hip_batch_plan_launches: number of kernel launches recorded in the graph. */
+hip_status hip_batch_plan_create(const hip_catalog *cats, int n_cats, hip_precision prec, hip_batch_plan **plan,
+                                 void *cuda_stream);
+hip_status hip_batch_plan_run(hip_batch_plan *plan, void *cuda_stream);
+void hip_batch_plan_destroy(hip_batch_plan *plan);
+int hip_batch_plan_launches(const hip_batch_plan *plan);
+hip_status hip_power_batched(const hip_catalog *cats, int n_cats, hip_precision prec, void *cuda_stream);
+const char *hip_batch_message(void);
+
 /* hip_power without any device allocation (no counterpart in the paper: this is
  * a property of the library, not of the estimator).
  *

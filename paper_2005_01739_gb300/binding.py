@@ -26,6 +26,14 @@ _lock = threading.Lock()
 _lib = None
 
 
+class HipCatalog(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("w", ctypes.c_void_p), ("N", ctypes.c_int64), ("L", ctypes.c_double),
+                ("R0", ctypes.c_double), ("k_edges", ctypes.c_void_p), ("n_k", ctypes.c_int),
+                ("ell_max", ctypes.c_int), ("los_axis", ctypes.c_int), ("prim_begin", ctypes.c_int64),
+                ("prim_end", ctypes.c_int64), ("P_out", ctypes.c_void_p), ("DD_out", ctypes.c_void_p),
+                ("npairs_out", ctypes.c_void_p)]
+
+
 class HipError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(msg)
@@ -57,6 +65,18 @@ def load(path: str | None = None):
         L.hip_noalloc_capacity.argtypes = []
         L.hip_noalloc_message.restype = ctypes.c_char_p
         L.hip_noalloc_message.argtypes = []
+        L.hip_batch_plan_create.restype = i
+        L.hip_batch_plan_create.argtypes = [P, i, i, ctypes.POINTER(ctypes.c_void_p), P]
+        L.hip_batch_plan_run.restype = i
+        L.hip_batch_plan_run.argtypes = [P, P]
+        L.hip_batch_plan_destroy.restype = None
+        L.hip_batch_plan_destroy.argtypes = [P]
+        L.hip_batch_plan_launches.restype = i
+        L.hip_batch_plan_launches.argtypes = [P]
+        L.hip_power_batched.restype = i
+        L.hip_power_batched.argtypes = [P, i, i, P]
+        L.hip_batch_message.restype = ctypes.c_char_p
+        L.hip_batch_message.argtypes = []
         L.hip_status_string.restype = ctypes.c_char_p
         L.hip_status_string.argtypes = [i]
         L.hip_last_error.restype = ctypes.c_char_p
@@ -147,6 +167,77 @@ def hip_power_noalloc(pos, w, L, R0, k_edges, ell_max=4, los_axis=2, prim_range=
                            f"({lib.hip_noalloc_message().decode()})")
     del keep_p, keep_w
     return P, DD, int(npairs.value)
+
+
+class BatchPlan:
+    """Batched power spectra of many catalogs (hip_batch_plan_*): the cell builds,
+    one persistent pair-kernel launch over all catalogs and the FP64 finalize,
+    recorded once into a CUDA graph and replayed by run().
+
+    `catalogs` is a list of dicts with keys pos, w (or None), L, R0, edges and
+    optionally ell_max (4), los_axis (2), prim_range.  After run(), .results[i] is
+    (P, DD, npairs) of catalog i."""
+
+    def __init__(self, catalogs, prec="mixed", stream=None):
+        self._lib = load()
+        self._keep = []
+        n = len(catalogs)
+        self._cats = (HipCatalog * n)()
+        self.results = []
+        for i, c in enumerate(catalogs):
+            pp, kp = _ptr(c["pos"])
+            wp, kw = _ptr(c.get("w"))
+            edges = np.ascontiguousarray(np.asarray(c["edges"], dtype=np.float64))
+            N = int(c["pos"].shape[0])
+            ell_max = int(c.get("ell_max", 4))
+            n_k = len(edges) - 1
+            P = np.zeros((ell_max // 2 + 1, n_k))
+            DD = np.zeros_like(P)
+            npairs = np.zeros(1, dtype=np.int64)
+            p0, p1 = c.get("prim_range", (0, N))
+            self._keep += [kp, kw, edges, P, DD, npairs]
+            self._cats[i] = HipCatalog(pp.value if pp is not None else None, wp.value if wp is not None else None,
+                                       N, float(c["L"]), float(c["R0"]), edges.ctypes.data, n_k, ell_max,
+                                       int(c.get("los_axis", 2)), int(p0), int(p1), P.ctypes.data, DD.ctypes.data,
+                                       npairs.ctypes.data)
+            self.results.append((P, DD, npairs))
+        self._plan = ctypes.c_void_p()
+        rc = self._lib.hip_batch_plan_create(ctypes.cast(self._cats, ctypes.c_void_p), n, PREC[prec],
+                                             ctypes.byref(self._plan), _stream_handle(stream))
+        if rc != HIP_OK:
+            raise HipError(rc, f"hip_batch_plan_create: {self._lib.hip_status_string(rc).decode()} "
+                               f"({self._lib.hip_batch_message().decode()})")
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.hip_batch_plan_launches(self._plan))
+
+    def run(self, stream=None):
+        rc = self._lib.hip_batch_plan_run(self._plan, _stream_handle(stream))
+        if rc != HIP_OK:
+            raise HipError(rc, f"hip_batch_plan_run: {self._lib.hip_status_string(rc).decode()} "
+                               f"({self._lib.hip_batch_message().decode()})")
+        return [(P.copy(), DD.copy(), int(n[0])) for P, DD, n in self.results]
+
+    def close(self):
+        if self._plan:
+            self._lib.hip_batch_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hip_power_batched(catalogs, prec="mixed", stream=None):
+    """One-shot batched power spectra (plan, run, destroy)."""
+    plan = BatchPlan(catalogs, prec, stream)
+    try:
+        return plan.run(stream)
+    finally:
+        plan.close()
 
 
 def hip_bispectrum(pos, w, rand_pos, L, R0, k_edges, lmax=4, prec="mixed", stream=None):

@@ -33,6 +33,35 @@ struct PowerKernelArgs {
     unsigned long long *npairs;
 };
 
+// One catalog of a batched power-spectrum launch (device-resident descriptor).
+template <typename T>
+struct BatchCat {
+    CellList<T> cl;
+    long long p0, p1;
+    int los, n_e, lin;
+    int item_begin, item_end;  // global work items [begin, end)
+    T R0, dk32hi, dk32lo;
+    T k[HIP_MAX_EDGES], klo[HIP_MAX_EDGES];
+    double *acc;                 // [3][n_e] FP64 edge sums (atomically accumulated)
+    unsigned long long *npairs;  // ordered pairs counted
+};
+
+// Per-catalog inputs of the batched FP64 finalize (device-resident).
+struct FinalCat {
+    double k[HIP_MAX_EDGES];
+    double R0, L;
+    int n_e, n_ell;
+    const double *acc;  // [3][n_e]
+    const double *S1;
+    double *Wt;         // [n_k]
+    double *DD, *P;     // [n_ell][n_k]
+};
+
+template <typename T>
+cudaError_t hip_power_pairs_batched(const BatchCat<T> *cats, int n_cats, int n_items, int nch, int *counter,
+                                    int grid, cudaStream_t st);
+cudaError_t hip_power_finalize_batched(const FinalCat *cats, int n_cats, int nk_max, cudaStream_t st);
+
 // Cell build: returns cudaSuccess or the first error.  `err` (device int) gets
 // bit 0 set if a non-finite position or weight is seen; S1 (device double)
 // receives sum of weights.

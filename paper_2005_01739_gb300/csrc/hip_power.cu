@@ -198,9 +198,9 @@ __device__ __forceinline__ void hip_sincos(double u, double *s, double *c) { sin
 // lane + 32 t in chunk t), pairs broadcast.  sin/cos of u = r k_e come from one
 // accurate sincos in chunk 0 and, for uniformly spaced edges, a rotation by the
 // pair's 32 r dk for every later chunk.
-template <int NCH, int MASK, bool LIN>
+template <int NCH, int MASK>
 __device__ __forceinline__ void hip_drain(const WarpSmem<float> &sm, int n, const float *kk, const float *kl,
-                                          int lane, int n_e, float (&H)[3][NCH], float (&Hc)[3][NCH])
+                                          int lane, int n_e, bool LIN, float (&H)[3][NCH], float (&Hc)[3][NCH])
 {
     const float c0 = c_coeffs.ser32[0][0];
     for (int q = 0; q < n; ++q) {
@@ -241,9 +241,9 @@ __device__ __forceinline__ void hip_drain(const WarpSmem<float> &sm, int n, cons
     }
 }
 
-template <int NCH, int MASK, bool LIN>
+template <int NCH, int MASK>
 __device__ __forceinline__ void hip_drain(const WarpSmem<double> &sm, int n, const double *kk, const double *,
-                                          int lane, int n_e, double (&H)[3][NCH], double (&)[3][NCH])
+                                          int lane, int n_e, bool LIN, double (&H)[3][NCH], double (&)[3][NCH])
 {
     for (int q = 0; q < n; ++q) {
         const double r = sm.qr[q];
@@ -282,12 +282,121 @@ __device__ __forceinline__ void hip_drain(const WarpSmem<double> &sm, int n, con
 __device__ __forceinline__ float hip_rot_angle(float r, float dhi, float dlo) { return fmaf(r, dhi, r * dlo); }
 __device__ __forceinline__ double hip_rot_angle(double r, double dhi, double) { return r * dhi; }
 
-// Pair pass.  Each warp works on its own: it takes a work item (home cell,
-// half-shell shift) from the global counter, stages 64-particle tiles of both
-// cells in its own shared-memory slice, tests candidates one per lane, and
-// queues accepted pairs; the queue (which persists across work items) is
-// drained whenever it holds 32 pairs.  After each drain the FP32 register sums
-// are folded into FP64 registers, so an FP32 sum never spans more than 64 pairs.
+// Drain a warp's queue and fold the FP32 register sums into the FP64 ones.
+template <typename T, int NCH, int MASK>
+__device__ __forceinline__ void hip_drain_fold(const WarpSmem<T> &sm, int &qn, const T *kk, const T *kl, int lane,
+                                               int n_e, bool lin, T (&H)[3][NCH], T (&Hc)[3][NCH],
+                                               double (&R)[3][NCH])
+{
+    __syncwarp();
+    hip_drain<NCH, MASK>(sm, qn, kk, kl, lane, n_e, lin, H, Hc);
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+            R[l][t] += (double)H[l][t] + (double)Hc[l][t];
+            H[l][t] = T(0);
+            Hc[l][t] = T(0);
+        }
+    qn = 0;
+    __syncwarp();
+}
+
+// One work item (home cell, half-shell shift) of one catalog, processed by one
+// warp: stage 64-particle tiles of both cells in the warp's shared memory, test
+// candidates one per lane, queue accepted pairs, drain the queue at 32 pairs.
+template <typename T, int NCH, int MASK>
+__device__ __forceinline__ void hip_pair_item(const CellList<T> &cl, int item, long long p0, long long p1, int los,
+                                              T R0sq, T invR0, bool lin, T dk32hi, T dk32lo, WarpSmem<T> &sm,
+                                              int lane, const T *kk, const T *kl, int n_e, T (&H)[3][NCH],
+                                              T (&Hc)[3][NCH], double (&R)[3][NCH], int &qn,
+                                              unsigned long long &cnt)
+{
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int n_c = cl.n_c;
+    const int c = item / HIP_NSHIFT, q = item - c * HIP_NSHIFT;
+    const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
+    const int dx = c_shift[q][0], dy = c_shift[q][1], dz = c_shift[q][2];
+    const int nb = (((cx + dx + n_c) % n_c) * n_c + (cy + dy + n_c) % n_c) * n_c + (cz + dz + n_c) % n_c;
+    const T sx = T(dx) * cl.cs, sy = T(dy) * cl.cs, sz = T(dz) * cl.cs;
+    const int a0 = cl.cell_start[c], a1 = cl.cell_start[c + 1];
+    const int b0 = cl.cell_start[nb], b1 = cl.cell_start[nb + 1];
+    const bool self = (q == 0);
+    for (int hb = a0; hb < a1; hb += HIP_WTILE) {
+        const int hn = min(HIP_WTILE, a1 - hb);
+        __syncwarp();
+        for (int i = lane; i < hn; i += 32) {
+            sm.hx[i] = cl.x[hb + i];
+            sm.hy[i] = cl.y[hb + i];
+            sm.hz[i] = cl.z[hb + i];
+            sm.hw[i] = cl.w[hb + i];
+            const long long oi = cl.idx[hb + i];
+            sm.hin[i] = (oi >= p0 && oi < p1) ? 1 : 0;
+        }
+        for (int nbs = self ? hb : b0; nbs < b1; nbs += HIP_WTILE) {
+            const int nn = min(HIP_WTILE, b1 - nbs);
+            __syncwarp();
+            for (int i = lane; i < nn; i += 32) {
+                sm.nx[i] = cl.x[nbs + i];
+                sm.ny[i] = cl.y[nbs + i];
+                sm.nz[i] = cl.z[nbs + i];
+                sm.nw[i] = cl.w[nbs + i];
+                const long long oi = cl.idx[nbs + i];
+                sm.nin[i] = (oi >= p0 && oi < p1) ? 1 : 0;
+            }
+            __syncwarp();
+            const bool same = self && (nbs == hb);
+            for (int il = 0; il < hn; ++il) {
+                const T xi = sm.hx[il] - sx, yi = sm.hy[il] - sy, zi = sm.hz[il] - sz;
+                const float wi = sm.hw[il];
+                const int ini = sm.hin[il];
+                for (int jb = same ? il + 1 : 0; jb < nn; jb += 32) {
+                    const int jl = jb + lane;
+                    bool ok = false;
+                    T ddx = T(0), ddy = T(0), ddz = T(0), r2 = T(0);
+                    int mult = 0;
+                    if (jl < nn) {
+                        ddx = xi - sm.nx[jl];
+                        ddy = yi - sm.ny[jl];
+                        ddz = zi - sm.nz[jl];
+                        r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        mult = ini + sm.nin[jl];
+                        ok = (r2 < R0sq) && (r2 > T(0)) && (mult > 0);
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, ok);
+                    if (ok) {
+                        const T r = hip_sqrt<T>(r2);
+                        const T dl = los == 0 ? ddx : (los == 1 ? ddy : ddz);
+                        const T mu = dl / r;
+                        T l2, l4;
+                        hip_legendre24<T>(mu, l2, l4);
+                        const T om = T(wi) * T(sm.nw[jl]) * hip_W<T>(r * invR0) * T(mult);
+                        const int slot = qn + __popc(m & lt_mask);
+                        sm.qr[slot] = r;
+                        sm.qo[0][slot] = om;
+                        sm.qo[1][slot] = om * l2;
+                        sm.qo[2][slot] = om * l4;
+                        if (lin) {
+                            T rs, rc;
+                            hip_sincos(hip_rot_angle(r, dk32hi, dk32lo), &rs, &rc);
+                            sm.qc[slot] = rc;
+                            sm.qs[slot] = rs;
+                        }
+                        cnt += (unsigned long long)mult;
+                    }
+                    qn += __popc(m);
+                    if (qn >= 32) hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, lane, n_e, lin, H, Hc, R);
+                }
+            }
+        }
+    }
+}
+
+// Pair pass of one catalog.  Each warp works on its own: it takes work items
+// from the global counter and processes them with hip_pair_item; the queue
+// persists across items.  After each drain the FP32 register sums are folded
+// into FP64 registers, so an FP32 sum never spans more than 64 pairs.  At the
+// end each CTA reduces its warps in shared memory into one FP64 partial row.
 template <typename T, int NCH, int MASK, bool LIN>
 __global__ void __launch_bounds__(HIP_PAIR_THREADS)
     k_power_pairs(CellList<T> cl, PowerKernelArgs a, EdgeTable<T> ed, T R0, T dk32hi, T dk32lo)
@@ -296,9 +405,8 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
     __shared__ double red[3][HIP_MAX_EDGES];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem<T> &sm = smem[warp];
-    const unsigned lt_mask = (1u << lane) - 1u;
     const T R0sq = R0 * R0, invR0 = T(1) / R0;
-    const int n_e = a.n_e, n_c = cl.n_c;
+    const int n_e = a.n_e;
     const int n_ell = (MASK & 16) ? 3 : ((MASK & 4) ? 2 : 1);
 
     T kk[NCH], kl[NCH];
@@ -320,105 +428,15 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
         }
     unsigned long long cnt = 0;
     int qn = 0;
-
-    auto drain = [&]() {
-        __syncwarp();
-        hip_drain<NCH, MASK, LIN>(sm, qn, kk, kl, lane, n_e, H, Hc);
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-#pragma unroll
-            for (int t = 0; t < NCH; ++t) {
-                R[l][t] += (double)H[l][t] + (double)Hc[l][t];
-                H[l][t] = T(0);
-                Hc[l][t] = T(0);
-            }
-        qn = 0;
-        __syncwarp();
-    };
-
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(a.work_counter, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.n_items) break;
-        const int c = item / HIP_NSHIFT, q = item - c * HIP_NSHIFT;
-        const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
-        const int dx = c_shift[q][0], dy = c_shift[q][1], dz = c_shift[q][2];
-        const int nb = (((cx + dx + n_c) % n_c) * n_c + (cy + dy + n_c) % n_c) * n_c + (cz + dz + n_c) % n_c;
-        const T sx = T(dx) * cl.cs, sy = T(dy) * cl.cs, sz = T(dz) * cl.cs;
-        const int a0 = cl.cell_start[c], a1 = cl.cell_start[c + 1];
-        const int b0 = cl.cell_start[nb], b1 = cl.cell_start[nb + 1];
-        const bool self = (q == 0);
-        for (int hb = a0; hb < a1; hb += HIP_WTILE) {
-            const int hn = min(HIP_WTILE, a1 - hb);
-            __syncwarp();
-            for (int i = lane; i < hn; i += 32) {
-                sm.hx[i] = cl.x[hb + i];
-                sm.hy[i] = cl.y[hb + i];
-                sm.hz[i] = cl.z[hb + i];
-                sm.hw[i] = cl.w[hb + i];
-                const long long oi = cl.idx[hb + i];
-                sm.hin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
-            }
-            for (int nbs = self ? hb : b0; nbs < b1; nbs += HIP_WTILE) {
-                const int nn = min(HIP_WTILE, b1 - nbs);
-                __syncwarp();
-                for (int i = lane; i < nn; i += 32) {
-                    sm.nx[i] = cl.x[nbs + i];
-                    sm.ny[i] = cl.y[nbs + i];
-                    sm.nz[i] = cl.z[nbs + i];
-                    sm.nw[i] = cl.w[nbs + i];
-                    const long long oi = cl.idx[nbs + i];
-                    sm.nin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
-                }
-                __syncwarp();
-                const bool same = self && (nbs == hb);
-                for (int il = 0; il < hn; ++il) {
-                    const T xi = sm.hx[il] - sx, yi = sm.hy[il] - sy, zi = sm.hz[il] - sz;
-                    const float wi = sm.hw[il];
-                    const int ini = sm.hin[il];
-                    for (int jb = same ? il + 1 : 0; jb < nn; jb += 32) {
-                        const int jl = jb + lane;
-                        bool ok = false;
-                        T ddx = T(0), ddy = T(0), ddz = T(0), r2 = T(0);
-                        int mult = 0;
-                        if (jl < nn) {
-                            ddx = xi - sm.nx[jl];
-                            ddy = yi - sm.ny[jl];
-                            ddz = zi - sm.nz[jl];
-                            r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            mult = ini + sm.nin[jl];
-                            ok = (r2 < R0sq) && (r2 > T(0)) && (mult > 0);
-                        }
-                        const unsigned m = __ballot_sync(0xffffffffu, ok);
-                        if (ok) {
-                            const T r = hip_sqrt<T>(r2);
-                            const T dl = a.los == 0 ? ddx : (a.los == 1 ? ddy : ddz);
-                            const T mu = dl / r;
-                            T l2, l4;
-                            hip_legendre24<T>(mu, l2, l4);
-                            const T om = T(wi) * T(sm.nw[jl]) * hip_W<T>(r * invR0) * T(mult);
-                            const int slot = qn + __popc(m & lt_mask);
-                            sm.qr[slot] = r;
-                            sm.qo[0][slot] = om;
-                            sm.qo[1][slot] = om * l2;
-                            sm.qo[2][slot] = om * l4;
-                            if (LIN) {
-                                T rs, rc;
-                                hip_sincos(hip_rot_angle(r, dk32hi, dk32lo), &rs, &rc);
-                                sm.qc[slot] = rc;
-                                sm.qs[slot] = rs;
-                            }
-                            cnt += (unsigned long long)mult;
-                        }
-                        qn += __popc(m);
-                        if (qn >= 32) drain();
-                    }
-                }
-            }
-        }
+        hip_pair_item<T, NCH, MASK>(cl, item, a.p0, a.p1, a.los, R0sq, invR0, LIN, dk32hi, dk32lo, sm, lane, kk, kl,
+                                    n_e, H, Hc, R, qn, cnt);
     }
-    if (qn > 0) drain();
+    if (qn > 0) hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, lane, n_e, LIN, H, Hc, R);
     // CTA reduction of the per-lane FP64 sums into one partial row.
     for (int i = threadIdx.x; i < 3 * HIP_MAX_EDGES; i += HIP_PAIR_THREADS) (&red[0][0])[i] = 0.0;
     __syncthreads();
@@ -441,6 +459,72 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if (lane == 0 && cnt) atomicAdd(a.npairs, cnt);
+}
+
+// Pair pass over many catalogs in one launch.  Global work items are the
+// catalogs' items laid end to end (catalog c owns [item_begin, item_end));
+// a warp that moves to another catalog first drains its queue and adds its FP64
+// sums to the previous catalog's accumulator (FP64 atomics), then loads the new
+// catalog's edges.  All catalogs share the kernel's NCH (the largest needed).
+template <typename T, int NCH>
+__global__ void __launch_bounds__(HIP_PAIR_THREADS)
+    k_power_pairs_batched(const BatchCat<T> *__restrict__ cats, int n_cats, int n_items, int *work_counter)
+{
+    __shared__ WarpSmem<T> smem[HIP_PAIR_WARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem<T> &sm = smem[warp];
+    T kk[NCH], kl[NCH];
+    T H[3][NCH], Hc[3][NCH];
+    double R[3][NCH];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+            H[l][t] = T(0);
+            Hc[l][t] = T(0);
+            R[l][t] = 0.0;
+        }
+    unsigned long long cnt = 0;
+    int qn = 0, cur = -1;
+    auto leave = [&](int c) {
+        if (qn > 0) hip_drain_fold<T, NCH, 21>(sm, qn, kk, kl, lane, cats[c].n_e, cats[c].lin != 0, H, Hc, R);
+        const int ne = cats[c].n_e;
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                const int e = lane + 32 * t;
+                if (e < ne && R[l][t] != 0.0) atomicAdd(&cats[c].acc[l * ne + e], R[l][t]);
+                R[l][t] = 0.0;
+            }
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0 && cnt) atomicAdd(cats[c].npairs, cnt);
+        cnt = 0;
+    };
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(work_counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        int c = cur < 0 ? 0 : cur;
+        while (item >= cats[c].item_end) ++c;
+        while (item < cats[c].item_begin) --c;
+        if (c != cur) {
+            if (cur >= 0) leave(cur);
+            cur = c;
+            const int ne = cats[c].n_e;
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                const int e = lane + 32 * t;
+                kk[t] = e < ne ? cats[c].k[e] : T(0);
+                kl[t] = e < ne ? cats[c].klo[e] : T(0);
+            }
+        }
+        const BatchCat<T> &bc = cats[c];
+        hip_pair_item<T, NCH, 21>(bc.cl, item - bc.item_begin, bc.p0, bc.p1, bc.los, bc.R0 * bc.R0, T(1) / bc.R0,
+                                  bc.lin != 0, bc.dk32hi, bc.dk32lo, sm, lane, kk, kl, bc.n_e, H, Hc, R, qn, cnt);
+    }
+    if (cur >= 0) leave(cur);
 }
 
 template <typename T>
@@ -518,6 +602,24 @@ template cudaError_t hip_power_pairs<float>(const CellList<float> &, const Power
 template cudaError_t hip_power_pairs<double>(const CellList<double> &, const PowerKernelArgs &, const double *, int,
                                              double, int, cudaStream_t);
 
+template <typename T>
+cudaError_t hip_power_pairs_batched(const BatchCat<T> *cats, int n_cats, int n_items, int nch, int *counter,
+                                    int grid, cudaStream_t st)
+{
+    if (nch <= 1)
+        k_power_pairs_batched<T, 1><<<grid, HIP_PAIR_THREADS, 0, st>>>(cats, n_cats, n_items, counter);
+    else if (nch <= 2)
+        k_power_pairs_batched<T, 2><<<grid, HIP_PAIR_THREADS, 0, st>>>(cats, n_cats, n_items, counter);
+    else if (nch <= 4)
+        k_power_pairs_batched<T, 4><<<grid, HIP_PAIR_THREADS, 0, st>>>(cats, n_cats, n_items, counter);
+    else
+        k_power_pairs_batched<T, 8><<<grid, HIP_PAIR_THREADS, 0, st>>>(cats, n_cats, n_items, counter);
+    return cudaGetLastError();
+}
+template cudaError_t hip_power_pairs_batched<float>(const BatchCat<float> *, int, int, int, int *, int, cudaStream_t);
+template cudaError_t hip_power_pairs_batched<double>(const BatchCat<double> *, int, int, int, int *, int,
+                                                     cudaStream_t);
+
 // --------------------------------------------------------------- finalize ----
 struct FinalArgs {
     double k[HIP_MAX_EDGES];
@@ -587,6 +689,74 @@ __global__ void __launch_bounds__(1024) k_power_final(FinalArgs f, const double 
         DD[i] = dd;
         P[i] = p;
     }
+}
+
+// Batched FP64 finalize: W~^a for every (catalog, bin), then DD and P per catalog.
+struct GL16 {
+    double x[16], w[16];
+};
+
+__global__ void k_window_transform_batched(const FinalCat *__restrict__ cats, GL16 g)
+{
+    const FinalCat &f = cats[blockIdx.y];
+    const int a = blockIdx.x;
+    if (a >= f.n_e - 1) return;
+    const double klo = f.k[a], khi = f.k[a + 1], R0 = f.R0;
+    const double k3lo = klo * klo * klo, k3hi = khi * khi * khi;
+    const double hmax = 3.14159265358979323846 / (4.0 * khi);
+    const double brk[4] = {0.0, 0.5 * R0, 0.75 * R0, R0};
+    double acc = 0.0;
+    for (int piece = 0; piece < 3; ++piece) {
+        const double lo = brk[piece], len = brk[piece + 1] - brk[piece];
+        const int np = max(1, (int)ceil(len / hmax));
+        const double h = len / np;
+        for (int i = threadIdx.x; i < np * 16; i += blockDim.x) {
+            const int p = i >> 4, q = i & 15;
+            const double r = lo + h * (p + 0.5 * (g.x[q] + 1.0));
+            double Fh[5], Fl[5];
+            hip_F_f64<1>(r * khi, c_coeffs, Fh);
+            hip_F_f64<1>(r * klo, c_coeffs, Fl);
+            const double jb = 3.0 * (k3hi * Fh[0] - k3lo * Fl[0]) / (k3hi - k3lo);
+            acc += 0.5 * h * g.w[q] * r * r * jb * hip_W<double>(r / R0);
+        }
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) f.Wt[a] = 4.0 * 3.14159265358979323846 * v;
+    }
+}
+
+__global__ void k_power_final_batched(const FinalCat *__restrict__ cats)
+{
+    const FinalCat &f = cats[blockIdx.x];
+    const int n_e = f.n_e, n_k = n_e - 1;
+    const double V = f.L * f.L * f.L, nw = f.S1[0] / V;
+    for (int i = threadIdx.x; i < f.n_ell * n_k; i += blockDim.x) {
+        const int il = i / n_k, a = i - il * n_k;
+        const double k3lo = f.k[a] * f.k[a] * f.k[a], k3hi = f.k[a + 1] * f.k[a + 1] * f.k[a + 1];
+        const double dd = 3.0 * (k3hi * f.acc[il * n_e + a + 1] - k3lo * f.acc[il * n_e + a]) / (k3hi - k3lo);
+        const int l = 2 * il;
+        double p = ((il & 1) ? -1.0 : 1.0) * (2.0 * l + 1.0) * dd / (nw * nw * V);
+        if (il == 0) p -= f.Wt[a];
+        f.DD[i] = dd;
+        f.P[i] = p;
+    }
+}
+
+static void gl16(double *x, double *w);
+
+cudaError_t hip_power_finalize_batched(const FinalCat *cats, int n_cats, int nk_max, cudaStream_t st)
+{
+    GL16 g;
+    gl16(g.x, g.w);
+    k_window_transform_batched<<<dim3(nk_max, n_cats), 256, 0, st>>>(cats, g);
+    k_power_final_batched<<<n_cats, 256, 0, st>>>(cats);
+    return cudaGetLastError();
 }
 
 static void gl16(double *x, double *w)

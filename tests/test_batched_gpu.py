@@ -1,0 +1,85 @@
+"""Batched power spectra (many catalogs, one persistent pair launch inside a CUDA
+graph) against the FP64 oracle and against single-catalog hip_power calls."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_01739_gb300 import binding, catalogs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_01739_gb300 import build
+    build.build()
+    binding.load()
+
+
+def _err(P, Pref):
+    floor = 1e-2 * np.max(np.abs(Pref[0]))
+    scale = np.maximum(np.maximum(np.abs(Pref), np.abs(Pref[0])[None, :]), floor)
+    return float(np.max(np.abs(P - Pref) / scale))
+
+
+def _batch(device):
+    """Eight catalogs of uneven N, box, R0, bins (uniform and not), l_max and line of sight."""
+    import torch
+    rng = np.random.default_rng(9)
+    cats = []
+    for i in range(8):
+        N = int(np.exp(rng.uniform(np.log(300), np.log(5000))))
+        L = float(rng.uniform(40, 90))
+        R0 = float([6.0, 9.0, 13.0][i % 3])
+        nk = [8, 40, 70][i % 3]
+        edges = catalogs.linear_edges(25.0 / R0 / 10, 25.0 / R0 / 10 + 3.0 * nk / R0 / 3, nk)
+        if i == 5:
+            edges = np.concatenate([[0.0], np.geomspace(0.05, 3.0, nk)])
+        pos, w = catalogs.thomas(N, L, max(4, N // 30), 1.2, seed=500 + i, background_frac=0.3,
+                                 los_sigma=1.0, weights="u05_15" if i % 2 else "unit")
+        c = dict(pos=pos, w=w, L=L, R0=R0, edges=edges, ell_max=[4, 2, 4, 0][i % 4], los_axis=i % 3)
+        if device:
+            c["pos"] = torch.from_numpy(pos).cuda()
+            c["w"] = None if w is None else torch.from_numpy(w).cuda()
+        cats.append((c, pos, w))
+    return cats
+
+
+def test_batched_matches_oracle_and_single_calls():
+    cats = _batch(device=True)
+    plan = binding.BatchPlan([c for c, _, _ in cats], "mixed")
+    assert plan.launches == 3 * len(cats) + 3
+    res1 = plan.run()
+    res2 = plan.run()  # replay of the same graph
+    for (c, pos, w), (P, DD, n), (P2, _, n2) in zip(cats, res1, res2):
+        w64 = None if w is None else w.astype(np.float64)
+        DDr, nr = oracle.power_pair_sum(pos.astype(np.float64), w64, c["L"], c["R0"], c["edges"], c["ell_max"],
+                                        c["los_axis"])
+        S1 = len(pos) if w is None else float(np.sum(w64))
+        Pr = oracle.power_from_pairs(DDr, S1, c["L"], oracle.window_transform_binned(c["edges"], c["R0"]))
+        assert abs(n - nr) <= 2 and n2 == n
+        assert _err(P, Pr) < 1e-5
+        assert _err(P2, P) < 1e-6
+        Ps, _, ns = binding.hip_power(c["pos"], c["w"], c["L"], c["R0"], c["edges"], c["ell_max"], c["los_axis"],
+                                      "mixed")
+        assert _err(P, Ps) < 2e-6
+    plan.close()
+
+
+def test_batched_fp64_host_inputs_and_nonfinite():
+    cats = _batch(device=False)[:4]
+    res = binding.hip_power_batched([c for c, _, _ in cats], "fp64")
+    for (c, pos, w), (P, DD, n) in zip(cats, res):
+        Ps, _, ns = binding.hip_power(pos, w, c["L"], c["R0"], c["edges"], c["ell_max"], c["los_axis"], "fp64")
+        assert n == ns
+        assert _err(P, Ps) < 1e-10
+    bad = [dict(c) for c, _, _ in cats]
+    p = bad[2]["pos"].copy()
+    p[3, 2] = np.nan
+    bad[2]["pos"] = p
+    with pytest.raises(binding.HipError) as ei:
+        binding.hip_power_batched(bad, "mixed")
+    assert ei.value.status == binding.HIP_ERR_NONFINITE
