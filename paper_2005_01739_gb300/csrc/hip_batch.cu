@@ -64,6 +64,7 @@ struct hip_batch_plan {
     std::vector<size_t> out_off;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
     int launches = 0;
 };
 
@@ -194,7 +195,16 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
     }
     const int grid = hip_power_grid<T>();
 
-    // ---- record the graph
+    // ---- record the graph, on a stream of our own (the legacy default stream,
+    // which callers may pass, cannot be captured); runs replay it on the caller's.
+    (void)st;
+    cudaStream_t cst = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cst, cudaStreamNonBlocking)) != cudaSuccess) {
+        std::snprintf(g_batch_msg, sizeof(g_batch_msg), "stream: %s", cudaGetErrorString(e));
+        return HIP_ERR_CUDA;
+    }
+    pl->cap_stream = cst;
+    st = cst;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
         std::snprintf(g_batch_msg, sizeof(g_batch_msg), "begin capture: %s", cudaGetErrorString(e));
         return HIP_ERR_CUDA;
@@ -260,6 +270,7 @@ static void plan_free(hip_batch_plan *pl)
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->buf) cudaFree(pl->buf);
     if (pl->h_out) cudaFreeHost(pl->h_out);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     delete pl;
 }
 
