@@ -175,6 +175,96 @@ __device__ __forceinline__ void hip_cterm(const BWarpSmem<T, NKMAX> &sm, int n, 
     }
 }
 
+// The C term on the tensor cores (FP32 path): for each l, the batch's
+// contribution C_l[a][b] = sum_q (psi_q J[l][q][a]) J[l][q][b] is a
+// [n_k x 16] x [16 x n_k] product, done with mma.sync m16n8k8 TF32 in three
+// products of the split x = hi + lo (hi*hi + hi*lo + lo*hi, FP32 accumulate),
+// which keeps ~FP32 accuracy; the 16 x 8 result tiles are added to the CTA
+// accumulator.  Fragment layouts of m16n8k8 (g = lane/4, t = lane%4):
+// A a0..a3 = (g, t), (g+8, t), (g, t+4), (g+8, t+4); B b0, b1 = (t, g), (t+4, g);
+// C c0..c3 = (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1).
+__device__ __forceinline__ unsigned hip_tf32(float x)
+{
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void hip_mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int NKMAX>
+__device__ __forceinline__ void hip_cterm_mma(const BWarpSmem<float, NKMAX> &sm, int n, int nk, float sp, int lane,
+                                              float *Tc)
+{
+    constexpr int MT = NKMAX / 16, NT = NKMAX / 8;  // row tiles of 16, column tiles of 8
+    const int g = lane >> 2, t = lane & 3;
+    float psi[2][2];  // psi of the K columns this lane feeds into A: q = 8 ks + t (+4)
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+        const int q0 = 8 * ks + t, q1 = q0 + 4;
+        psi[ks][0] = q0 < n ? -sp * sm.qpsi[q0] : 0.f;
+        psi[ks][1] = q1 < n ? -sp * sm.qpsi[q1] : 0.f;
+    }
+#pragma unroll 1
+    for (int l = 0; l <= HIP_LMAX; ++l) {
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            if (16 * mt >= nk) break;
+            float acc[NT][4];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const int q0 = 8 * ks + t, q1 = q0 + 4;
+                const float x0 = q0 < n ? psi[ks][0] * sm.J[l][q0][16 * mt + g] : 0.f;
+                const float x1 = q0 < n ? psi[ks][0] * sm.J[l][q0][16 * mt + g + 8] : 0.f;
+                const float x2 = q1 < n ? psi[ks][1] * sm.J[l][q1][16 * mt + g] : 0.f;
+                const float x3 = q1 < n ? psi[ks][1] * sm.J[l][q1][16 * mt + g + 8] : 0.f;
+                unsigned ah[4] = {hip_tf32(x0), hip_tf32(x1), hip_tf32(x2), hip_tf32(x3)};
+                unsigned al[4] = {hip_tf32(x0 - __uint_as_float(ah[0])), hip_tf32(x1 - __uint_as_float(ah[1])),
+                                  hip_tf32(x2 - __uint_as_float(ah[2])), hip_tf32(x3 - __uint_as_float(ah[3]))};
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    if (8 * nt >= nk) break;
+                    const float y0 = q0 < n ? sm.J[l][q0][8 * nt + g] : 0.f;
+                    const float y1 = q1 < n ? sm.J[l][q1][8 * nt + g] : 0.f;
+                    unsigned bh[2] = {hip_tf32(y0), hip_tf32(y1)};
+                    unsigned bl[2] = {hip_tf32(y0 - __uint_as_float(bh[0])), hip_tf32(y1 - __uint_as_float(bh[1]))};
+                    hip_mma_tf32(acc[nt], ah, bh);
+                    hip_mma_tf32(acc[nt], ah, bl);
+                    hip_mma_tf32(acc[nt], al, bh);
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                if (8 * nt >= nk) break;
+                const int r0 = 16 * mt + g, r1 = r0 + 8, c0 = 8 * nt + 2 * t, c1 = c0 + 1;
+                float *T = Tc + (size_t)l * nk * nk;
+                if (r0 < nk && c0 < nk) atomicAdd(&T[r0 * nk + c0], acc[nt][0]);
+                if (r0 < nk && c1 < nk) atomicAdd(&T[r0 * nk + c1], acc[nt][1]);
+                if (r1 < nk && c0 < nk) atomicAdd(&T[r1 * nk + c0], acc[nt][2]);
+                if (r1 < nk && c1 < nk) atomicAdd(&T[r1 * nk + c1], acc[nt][3]);
+            }
+        }
+    }
+}
+
+template <typename T, int NKMAX>
+__device__ __forceinline__ void hip_cterm_any(const BWarpSmem<T, NKMAX> &sm, int n, int nk, T sp, int lane, T *Tc)
+{
+    if constexpr (sizeof(T) == 4)
+        hip_cterm_mma<NKMAX>(sm, n, nk, sp, lane, Tc);
+    else
+        hip_cterm<T, NKMAX>(sm, n, nk, sp, lane, Tc);
+}
+
 template <typename T, int NCH, int NKMAX>
 __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
 {
@@ -262,7 +352,7 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
                         __syncwarp();
                         hip_bdrain<T, NCH, NKMAX>(sm, HIP_BQ, kk, kl, k3, k3n, jfac, lane, n_e, E);
                         __syncwarp();
-                        hip_cterm<T, NKMAX>(sm, HIP_BQ, nk, sp, lane, Tc);
+                        hip_cterm_any<T, NKMAX>(sm, HIP_BQ, nk, sp, lane, Tc);
                         const int rest = qn - HIP_BQ;
                         T mv[3] = {T(0), T(0), T(0)};
                         if (lane < rest) {
@@ -290,7 +380,7 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
                 __syncwarp();
                 hip_bdrain<T, NCH, NKMAX>(sm, qn, kk, kl, k3, k3n, jfac, lane, n_e, E);
                 __syncwarp();
-                hip_cterm<T, NKMAX>(sm, qn, nk, sp, lane, Tc);
+                hip_cterm_any<T, NKMAX>(sm, qn, nk, sp, lane, Tc);
                 qn = 0;
             }
             // edge sums -> A^a_lm = jfac_a (k_{a+1}^3 E_{a+1} - k_a^3 E_a)
