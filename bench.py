@@ -163,12 +163,17 @@ def oracle_sample(wl, seconds: float):
             "cores": oracle.num_threads()}
 
 
-def bispectrum_rate(binding, stream, reps: int = 2):
+def bispectrum_rate(binding, stream, reps: int = 2, scale: float = 1.0):
     """B_l (l = 0..4) of the 5e5-particle workload with 1.5e6 randoms: ordered
-    (primary, data) pairs, random primaries included, times bins, per second."""
+    (primary, data) pairs, random primaries included, times bins, per second.
+    `scale` < 1 shrinks the volume at fixed density (profiler captures only)."""
     import torch
     from paper_2005_01739_gb300 import catalogs
     wl = catalogs.workload("bk_n5e5")
+    if scale != 1.0:
+        L = 1000.0 * scale ** (1.0 / 3.0)
+        pos, _ = catalogs.thomas(int(500_000 * scale), L, int(12_500 * scale), 1.5, 1002)
+        wl = dict(wl, pos=pos, rand=catalogs.uniform(int(1_500_000 * scale), L, 1002 + 7919), L=L)
     dpos = torch.from_numpy(wl["pos"]).cuda()
     drnd = torch.from_numpy(wl["rand"]).cuda()
     nk = len(wl["edges"]) - 1
@@ -211,6 +216,18 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_bispectrum_only(args):
+    import torch
+
+    from paper_2005_01739_gb300 import binding, build
+    build.build()
+    binding.load()
+    stream = torch.cuda.Stream()
+    print(json.dumps({"bispectrum": bispectrum_rate(binding, stream, reps=args.steps, scale=args.scale)}),
+          flush=True)
     return 0
 
 
@@ -344,11 +361,14 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-bispectrum", action="store_true")
+    ap.add_argument("--bk-only", action="store_true", help="time only the bispectrum workload")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the catalog volume at fixed density (profiler captures only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.bk_only:
+        return run_bispectrum_only(args)
     return run_ours(args)
 
 
