@@ -325,6 +325,7 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     const size_t o_rw = cv.take(sizeof(float) * N_r), o_ridx = cv.take(sizeof(int) * N_r);
     const size_t o_rcid = cv.take(sizeof(int) * N_r);
     const size_t o_ds = cv.take(sizeof(int) * (n_cells + 1)), o_df = cv.take(sizeof(int) * n_cells);
+    const size_t o_dsc = cv.take(sizeof(int) * N), o_rsc = cv.take(sizeof(int) * N_r);
     const size_t o_rs = cv.take(sizeof(int) * (n_cells + 1)), o_rf = cv.take(sizeof(int) * n_cells);
     const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * n_e);
     const size_t o_bp = cv.take(sizeof(double) * bparts_max * tsz);
@@ -369,6 +370,8 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     HIP_CK(hip_build_cells<T>(drpp, nullptr, N_r, L, n_c, rx, ry, rz, (float *)(b + o_rw), (int *)(b + o_ridx),
                               (int *)(b + o_rcid), rstart, (int *)(b + o_rf), S1r, errr, st),
            "cell build (randoms)");
+    HIP_CK(hip_sorted_cells(dstart, n_cells, (int *)(b + o_dsc), st), "sorted cells (data)");
+    HIP_CK(hip_sorted_cells(rstart, n_cells, (int *)(b + o_rsc), st), "sorted cells (randoms)");
     int herr[2] = {0, 0};
     double hS1 = 0.0;
     HIP_CK(cudaMemcpyAsync(herr, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "D2H error word");
@@ -398,6 +401,10 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     ba.data = dcl;
     ba.rand = rcl;
     ba.n_cells = n_cells;
+    ba.dcell = (const int *)(b + o_dsc);
+    ba.rcell = (const int *)(b + o_rsc);
+    ba.n_data = (int)N;
+    ba.n_rand = (int)N_r;
     ba.n_e = n_e;
     ba.R0 = (T)R0;
     ba.rand_weight = (T)(-hS1 / (double)N_r);

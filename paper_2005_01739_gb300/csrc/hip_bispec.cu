@@ -95,6 +95,7 @@ __device__ __forceinline__ void hip_real_ylm(T x, T y, T z, T *R)
 }
 
 #define HIP_BQ 16                       // neighbours per drain
+#define HIP_BPRIM 8                     // primaries per work item
 #define HIP_BQCAP (HIP_BQ + 32)         // queue capacity (a ballot adds up to 32)
 #define HIP_BWARPS 4
 #define HIP_BTHREADS (HIP_BWARPS * 32)
@@ -104,9 +105,24 @@ template <typename T, int NKMAX>
 struct BWarpSmem {
     T qr[HIP_BQCAP], qw[HIP_BQCAP], qpsi[HIP_BQCAP];
     T qy[HIP_NLM][HIP_BQCAP];
-    T J[HIP_LMAX + 1][HIP_BQ][NKMAX];  // jbar^a_l of each drained neighbour
-    T X[NKMAX + 1][HIP_NLM];           // k_e^3 * (edge sums), then A^a_lm
+    union {
+        T J[HIP_LMAX + 1][HIP_BQ][NKMAX];  // jbar^a_l of each drained neighbour (C term)
+        T X[NKMAX + 1][HIP_NLM];           // at the end of a primary: k_e^3 E_e, then A^a_lm
+    };
 };
+
+__global__ void k_sorted_cells(const int *__restrict__ start, int n_cells, int *__restrict__ scell)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x)
+        for (int i = start[c]; i < start[c + 1]; ++i) scell[i] = c;
+}
+
+cudaError_t hip_sorted_cells(const int *cell_start, int n_cells, int *scell, cudaStream_t st)
+{
+    const int blocks = (n_cells + 255) / 256;
+    k_sorted_cells<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(cell_start, n_cells, scell);
+    return cudaGetLastError();
+}
 
 __device__ __forceinline__ float hip_sqrt_b(float v) { return sqrtf(v); }
 __device__ __forceinline__ double hip_sqrt_b(double v) { return sqrt(v); }
@@ -290,17 +306,20 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
         jfac[t] = e + 1 < n_e ? a.jfac[e] : T(0);
     }
     unsigned long long cnt_d = 0, cnt_r = 0;
+    const int n_prim = a.n_data + a.n_rand;
+    const int n_items = (n_prim + HIP_BPRIM - 1) / HIP_BPRIM;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(a.work_counter, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= 2 * a.n_cells) break;
-        const bool is_rand = item >= a.n_cells;
-        const CellList<T> &pl = is_rand ? a.rand : a.data;
-        const int c = is_rand ? item - a.n_cells : item;
-        const int p0 = pl.cell_start[c], p1 = pl.cell_start[c + 1];
-        const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
-        for (int p = p0; p < p1; ++p) {
+        if (item >= n_items) break;
+        const int g0 = item * HIP_BPRIM, g1 = min(g0 + HIP_BPRIM, n_prim);
+        for (int g = g0; g < g1; ++g) {
+            const bool is_rand = g >= a.n_data;
+            const CellList<T> &pl = is_rand ? a.rand : a.data;
+            const int p = is_rand ? g - a.n_data : g;
+            const int c = is_rand ? a.rcell[p] : a.dcell[p];
+            const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
             const T px = pl.x[p], py = pl.y[p], pz = pl.z[p];
             const T sp = is_rand ? a.rand_weight : T(pl.w[p]);
             const int self = is_rand ? -1 : p;

@@ -10,6 +10,8 @@ struct BispecArgs {
     CellList<T> data;        // neighbours (and data primaries)
     CellList<T> rand;        // random primaries (same cell grid)
     int n_cells;             // cells per catalog (n_c^3)
+    const int *dcell, *rcell;  // cell of each sorted data / random particle
+    int n_data, n_rand;      // primaries: the data, then the randoms
     int n_e;                 // bin edges = n_k + 1
     T R0;
     T rand_weight;           // -S1 / N_r
@@ -18,6 +20,9 @@ struct BispecArgs {
     unsigned long long *npairs;  // [0] data-primary pairs, [1] random-primary pairs
     T k[HIP_BMAXE], klo[HIP_BMAXE], k3[HIP_BMAXE], jfac[HIP_BMAXE];
 };
+
+// Cell index of every sorted particle from the cell start table.
+cudaError_t hip_sorted_cells(const int *cell_start, int n_cells, int *scell, cudaStream_t st);
 
 template <typename T>
 cudaError_t hip_bispec_pairs(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st);
