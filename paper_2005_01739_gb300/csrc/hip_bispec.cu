@@ -100,13 +100,16 @@ __device__ __forceinline__ void hip_real_ylm(T x, T y, T z, T *R)
 #define HIP_BWARPS 4
 #define HIP_BTHREADS (HIP_BWARPS * 32)
 #define HIP_NLM 25
+#define HIP_NLMP 28                     // 25 harmonics padded to a multiple of 4
 
 template <typename T, int NKMAX>
 struct BWarpSmem {
     T qr[HIP_BQCAP], qw[HIP_BQCAP], qpsi[HIP_BQCAP];
-    T qy[HIP_NLM][HIP_BQCAP];
+    alignas(16) T qy[HIP_BQCAP][HIP_NLMP];  // R_lm of each queued neighbour (row padded to 16 bytes)
     union {
-        T J[HIP_LMAX + 1][HIP_BQ][NKMAX];  // jbar^a_l of each drained neighbour (C term)
+        // jbar^a_l of each drained neighbour (C term); rows padded by 4 so that the
+        // MMA fragment loads (8 rows x 4 columns per instruction) hit 32 banks
+        T J[HIP_LMAX + 1][HIP_BQ][NKMAX + 4];
         T X[NKMAX + 1][HIP_NLM];           // at the end of a primary: k_e^3 E_e, then A^a_lm
     };
 };
@@ -155,11 +158,14 @@ __device__ __forceinline__ void hip_bdrain(BWarpSmem<T, NKMAX> &sm, int n, const
         for (int t = 0; t < NCH; ++t) {
             hip_F_all(hip_arg(r, kk[t], kl[t]), F[t]);
             if (lane + 32 * t < n_e) {
+                T y[HIP_NLMP];
+#pragma unroll
+                for (int i = 0; i < HIP_NLMP; ++i) y[i] = sm.qy[q][i];
 #pragma unroll
                 for (int l = 0; l <= HIP_LMAX; ++l) {
                     const T f = ww * F[t][l];
 #pragma unroll
-                    for (int m = -l; m <= l; ++m) E[t][l * l + l + m] += f * sm.qy[l * l + l + m][q];
+                    for (int m = -l; m <= l; ++m) E[t][l * l + l + m] += f * y[l * l + l + m];
                 }
             }
         }
@@ -358,7 +364,7 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
                         sm.qw[slot] = wj * W;
                         sm.qpsi[slot] = wj * wj * W * W;
 #pragma unroll
-                        for (int i = 0; i < HIP_NLM; ++i) sm.qy[i][slot] = R[i];
+                        for (int i = 0; i < HIP_NLM; ++i) sm.qy[slot][i] = R[i];
                     }
                     const int nq = __popc(m);
                     if (is_rand)
@@ -381,14 +387,14 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
                         }
                         T my[HIP_NLM];
 #pragma unroll
-                        for (int i = 0; i < HIP_NLM; ++i) my[i] = lane < rest ? sm.qy[i][HIP_BQ + lane] : T(0);
+                        for (int i = 0; i < HIP_NLM; ++i) my[i] = lane < rest ? sm.qy[HIP_BQ + lane][i] : T(0);
                         __syncwarp();
                         if (lane < rest) {
                             sm.qr[lane] = mv[0];
                             sm.qw[lane] = mv[1];
                             sm.qpsi[lane] = mv[2];
 #pragma unroll
-                            for (int i = 0; i < HIP_NLM; ++i) sm.qy[i][lane] = my[i];
+                            for (int i = 0; i < HIP_NLM; ++i) sm.qy[lane][i] = my[i];
                         }
                         qn = rest;
                         __syncwarp();

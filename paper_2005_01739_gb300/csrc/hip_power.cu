@@ -197,99 +197,135 @@ __device__ __forceinline__ void hip_sincos(double u, double *s, double *c) { sin
 // Bin pass over the n queued pairs of a warp: lanes over bin edges (edge
 // lane + 32 t in chunk t), pairs broadcast.  sin/cos of u = r k_e come from one
 // accurate sincos in chunk 0 and, for uniformly spaced edges, a rotation by the
-// pair's 32 r dk for every later chunk.
-template <int NCH, int MASK>
-__device__ __forceinline__ void hip_drain(const WarpSmem<float> &sm, int n, const float *kk, const float *kl,
-                                          int lane, int n_e, bool LIN, float (&H)[3][NCH], float (&Hc)[3][NCH])
+// pair's 32 r dk for every later chunk.  When the last used chunk (index tl)
+// holds tw <= 16 edges it is "packed": lane l handles edge 32 tl + l % tw of
+// pair q0 + l / tw, so 32 / tw pairs share one pass instead of leaving most
+// lanes idle.
+__device__ __forceinline__ void hip_edge_acc(float u, float s, float c, bool need_sc, float o0, float o2, float o4,
+                                             int mask, float &H0, float &H2, float &H4, float &C0, float &C2,
+                                             float &C4)
 {
-    const float c0 = c_coeffs.ser32[0][0];
+    float Fm[5], Fc[5];
+    if (u < HIP_F32_USMALL) {
+        if (mask & 16)
+            hip_F_f32_series<21>(u, c_coeffs, Fm, Fc);
+        else if (mask & 4)
+            hip_F_f32_series<5>(u, c_coeffs, Fm, Fc);
+        else
+            hip_F_f32_series<1>(u, c_coeffs, Fm, Fc);
+        H0 = fmaf(o0, c_coeffs.ser32[0][0], H0);
+        C0 = fmaf(o0, Fc[0], C0);
+        if (mask & 4) C2 = fmaf(o2, Fc[2], C2);
+        if (mask & 16) C4 = fmaf(o4, Fc[4], C4);
+    } else {
+        if (need_sc) sincosf(u, &s, &c);
+        if (mask & 16)
+            hip_F_f32_closed<21>(u, s, c, c_coeffs, Fm);
+        else if (mask & 4)
+            hip_F_f32_closed<5>(u, s, c, c_coeffs, Fm);
+        else
+            hip_F_f32_closed<1>(u, s, c, c_coeffs, Fm);
+    }
+    H0 = fmaf(o0, Fm[0], H0);
+    if (mask & 4) H2 = fmaf(o2, Fm[2], H2);
+    if (mask & 16) H4 = fmaf(o4, Fm[4], H4);
+}
+
+__device__ __forceinline__ void hip_edge_acc(double u, double s, double c, bool need_sc, double o0, double o2,
+                                             double o4, int mask, double &H0, double &H2, double &H4, double &,
+                                             double &, double &)
+{
+    double F[5];
+    if (u < HIP_F64_USMALL) {
+        if (mask & 16)
+            hip_F_f64_series<21>(u, c_coeffs, F);
+        else if (mask & 4)
+            hip_F_f64_series<5>(u, c_coeffs, F);
+        else
+            hip_F_f64_series<1>(u, c_coeffs, F);
+    } else {
+        if (need_sc) sincos(u, &s, &c);
+        if (mask & 16)
+            hip_F_f64_closed<21>(u, s, c, c_coeffs, F);
+        else if (mask & 4)
+            hip_F_f64_closed<5>(u, s, c, c_coeffs, F);
+        else
+            hip_F_f64_closed<1>(u, s, c, c_coeffs, F);
+    }
+    H0 = fma(o0, F[0], H0);
+    if (mask & 4) H2 = fma(o2, F[2], H2);
+    if (mask & 16) H4 = fma(o4, F[4], H4);
+}
+
+__device__ __forceinline__ float hip_arg(float r, float khi, float klo) { return fmaf(r, khi, r * klo); }
+__device__ __forceinline__ double hip_arg(double r, double khi, double) { return r * khi; }
+
+// Edge handled by `lane` in chunk t (or -1), given the tail chunk tl and the
+// packed tail width tw (0 when the tail is not packed).
+__device__ __forceinline__ int hip_lane_edge(int lane, int t, int n_e, int tl, int tw)
+{
+    if (t == tl && tw > 0) return lane < (32 / tw) * tw ? 32 * tl + lane % tw : -1;
+    const int e = lane + 32 * t;
+    return (t <= tl && e < n_e) ? e : -1;
+}
+
+template <typename T, int NCH, int MASK>
+__device__ __forceinline__ void hip_drain(const WarpSmem<T> &sm, int n, const T *kk, const T *kl, int lane, int n_e,
+                                          bool LIN, int tl, int tw, T (&H)[3][NCH], T (&Hc)[3][NCH])
+{
     for (int q = 0; q < n; ++q) {
-        const float r = sm.qr[q];
-        const float o0 = sm.qo[0][q], o2 = sm.qo[1][q], o4 = sm.qo[2][q];
-        const float rc = sm.qc[q], rs = sm.qs[q];
-        float s = 0.f, c = 1.f;
+        const T r = sm.qr[q];
+        const T o0 = sm.qo[0][q], o2 = sm.qo[1][q], o4 = sm.qo[2][q];
+        const T rc = sm.qc[q], rs = sm.qs[q];
+        T s = T(0), c = T(1);
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
-            const float u = fmaf(r, kk[t], r * kl[t]);
-            if (LIN) {
-                if (t == 0) {
-                    sincosf(u, &s, &c);
-                } else {
-                    const float s2 = fmaf(s, rc, c * rs);
-                    c = fmaf(c, rc, -s * rs);
-                    s = s2;
+            if (t < tl || (t == tl && tw == 0)) {
+                const T u = hip_arg(r, kk[t], kl[t]);
+                if (LIN) {
+                    if (t == 0) {
+                        hip_sincos(u, &s, &c);
+                    } else {
+                        const T s2 = fma(s, rc, c * rs);
+                        c = fma(c, rc, -s * rs);
+                        s = s2;
+                    }
                 }
-            }
-            if (lane + 32 * t < n_e) {
-                float Fm[5], Fc[5];
-                if (u < HIP_F32_USMALL) {
-                    hip_F_f32_series<MASK>(u, c_coeffs, Fm, Fc);
-                    H[0][t] = fmaf(o0, c0, H[0][t]);
-                    Hc[0][t] = fmaf(o0, Fc[0], Hc[0][t]);
-                    if (MASK & 4) Hc[1][t] = fmaf(o2, Fc[2], Hc[1][t]);
-                    if (MASK & 16) Hc[2][t] = fmaf(o4, Fc[4], Hc[2][t]);
-                } else {
-                    float sc = s, cc = c;
-                    if (!LIN) sincosf(u, &sc, &cc);
-                    hip_F_f32_closed<MASK>(u, sc, cc, c_coeffs, Fm);
-                }
-                H[0][t] = fmaf(o0, Fm[0], H[0][t]);
-                if (MASK & 4) H[1][t] = fmaf(o2, Fm[2], H[1][t]);
-                if (MASK & 16) H[2][t] = fmaf(o4, Fm[4], H[2][t]);
+                if (lane + 32 * t < n_e)
+                    hip_edge_acc(u, s, c, !LIN, o0, o2, o4, MASK, H[0][t], H[1][t], H[2][t], Hc[0][t], Hc[1][t],
+                                 Hc[2][t]);
             }
         }
     }
-}
-
-template <int NCH, int MASK>
-__device__ __forceinline__ void hip_drain(const WarpSmem<double> &sm, int n, const double *kk, const double *,
-                                          int lane, int n_e, bool LIN, double (&H)[3][NCH], double (&)[3][NCH])
-{
-    for (int q = 0; q < n; ++q) {
-        const double r = sm.qr[q];
-        const double o0 = sm.qo[0][q], o2 = sm.qo[1][q], o4 = sm.qo[2][q];
-        const double rc = sm.qc[q], rs = sm.qs[q];
-        double s = 0.0, c = 1.0;
+    if (tw > 0) {
+        const int per = 32 / tw, sub = lane / tw;
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
-            const double u = r * kk[t];
-            if (LIN) {
-                if (t == 0) {
-                    sincos(u, &s, &c);
-                } else {
-                    const double s2 = fma(s, rc, c * rs);
-                    c = fma(c, rc, -s * rs);
-                    s = s2;
+            if (t != tl) continue;
+            for (int q0 = 0; q0 < n; q0 += per) {
+                const int q = q0 + sub;
+                if (sub < per && q < n) {
+                    const T r = sm.qr[q];
+                    hip_edge_acc(hip_arg(r, kk[t], kl[t]), T(0), T(1), true, sm.qo[0][q], sm.qo[1][q], sm.qo[2][q],
+                                 MASK, H[0][t], H[1][t], H[2][t], Hc[0][t], Hc[1][t], Hc[2][t]);
                 }
-            }
-            if (lane + 32 * t < n_e) {
-                double F[5];
-                if (u < HIP_F64_USMALL) {
-                    hip_F_f64_series<MASK>(u, c_coeffs, F);
-                } else {
-                    double sc = s, cc = c;
-                    if (!LIN) sincos(u, &sc, &cc);
-                    hip_F_f64_closed<MASK>(u, sc, cc, c_coeffs, F);
-                }
-                H[0][t] = fma(o0, F[0], H[0][t]);
-                if (MASK & 4) H[1][t] = fma(o2, F[2], H[1][t]);
-                if (MASK & 16) H[2][t] = fma(o4, F[4], H[2][t]);
             }
         }
     }
 }
 
 __device__ __forceinline__ float hip_rot_angle(float r, float dhi, float dlo) { return fmaf(r, dhi, r * dlo); }
+
 __device__ __forceinline__ double hip_rot_angle(double r, double dhi, double) { return r * dhi; }
 
 // Drain a warp's queue and fold the FP32 register sums into the FP64 ones.
 template <typename T, int NCH, int MASK>
 __device__ __forceinline__ void hip_drain_fold(const WarpSmem<T> &sm, int &qn, const T *kk, const T *kl, int lane,
-                                               int n_e, bool lin, T (&H)[3][NCH], T (&Hc)[3][NCH],
+                                               int n_e, bool lin, int tl, int tw, T (&H)[3][NCH], T (&Hc)[3][NCH],
                                                double (&R)[3][NCH])
 {
     __syncwarp();
-    hip_drain<NCH, MASK>(sm, qn, kk, kl, lane, n_e, lin, H, Hc);
+    hip_drain<T, NCH, MASK>(sm, qn, kk, kl, lane, n_e, lin, tl, tw, H, Hc);
 #pragma unroll
     for (int l = 0; l < 3; ++l)
 #pragma unroll
@@ -308,7 +344,8 @@ __device__ __forceinline__ void hip_drain_fold(const WarpSmem<T> &sm, int &qn, c
 template <typename T, int NCH, int MASK>
 __device__ __forceinline__ void hip_pair_item(const CellList<T> &cl, int item, long long p0, long long p1, int los,
                                               T R0sq, T invR0, bool lin, T dk32hi, T dk32lo, WarpSmem<T> &sm,
-                                              int lane, const T *kk, const T *kl, int n_e, T (&H)[3][NCH],
+                                              int lane, const T *kk, const T *kl, int n_e, int tl, int tw,
+                                              T (&H)[3][NCH],
                                               T (&Hc)[3][NCH], double (&R)[3][NCH], int &qn,
                                               unsigned long long &cnt)
 {
@@ -385,7 +422,7 @@ __device__ __forceinline__ void hip_pair_item(const CellList<T> &cl, int item, l
                         cnt += (unsigned long long)mult;
                     }
                     qn += __popc(m);
-                    if (qn >= 32) hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, lane, n_e, lin, H, Hc, R);
+                    if (qn >= 32) hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, lane, n_e, lin, tl, tw, H, Hc, R);
                 }
             }
         }
@@ -408,13 +445,14 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
     const T R0sq = R0 * R0, invR0 = T(1) / R0;
     const int n_e = a.n_e;
     const int n_ell = (MASK & 16) ? 3 : ((MASK & 4) ? 2 : 1);
+    const int tl = (n_e - 1) / 32, tw = (n_e - 32 * tl <= 16) ? n_e - 32 * tl : 0;
 
     T kk[NCH], kl[NCH];
 #pragma unroll
     for (int t = 0; t < NCH; ++t) {
-        const int e = lane + 32 * t;
-        kk[t] = e < n_e ? ed.k[e] : T(0);
-        kl[t] = e < n_e ? ed.klo[e] : T(0);
+        const int e = hip_lane_edge(lane, t, n_e, tl, tw);
+        kk[t] = e >= 0 ? ed.k[e] : T(0);
+        kl[t] = e >= 0 ? ed.klo[e] : T(0);
     }
     T H[3][NCH], Hc[3][NCH];
     double R[3][NCH];
@@ -434,9 +472,9 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.n_items) break;
         hip_pair_item<T, NCH, MASK>(cl, item, a.p0, a.p1, a.los, R0sq, invR0, LIN, dk32hi, dk32lo, sm, lane, kk, kl,
-                                    n_e, H, Hc, R, qn, cnt);
+                                    n_e, tl, tw, H, Hc, R, qn, cnt);
     }
-    if (qn > 0) hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, lane, n_e, LIN, H, Hc, R);
+    if (qn > 0) hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, lane, n_e, LIN, tl, tw, H, Hc, R);
     // CTA reduction of the per-lane FP64 sums into one partial row.
     for (int i = threadIdx.x; i < 3 * HIP_MAX_EDGES; i += HIP_PAIR_THREADS) (&red[0][0])[i] = 0.0;
     __syncthreads();
@@ -446,8 +484,8 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
             for (int l = 0; l < 3; ++l)
 #pragma unroll
                 for (int t = 0; t < NCH; ++t) {
-                    const int e = lane + 32 * t;
-                    if (e < n_e) red[l][e] += R[l][t];
+                    const int e = hip_lane_edge(lane, t, n_e, tl, tw);
+                    if (e >= 0) atomicAdd(&red[l][e], R[l][t]);  // packed-tail lanes share edges
                 }
         }
         __syncthreads();
@@ -485,16 +523,17 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
             R[l][t] = 0.0;
         }
     unsigned long long cnt = 0;
-    int qn = 0, cur = -1;
+    int qn = 0, cur = -1, tl = 0, tw = 0;
     auto leave = [&](int c) {
-        if (qn > 0) hip_drain_fold<T, NCH, 21>(sm, qn, kk, kl, lane, cats[c].n_e, cats[c].lin != 0, H, Hc, R);
+        if (qn > 0)
+            hip_drain_fold<T, NCH, 21>(sm, qn, kk, kl, lane, cats[c].n_e, cats[c].lin != 0, tl, tw, H, Hc, R);
         const int ne = cats[c].n_e;
 #pragma unroll
         for (int l = 0; l < 3; ++l)
 #pragma unroll
             for (int t = 0; t < NCH; ++t) {
-                const int e = lane + 32 * t;
-                if (e < ne && R[l][t] != 0.0) atomicAdd(&cats[c].acc[l * ne + e], R[l][t]);
+                const int e = hip_lane_edge(lane, t, ne, tl, tw);
+                if (e >= 0 && R[l][t] != 0.0) atomicAdd(&cats[c].acc[l * ne + e], R[l][t]);
                 R[l][t] = 0.0;
             }
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -513,16 +552,19 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
             if (cur >= 0) leave(cur);
             cur = c;
             const int ne = cats[c].n_e;
+            tl = (ne - 1) / 32;
+            tw = (ne - 32 * tl <= 16) ? ne - 32 * tl : 0;
 #pragma unroll
             for (int t = 0; t < NCH; ++t) {
-                const int e = lane + 32 * t;
-                kk[t] = e < ne ? cats[c].k[e] : T(0);
-                kl[t] = e < ne ? cats[c].klo[e] : T(0);
+                const int e = hip_lane_edge(lane, t, ne, tl, tw);
+                kk[t] = e >= 0 ? cats[c].k[e] : T(0);
+                kl[t] = e >= 0 ? cats[c].klo[e] : T(0);
             }
         }
         const BatchCat<T> &bc = cats[c];
         hip_pair_item<T, NCH, 21>(bc.cl, item - bc.item_begin, bc.p0, bc.p1, bc.los, bc.R0 * bc.R0, T(1) / bc.R0,
-                                  bc.lin != 0, bc.dk32hi, bc.dk32lo, sm, lane, kk, kl, bc.n_e, H, Hc, R, qn, cnt);
+                                  bc.lin != 0, bc.dk32hi, bc.dk32lo, sm, lane, kk, kl, bc.n_e, tl, tw, H, Hc, R, qn,
+                                  cnt);
     }
     if (cur >= 0) leave(cur);
 }
