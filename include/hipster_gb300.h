@@ -109,6 +109,19 @@ hip_status hip_bispectrum(const float *pos, const float *w, int64_t N, const flo
                           double R0, hip_window window, const double *k_edges, int n_k, int lmax, hip_precision prec,
                           double *B_out, int64_t *npairs_out, void *cuda_stream);
 
+/* The bispectrum's primary sum over chosen primaries, for sharding and sampled
+ * checks: T_out = sum_{i in data range} w_i G^ab_l(x_i) - (S1/N_r) sum_{r in random
+ * range} G^ab_l(x_r), with G as in hip_bispectrum (before the normalisation and
+ * the analytic terms of Sec. 4.5).  prim_ranges = {d0, d1, r0, r1}: data
+ * primaries [d0, d1) and random primaries [r0, r1) in input order (neighbours
+ * are always all the data).  Partial sums over disjoint ranges add up to the
+ * full T.  Other arguments, errors and npairs_out as in hip_bispectrum;
+ * T_out is [(lmax+1) * n_k * n_k] float64 host. */
+hip_status hip_bispectrum_partial(const float *pos, const float *w, int64_t N, const float *rand_pos, int64_t N_r,
+                                  double L, double R0, hip_window window, const double *k_edges, int n_k, int lmax,
+                                  hip_precision prec, const int64_t *prim_ranges, double *T_out, int64_t *npairs_out,
+                                  void *cuda_stream);
+
 /* One catalog of a batched power-spectrum computation: the arguments of
  * hip_power for that catalog (host or device inputs; host outputs). */
 typedef struct {

@@ -77,6 +77,8 @@ def load(path: str | None = None):
         L.hip_power_batched.argtypes = [P, i, i, P]
         L.hip_batch_message.restype = ctypes.c_char_p
         L.hip_batch_message.argtypes = []
+        L.hip_bispectrum_partial.restype = i
+        L.hip_bispectrum_partial.argtypes = [P, P, i64, P, i64, d, d, i, P, i, i, i, P, P, P, P]
         L.hip_status_string.restype = ctypes.c_char_p
         L.hip_status_string.argtypes = [i]
         L.hip_last_error.restype = ctypes.c_char_p
@@ -260,6 +262,31 @@ def hip_bispectrum(pos, w, rand_pos, L, R0, k_edges, lmax=4, prec="mixed", strea
     _check(lib, rc, "hip_bispectrum")
     del keep_p, keep_w, keep_r
     return B, (int(npairs[0]), int(npairs[1]))
+
+
+def hip_bispectrum_partial(pos, w, rand_pos, L, R0, k_edges, lmax=4, prec="mixed", data_range=None,
+                           rand_range=None, stream=None):
+    """T^ab_l summed over data primaries in data_range and random primaries in
+    rand_range (input order), before normalisation.  Returns (T, (pairs, pairs))."""
+    lib = load()
+    n = int(pos.shape[0])
+    nr = int(rand_pos.shape[0])
+    pp, keep_p = _ptr(pos)
+    wp, keep_w = _ptr(w)
+    rp, keep_r = _ptr(rand_pos)
+    edges = np.ascontiguousarray(np.asarray(k_edges, dtype=np.float64))
+    n_k = len(edges) - 1
+    T = np.zeros((lmax + 1, n_k, n_k))
+    d0, d1 = (0, n) if data_range is None else data_range
+    r0, r1 = (0, nr) if rand_range is None else rand_range
+    rng = np.array([d0, d1, r0, r1], dtype=np.int64)
+    npairs = (ctypes.c_int64 * 2)()
+    rc = lib.hip_bispectrum_partial(pp, wp, n, rp, nr, float(L), float(R0), 0, edges.ctypes.data_as(ctypes.c_void_p),
+                                    n_k, int(lmax), PREC[prec], rng.ctypes.data_as(ctypes.c_void_p),
+                                    T.ctypes.data_as(ctypes.c_void_p), npairs, _stream_handle(stream))
+    _check(lib, rc, "hip_bispectrum_partial")
+    del keep_p, keep_w, keep_r
+    return T, (int(npairs[0]), int(npairs[1]))
 
 
 def debug_F(prec: str, l: int, u: float) -> float:

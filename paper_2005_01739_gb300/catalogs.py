@@ -115,4 +115,28 @@ def workload(name: str):
         pos, w = thomas(500_000, 1000.0, 12_500, 1.5, 1002)
         rand = uniform(1_500_000, 1000.0, 1002 + 7919)
         return dict(pos=pos, w=w, rand=rand, L=1000.0, R0=40.0, edges=linear_edges(0.3, 3.0, 25), lmax=4)
+    if name == "batched64":  # index 3
+        return dict(catalogs=[batched_catalog(c) for c in range(64)])
+    if name == "large_zeldovich":  # index 4
+        pos = zeldovich_lattice(256, 1000.0, 1004)
+        edges_p = linear_edges(1.25, 10.0, 200)            # R0 = 20: k_min = 25/R0
+        edges_b = linear_edges(25.0 / 15.0, 25.0 / 15.0 + 40 * 3.0 / 15.0, 40)  # R0 = 15, dk = 3/R0
+        return dict(pos=pos, w=None, L=1000.0, R0=20.0, edges=edges_p, ell_max=4, R0_b=15.0, edges_b=edges_b,
+                    lmax=4)
     raise KeyError(name)
+
+
+def batched_catalog(c: int):
+    """Catalog c of the 64-catalog batch (seed 2000 + c): N log-uniform in
+    [1e5, 4e6], L uniform in [500, 2000], R0 drawn from {10, 20, 40}; bins of
+    width 3/R0 from k = 25/R0 up to 10 h/Mpc (the R0 ~ 1/k_min and dk >~ 3/R0
+    rules of Sec. 9.1); Thomas process as the 2e6 workload (sigma 1.5, 40
+    children per parent, weights U(0.5, 1.5))."""
+    rng = np.random.default_rng(2000 + c)
+    N = int(np.exp(rng.uniform(np.log(1e5), np.log(4e6))))
+    L = float(rng.uniform(500.0, 2000.0))
+    R0 = float(rng.choice([10.0, 20.0, 40.0]))
+    nk = int((10.0 * R0 - 25.0) // 3.0)
+    edges = np.linspace(25.0 / R0, 25.0 / R0 + nk * 3.0 / R0, nk + 1)
+    pos, w = thomas(N, L, max(1, N // 40), 1.5, 2000 + c, weights="u05_15")
+    return dict(pos=pos, w=w, L=L, R0=R0, edges=edges, ell_max=4, los_axis=2)

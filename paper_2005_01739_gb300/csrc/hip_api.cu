@@ -304,7 +304,7 @@ extern "C" hip_status hip_power(const float *pos, const float *w, int64_t N, dou
 template <typename T>
 static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const float *rpos, int64_t N_r, double L,
                               double R0, const double *k_edges, int n_k, int lmax, double *B_out,
-                              int64_t *npairs_out, cudaStream_t st, int dev)
+                              int64_t *npairs_out, cudaStream_t st, int dev, const int64_t *ranges, bool partial)
 {
     Workspace &ws = hip_workspace(dev);
     const int n_c = hip_cells_per_side(L, R0);
@@ -411,6 +411,10 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     ba.work_counter = bcounter;
     ba.partials = (double *)(b + o_bp);
     ba.npairs = npairs + 1;
+    ba.dp0 = ranges ? ranges[0] : 0;
+    ba.dp1 = ranges ? ranges[1] : N;
+    ba.rp0 = ranges ? ranges[2] : 0;
+    ba.rp1 = ranges ? ranges[3] : N_r;
     for (int q = 0; q < HIP_BMAXE; ++q) {
         const double k = q < n_e ? k_edges[q] : 0.0;
         ba.k[q] = (T)k;
@@ -421,7 +425,10 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     int bgrid = 0;
     HIP_CK(hip_bispec_pairs<T>(ba, bparts_max, &bgrid, st), "bispectrum kernel");
     double *B = (double *)(b + o_b);
-    HIP_CK(hip_bispec_finalize(ba.partials, bgrid, n_k, lmax, L, S1, DD, Wt, B, st), "bispectrum finalize");
+    if (partial)
+        HIP_CK(hip_bispec_sum(ba.partials, bgrid, n_k, lmax, B, st), "bispectrum sum");
+    else
+        HIP_CK(hip_bispec_finalize(ba.partials, bgrid, n_k, lmax, L, S1, DD, Wt, B, st), "bispectrum finalize");
     const size_t nout = (size_t)(lmax + 1) * n_k * n_k;
     std::vector<double> hB(nout);
     unsigned long long hn[3] = {0, 0, 0};
@@ -457,8 +464,40 @@ extern "C" hip_status hip_bispectrum(const float *pos, const float *w, int64_t N
     if ((hs = hip_device_setup(&dev)) != HIP_OK) return hs;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (prec == HIP_PREC_MIXED)
-        return bispec_impl<float>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, lmax, B_out, npairs_out, st, dev);
-    return bispec_impl<double>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, lmax, B_out, npairs_out, st, dev);
+        return bispec_impl<float>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, lmax, B_out, npairs_out, st, dev,
+                                  nullptr, false);
+    return bispec_impl<double>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, lmax, B_out, npairs_out, st, dev,
+                               nullptr, false);
+}
+
+extern "C" hip_status hip_bispectrum_partial(const float *pos, const float *w, int64_t N, const float *rand_pos,
+                                             int64_t N_r, double L, double R0, hip_window window,
+                                             const double *k_edges, int n_k, int lmax, hip_precision prec,
+                                             const int64_t *prim_ranges, double *T_out, int64_t *npairs_out,
+                                             void *cuda_stream)
+{
+    g_errbuf[0] = 0;
+    if (!pos || !rand_pos || !T_out || !prim_ranges) return HIP_ERR_ARG;
+    if (N < 1 || N > 2000000000LL || N_r < 1 || N_r > 2000000000LL) return HIP_ERR_ARG;
+    if (window != HIP_WINDOW_PHILCOX) return HIP_ERR_ARG;
+    if (prec != HIP_PREC_FP64 && prec != HIP_PREC_MIXED) return HIP_ERR_ARG;
+    if (lmax < 0 || lmax > HIP_LMAX) return HIP_ERR_ARG;
+    if (!(L > 0.0) || !std::isfinite(L) || !(R0 > 0.0) || !(R0 < 0.5 * L)) return HIP_ERR_RANGE;
+    if (prim_ranges[0] < 0 || prim_ranges[1] > N || prim_ranges[0] > prim_ranges[1] || prim_ranges[2] < 0 ||
+        prim_ranges[3] > N_r || prim_ranges[2] > prim_ranges[3])
+        return HIP_ERR_RANGE;
+    hip_status hs = hip_check_edges(k_edges, n_k);
+    if (hs != HIP_OK) return hs;
+    if (n_k > (prec == HIP_PREC_MIXED ? HIP_BMAXE - 2 : 31)) return HIP_ERR_RANGE;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    int dev = 0;
+    if ((hs = hip_device_setup(&dev)) != HIP_OK) return hs;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (prec == HIP_PREC_MIXED)
+        return bispec_impl<float>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, lmax, T_out, npairs_out, st, dev,
+                                  prim_ranges, true);
+    return bispec_impl<double>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, lmax, T_out, npairs_out, st, dev,
+                               prim_ranges, true);
 }
 
 // ------------------------------------------------------ host self-checks -----

@@ -94,7 +94,7 @@ __device__ __forceinline__ void hip_real_ylm(T x, T y, T z, T *R)
     }
 }
 
-#define HIP_BQ 16                       // neighbours per drain
+#define HIP_BQ 8                        // neighbours per drain (one K = 8 MMA step)
 #define HIP_BPRIM 8                     // primaries per work item
 #define HIP_BQCAP (HIP_BQ + 32)         // queue capacity (a ballot adds up to 32)
 #define HIP_BWARPS 4
@@ -227,9 +227,9 @@ __device__ __forceinline__ void hip_cterm_mma(const BWarpSmem<float, NKMAX> &sm,
 {
     constexpr int MT = NKMAX / 16, NT = NKMAX / 8;  // row tiles of 16, column tiles of 8
     const int g = lane >> 2, t = lane & 3;
-    float psi[2][2];  // psi of the K columns this lane feeds into A: q = 8 ks + t (+4)
+    float psi[HIP_BQ / 8][2];  // psi of the K columns this lane feeds into A: q = 8 ks + t (+4)
 #pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
+    for (int ks = 0; ks < HIP_BQ / 8; ++ks) {
         const int q0 = 8 * ks + t, q1 = q0 + 4;
         psi[ks][0] = q0 < n ? -sp * sm.qpsi[q0] : 0.f;
         psi[ks][1] = q1 < n ? -sp * sm.qpsi[q1] : 0.f;
@@ -243,7 +243,7 @@ __device__ __forceinline__ void hip_cterm_mma(const BWarpSmem<float, NKMAX> &sm,
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
+            for (int ks = 0; ks < HIP_BQ / 8; ++ks) {
                 const int q0 = 8 * ks + t, q1 = q0 + 4;
                 const float x0 = q0 < n ? psi[ks][0] * sm.J[l][q0][16 * mt + g] : 0.f;
                 const float x1 = q0 < n ? psi[ks][0] * sm.J[l][q0][16 * mt + g + 8] : 0.f;
@@ -329,6 +329,10 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
             const T px = pl.x[p], py = pl.y[p], pz = pl.z[p];
             const T sp = is_rand ? a.rand_weight : T(pl.w[p]);
             const int self = is_rand ? -1 : p;
+            {
+                const long long oi = pl.idx[p];
+                if (is_rand ? (oi < a.rp0 || oi >= a.rp1) : (oi < a.dp0 || oi >= a.dp1)) continue;
+            }
             T E[NCH][HIP_NLM];
 #pragma unroll
             for (int t = 0; t < NCH; ++t)
@@ -517,5 +521,22 @@ cudaError_t hip_bispec_finalize(const double *partials, int nparts, int nk, int 
 {
     const int tot = (lmax + 1) * nk * nk;
     k_bispec_final<<<(tot + 255) / 256, 256, 0, st>>>(partials, nparts, nk, lmax, L, S1, S, Wt, B);
+    return cudaGetLastError();
+}
+
+__global__ void k_bispec_sum(const double *__restrict__ partials, int nparts, int nk, int lmax, double *T)
+{
+    const int tot = (lmax + 1) * nk * nk;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int p = 0; p < nparts; ++p) t += partials[(size_t)p * (HIP_LMAX + 1) * nk * nk + i];
+        T[i] = t;
+    }
+}
+
+cudaError_t hip_bispec_sum(const double *partials, int nparts, int nk, int lmax, double *T, cudaStream_t st)
+{
+    const int tot = (lmax + 1) * nk * nk;
+    k_bispec_sum<<<(tot + 255) / 256, 256, 0, st>>>(partials, nparts, nk, lmax, T);
     return cudaGetLastError();
 }

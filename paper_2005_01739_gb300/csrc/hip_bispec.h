@@ -12,6 +12,7 @@ struct BispecArgs {
     int n_cells;             // cells per catalog (n_c^3)
     const int *dcell, *rcell;  // cell of each sorted data / random particle
     int n_data, n_rand;      // primaries: the data, then the randoms
+    long long dp0, dp1, rp0, rp1;  // primary ranges (input order) of the data and of the randoms
     int n_e;                 // bin edges = n_k + 1
     T R0;
     T rand_weight;           // -S1 / N_r
@@ -26,6 +27,9 @@ cudaError_t hip_sorted_cells(const int *cell_start, int n_cells, int *scell, cud
 
 template <typename T>
 cudaError_t hip_bispec_pairs(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st);
+
+// T^ab_l = sum of the partial rows (the primary sum before normalisation).
+cudaError_t hip_bispec_sum(const double *partials, int nparts, int nk, int lmax, double *T, cudaStream_t st);
 
 // B^ab_l from the summed T partials, S^a (ordered DD_0 sum of the power kernel)
 // and W~^a (Sec. 4.5 summary), all in FP64 on the device.

@@ -435,7 +435,7 @@ __device__ __forceinline__ void hip_pair_item(const CellList<T> &cl, int item, l
 // into FP64 registers, so an FP32 sum never spans more than 64 pairs.  At the
 // end each CTA reduces its warps in shared memory into one FP64 partial row.
 template <typename T, int NCH, int MASK, bool LIN>
-__global__ void __launch_bounds__(HIP_PAIR_THREADS)
+__global__ void __launch_bounds__(HIP_PAIR_THREADS, 6)
     k_power_pairs(CellList<T> cl, PowerKernelArgs a, EdgeTable<T> ed, T R0, T dk32hi, T dk32lo)
 {
     __shared__ WarpSmem<T> smem[HIP_PAIR_WARPS];
