@@ -87,7 +87,7 @@ def zeldovich_lattice(n_side: int, L: float, seed: int, rms_disp: float = 2.0,
     for K in (KX, KY, KZ):
         psi_k = 1j * K * dk / k2
         psi_k[0, 0, 0] = 0.0
-        disp.append(np.fft.irfftn(psi_k, s=(g, g, g)))
+        disp.append(np.fft.irfftn(psi_k, s=(g, g, g), axes=(0, 1, 2)))
     disp = np.stack(disp, axis=-1).reshape(-1, 3)
     rms = np.sqrt(np.mean(disp * disp))
     disp *= rms_disp / rms

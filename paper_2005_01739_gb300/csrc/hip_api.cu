@@ -243,7 +243,7 @@ static hip_status power_impl(const float *pos, const float *w, int64_t N, double
 
     HIP_CK(cudaMemsetAsync(npairs, 0, sizeof(unsigned long long), st), "memset");
     HIP_CK(cudaMemsetAsync(counter, 0, sizeof(int), st), "memset");
-    CellList<T> cl{x, y, z, wsrt, idx, cstart, n_c, (T)(L / n_c)};
+    CellList<T> cl{x, y, z, wsrt, idx, cstart, n_c, L, L / n_c};
     PowerKernelArgs ka;
     ka.n_e = n_e;
     ka.los = los;
@@ -380,8 +380,8 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     if (herr[0] || herr[1]) return HIP_ERR_NONFINITE;
 
     // S^a: ordered DD_0 pair sum over all data (the power pass with l = 0 only)
-    CellList<T> dcl{dx, dy, dz, (const float *)(b + o_dw), (const int *)(b + o_didx), dstart, n_c, (T)(L / n_c)};
-    CellList<T> rcl{rx, ry, rz, (const float *)(b + o_rw), (const int *)(b + o_ridx), rstart, n_c, (T)(L / n_c)};
+    CellList<T> dcl{dx, dy, dz, (const float *)(b + o_dw), (const int *)(b + o_didx), dstart, n_c, L, L / n_c};
+    CellList<T> rcl{rx, ry, rz, (const float *)(b + o_rw), (const int *)(b + o_ridx), rstart, n_c, L, L / n_c};
     HIP_CK(cudaMemsetAsync(npairs, 0, 3 * sizeof(unsigned long long), st), "memset");
     HIP_CK(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st), "memset");
     PowerKernelArgs ka;

@@ -136,7 +136,7 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
         BatchCat<T> &d = bc[oi];
         std::memset(&d, 0, sizeof(d));
         d.cl = CellList<T>{(T *)(b + L.o_x), (T *)(b + L.o_y), (T *)(b + L.o_z), (float *)(b + L.o_ws),
-                           (int *)(b + L.o_idx), (int *)(b + L.o_start), L.n_c, (T)(c.L / L.n_c)};
+                           (int *)(b + L.o_idx), (int *)(b + L.o_start), L.n_c, c.L, c.L / L.n_c};
         d.p0 = c.prim_begin;
         d.p1 = c.prim_end;
         d.los = c.los_axis;

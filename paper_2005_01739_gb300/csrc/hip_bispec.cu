@@ -339,11 +339,22 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
 #pragma unroll
                 for (int i = 0; i < HIP_NLM; ++i) E[t][i] = T(0);
             int qn = 0;
+            // cell shifts of this primary: lane 3 axis + d + 1 holds the shift
+            // of neighbour offset d along that axis (the shift's low part, below
+            // 1e-6 of the cell side, is under the FP32 B budget and dropped)
+            T shl = T(0);
+            if (lane < 9) {
+                const int ax = lane / 3, cc = ax == 0 ? cx : (ax == 1 ? cy : cz);
+                T lo;
+                hip_cell_shift(a.data, cc, lane % 3 - 1, shl, lo);
+            }
             for (int s = 0; s < 27; ++s) {
                 const int dx = s / 9 - 1, dy = (s / 3) % 3 - 1, dz = s % 3 - 1;
                 const int nb = (((cx + dx + n_c) % n_c) * n_c + (cy + dy + n_c) % n_c) * n_c + (cz + dz + n_c) % n_c;
                 const int b0 = a.data.cell_start[nb], b1 = a.data.cell_start[nb + 1];
-                const T ox = px - T(dx) * a.data.cs, oy = py - T(dy) * a.data.cs, oz = pz - T(dz) * a.data.cs;
+                const T shx = __shfl_sync(0xffffffffu, shl, dx + 1), shy = __shfl_sync(0xffffffffu, shl, dy + 4),
+                        shz = __shfl_sync(0xffffffffu, shl, dz + 7);
+                const T ox = px - shx, oy = py - shy, oz = pz - shz;
                 for (int jb = b0; jb < b1; jb += 32) {
                     const int j = jb + lane;
                     bool ok = false;

@@ -20,8 +20,51 @@ struct CellList {
     const int *idx;          // original index of each sorted particle
     const int *cell_start;   // [n_cells + 1]
     int n_c;                 // cells per side
-    T cs;                    // cell side = L / n_c (>= R0)
+    double L;                // box side
+    double cs;               // cell side = L / n_c (>= R0)
 };
+
+#ifdef __CUDACC__
+// Origin of cell c along one axis.  For FP32 lists it is the float nearest
+// c cs: for c >= 1 that origin is >= cs, so every float coordinate x in the
+// cell lies within a factor two of it and x - origin is exact in float
+// (Sterbenz's lemma); for c = 0 the offset is x itself.  Cell-local offsets
+// therefore carry no rounding, whatever L / n_c is.
+template <typename T>
+__device__ __forceinline__ double hip_cell_origin(int c, double cs);
+template <>
+__device__ __forceinline__ double hip_cell_origin<float>(int c, double cs)
+{
+    return (double)(float)(c * cs);
+}
+template <>
+__device__ __forceinline__ double hip_cell_origin<double>(int c, double cs)
+{
+    return c * cs;
+}
+
+// Offset of the frame of neighbour cell c + d (periodic image included) from
+// the frame of home cell c along one axis: unwrapped neighbour origin minus home
+// origin, so that a home offset h seen from the neighbour frame is h - shift.
+// For FP32 lists the double sum is exact (two floats and L, result ~ cs) and is
+// returned as hi + lo.
+template <typename T>
+__device__ __forceinline__ void hip_cell_shift(const CellList<T> &cl, int c, int d, T &hi, T &lo)
+{
+    int u = c + d;
+    double wrap = 0.0;
+    if (u < 0) {
+        u += cl.n_c;
+        wrap = -cl.L;
+    } else if (u >= cl.n_c) {
+        u -= cl.n_c;
+        wrap = cl.L;
+    }
+    const double s = (hip_cell_origin<T>(u, cl.cs) - hip_cell_origin<T>(c, cl.cs)) + wrap;
+    hi = (T)s;
+    lo = (T)(s - (double)hi);
+}
+#endif
 
 struct PowerKernelArgs {
     int n_e;                 // number of bin edges = n_k + 1
@@ -31,6 +74,16 @@ struct PowerKernelArgs {
     int *work_counter;
     double *partials;        // [gridDim.x][3][n_e]
     unsigned long long *npairs;
+};
+
+// Bin edges as seen by the pair kernels.  For FP32 each edge is split into
+// khi + klo (two floats) and u = r k is formed as fma(r, khi, r klo): rounding
+// the edge itself to a float would shift every pair's argument the same way, a
+// systematic error, while the rounding of u then varies from pair to pair.
+template <typename T>
+struct EdgeTable {
+    T k[HIP_MAX_EDGES];
+    T klo[HIP_MAX_EDGES];
 };
 
 // One catalog of a batched power-spectrum launch (device-resident descriptor).
@@ -72,6 +125,19 @@ cudaError_t hip_build_cells(const float *pos, const float *w, int64_t N, double 
 
 cudaError_t hip_upload_coeffs_power();
 cudaError_t hip_upload_coeffs_bispec();
+cudaError_t hip_upload_coeffs_pairs_f32_lin();
+cudaError_t hip_upload_coeffs_pairs_f32_gen();
+cudaError_t hip_upload_coeffs_pairs_f64();
+cudaError_t hip_upload_coeffs_pairs_batched();
+void hip_pairs_launch_f32_lin(const CellList<float> &cl, const PowerKernelArgs &a, const EdgeTable<float> &ed,
+                              int n_ell, float R0, float dhi, float dlo, int grid, cudaStream_t st);
+void hip_pairs_launch_f32_gen(const CellList<float> &cl, const PowerKernelArgs &a, const EdgeTable<float> &ed,
+                              int n_ell, float R0, float dhi, float dlo, int grid, cudaStream_t st);
+void hip_pairs_launch_f64(bool lin, const CellList<double> &cl, const PowerKernelArgs &a,
+                          const EdgeTable<double> &ed, int n_ell, double R0, double dhi, double dlo, int grid,
+                          cudaStream_t st);
+int hip_pairs_blocks_per_sm_f32();
+int hip_pairs_blocks_per_sm_f64();
 
 // Pair pass of the power spectrum; K = real type (float: mixed, double: plain).
 template <typename T>

@@ -128,7 +128,7 @@ extern "C" hip_status hip_power_noalloc(const float *pos, const float *w, int64_
     // the pair counter and the work counter start at zero on every call
     HIP_NA_CK(cudaMemsetAsync(npairs, 0, sizeof(unsigned long long), st), "clear pair count");
     HIP_NA_CK(cudaMemsetAsync(counter, 0, sizeof(int), st), "clear work counter");
-    CellList<float> cl{x, y, z, (const float *)(b + o_ws), idx, cstart, n_c, (float)(L / n_c)};
+    CellList<float> cl{x, y, z, (const float *)(b + o_ws), idx, cstart, n_c, L, L / n_c};
     PowerKernelArgs ka;
     ka.n_e = n_e;
     ka.los = los_axis;

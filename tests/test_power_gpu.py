@@ -101,6 +101,19 @@ def test_bin_chunks_parity(prec, nk, kmax):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_inexact_cell_side_large_arguments(prec):
+    # L / n_c = 19.46 is no float, and r k reaches 17.3 * 14 = 242: the cell
+    # offsets and the FP32 arguments r k must both stay exact to ~1e-7.
+    pos, w = catalogs.thomas(2000, 97.3, 50, 2.0, seed=34, background_frac=0.2, weights="u05_15")
+    L, R0 = 97.3, 17.3
+    edges = catalogs.linear_edges(0.5, 14.0, 200)
+    Pref, _, nref, _ = _oracle_P("inexact_cs", pos, w, L, R0, edges)
+    P, _, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, prec)
+    _same_count(prec, npairs, nref)
+    assert _err(P, Pref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_nonlinear_edges_and_los_axes(prec):
     pos, w = catalogs.thomas(2000, 50.0, 50, 1.5, seed=33, los_sigma=2.0, weights="u05_15")
     L, R0 = 50.0, 11.0
