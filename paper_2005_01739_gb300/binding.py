@@ -85,6 +85,8 @@ def load(path: str | None = None):
         L.hip_last_error.argtypes = []
         L.hip_debug_F.restype = d
         L.hip_debug_F.argtypes = [i, i, d]
+        L.hip_debug_D.restype = d
+        L.hip_debug_D.argtypes = [i, i, d]
         L.hip_debug_F_array.restype = None
         L.hip_debug_F_array.argtypes = [i, i, P, P, i64]
         L.hip_set_profiling.restype = None
@@ -292,6 +294,14 @@ def hip_bispectrum_partial(pos, w, rand_pos, L, R0, k_edges, lmax=4, prec="mixed
 def debug_F(prec: str, l: int, u: float) -> float:
     """Host evaluation of the kernels' F_l(u) = D_l(u)/u^3 (same source and tables)."""
     return load().hip_debug_F(PREC[prec], int(l), float(u))
+
+
+def debug_D(variant: str, l: int, u: float) -> float:
+    """D_l(u) = u^3 F_l(u) as the FP32 pair kernels evaluate it (host build of the same
+    code); variant "series", "fit" (closed form, fitted Si auxiliaries) or "asym"
+    (closed form, asymptotic auxiliaries).  sin u and cos u are passed in correctly
+    rounded, so the result isolates the D-form arithmetic."""
+    return load().hip_debug_D({"series": 0, "fit": 1, "asym": 2}[variant], int(l), float(u))
 
 
 def debug_F_array(prec: str, l: int, u) -> np.ndarray:

@@ -517,6 +517,27 @@ extern "C" double hip_debug_F(int prec, int l, double u)
     return F[l];
 }
 
+// D_l(u) = u^3 F_l(u) as the FP32 pair kernels evaluate it (host build of the
+// same code): variant 0 = series, 1 = closed form with fitted Si auxiliaries,
+// 2 = closed form with asymptotic auxiliaries.
+extern "C" double hip_debug_D(int variant, int l, double u)
+{
+    if (l < 0 || l > HIP_LMAX || variant < 0 || variant > 2) return NAN;
+    const HipCoeffs &C = hip_host_coeffs();
+    const float uf = (float)u;
+    float D[5] = {0, 0, 0, 0, 0};
+    if (variant == 0) {
+        hip_D_f32_series<31>(uf, C, D);
+    } else {
+        const float s = (float)std::sin((double)uf), c = (float)std::cos((double)uf);
+        if (variant == 1)
+            hip_D_f32_closed<31, false>(uf, 1.0f / uf, s, c, C, D);
+        else
+            hip_D_f32_closed<31, true>(uf, 1.0f / uf, s, c, C, D);
+    }
+    return (double)D[l];
+}
+
 // Vector form of hip_debug_F: out[i] = F_l(u[i]).
 extern "C" void hip_debug_F_array(int prec, int l, const double *u, double *out, int64_t n)
 {

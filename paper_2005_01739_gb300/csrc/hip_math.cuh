@@ -33,6 +33,7 @@
 #define HIP_F32_NSER 15        // Taylor terms of F_l in x = u^2 (u < 6)
 #define HIP_F32_NSERLO 9       // terms of the low-half coefficient chain
 #define HIP_F32_SIDEG 8        // degree of the u f(u), u^2 g(u) fits in t = (6/u)^2
+#define HIP_F32_UASYM 24.0f    // FP32: asymptotic f, g (four terms each) when u >= this
 
 #define HIP_F64_USMALL 2.5     // FP64: series below
 #define HIP_F64_USI 12.0       // FP64: Si by its power series below, fitted auxiliaries above
@@ -159,6 +160,74 @@ __host__ __device__ __forceinline__ void hip_F_f32_closed(float u, float s, floa
     if (MASK & 4) Fm[2] = fmaf(w3, fmaf(3.0f, si, -4.0f * s), w2 * c);
     if (MASK & 8) Fm[3] = fmaf(w2, s, w3 * fmaf(7.0f, c, 8.0f - 15.0f * w * s));
     if (MASK & 16) Fm[4] = fmaf(w3, fmaf(fmaf(-52.5f, w2, 11.0f), s, 7.5f * si), w2 * fmaf(52.5f, w2, -1.0f) * c);
+}
+
+// ----------------------------------------------------- D_l (FP32 pair path) ---
+// The FP32 pair kernels accumulate omega D_l(r k_e) / r^3 = omega k_e^3 F_l(r k_e)
+// per edge, so the closed forms are used without their 1/u^3 factor.
+//
+// Closed forms given s = sin u, c = cos u (u >= HIP_F32_USMALL).  Si(u) =
+// pi/2 - f(u) cos u - g(u) sin u with the auxiliary functions f, g either from
+// the fits used by hip_F_f32_closed (any u >= 6) or, when ASYM, from the first
+// four terms of their asymptotic series,
+//     f = (1/u) (1 - 2!/u^2 + 4!/u^4 - 6!/u^6),  g = (1/u^2) (1 - 3!/u^2 + 5!/u^4 - 7!/u^6),
+// whose remainders are below the first omitted terms 8!/u^9 and 9!/u^10:
+// 1.5e-8 and 6e-9 at u = 24, against |D_l| ~ u.
+//
+// w is 1/u as the caller has it (the pair kernels form it as (1/r)(1/k_e)).
+template <int MASK, bool ASYM>
+__host__ __device__ __forceinline__ void hip_D_f32_closed(float u, float w, float s, float c, const HipCoeffs &C,
+                                                          float *D)
+{
+    float w2 = 0.0f, si = 0.0f;
+    if (MASK & ((1 << 2) | (1 << 3) | (1 << 4))) w2 = w * w;
+    if (MASK & ((1 << 2) | (1 << 4))) {
+        float pf, pg;
+        if (ASYM) {
+            pf = fmaf(fmaf(fmaf(-720.0f, w2, 24.0f), w2, -2.0f), w2, 1.0f);
+            pg = fmaf(fmaf(fmaf(-5040.0f, w2, 120.0f), w2, -6.0f), w2, 1.0f);
+        } else {
+            const float t = 36.0f * w2;
+            pf = C.sif32[HIP_F32_SIDEG];
+            pg = C.sig32[HIP_F32_SIDEG];
+#pragma unroll
+            for (int q = HIP_F32_SIDEG - 1; q >= 0; --q) {
+                pf = fmaf(pf, t, C.sif32[q]);
+                pg = fmaf(pg, t, C.sig32[q]);
+            }
+        }
+        // Si = pi/2 - f cos - g sin, f = w pf, g = w^2 pg
+        si = HIP_HALF_PI_F - fmaf(w, fmaf(pf, c, w * pg * s), -HIP_HALF_PI_F_LO);
+    }
+    if (MASK & 1) D[0] = fmaf(-u, c, s);
+    if (MASK & 2) D[1] = fmaf(-u, s, 2.0f - 2.0f * c);
+    if (MASK & 4) D[2] = fmaf(u, c, fmaf(3.0f, si, -4.0f * s));
+    if (MASK & 8) D[3] = fmaf(fmaf(-15.0f, w, u), s, fmaf(7.0f, c, 8.0f));
+    if (MASK & 16) D[4] = fmaf(fmaf(-52.5f, w2, 11.0f), s, fmaf(fmaf(52.5f, w, -u), c, 7.5f * si));
+}
+
+// Series below HIP_F32_USMALL: D_l = u^(3 + l) (c_l0 + x P_l(x) + low-half chain),
+// x = u^2.  The constant's low half rides in the low chain, so that the 1/3 of
+// D_0 is not rounded to a float once for every pair.
+template <int MASK>
+__host__ __device__ __forceinline__ void hip_D_f32_series(float u, const HipCoeffs &C, float *D)
+{
+    const float x = u * u;
+    const float u3 = x * u;
+#pragma unroll
+    for (int l = 0; l <= HIP_LMAX; ++l) {
+        if (!(MASK & (1 << l))) continue;
+        float acc = C.ser32[l][HIP_F32_NSER - 1];
+#pragma unroll
+        for (int s = HIP_F32_NSER - 2; s >= 1; --s) acc = fmaf(acc, x, C.ser32[l][s]);
+        float cor = C.ser32lo[l][HIP_F32_NSERLO - 1];
+#pragma unroll
+        for (int s = HIP_F32_NSERLO - 2; s >= 0; --s) cor = fmaf(cor, x, C.ser32lo[l][s]);
+        float ul = u3;
+#pragma unroll
+        for (int q = 0; q < l; ++q) ul *= u;
+        D[l] = (fmaf(acc, x, C.ser32[l][0]) + cor) * ul;
+    }
 }
 
 template <int MASK>

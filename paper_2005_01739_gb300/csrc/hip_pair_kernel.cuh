@@ -34,10 +34,24 @@ cudaError_t HIP_PAIR_UPLOAD()
 // ------------------------------------------------------------- pair pass -----
 #define HIP_WTILE 64
 #define HIP_QCAP 64
+#define HIP_SQCAP 64
+
+// Series queue of the FP32 pass (empty for FP64): (u, pair slot, edge) of the
+// lanes whose argument is below HIP_F32_USMALL, evaluated 32 at a time one per
+// lane, and the per-edge FP32 sums they feed (folded to FP64 with each drain).
+template <typename T, int NCH>
+struct SeriesQueue {
+};
+template <int NCH>
+struct SeriesQueue<float, NCH> {
+    float u[HIP_SQCAP];
+    unsigned char q[HIP_SQCAP], e[HIP_SQCAP];
+    float acc[3][HIP_MAX_EDGES];
+};
 
 // Shared memory of one warp: a tile of the home cell, a tile of the shifted
 // neighbour cell, and the queue of accepted pairs awaiting the bin pass.
-template <typename T>
+template <typename T, int NCH>
 struct WarpSmem {
     T hx[HIP_WTILE], hy[HIP_WTILE], hz[HIP_WTILE];
     float hw[HIP_WTILE];
@@ -46,83 +60,15 @@ struct WarpSmem {
     float nw[HIP_WTILE];
     int nin[HIP_WTILE];
     T qr[HIP_QCAP], qrl[HIP_QCAP];  // separation r = qr + qrl (qrl: FP32 low part, 0 for FP64)
-    T qo[3][HIP_QCAP];             // omega L_l(mu), l = 0, 2, 4
+    T qo[3][HIP_QCAP];             // omega L_l(mu), l = 0, 2, 4 (FP32: divided by r^3)
     T qc[HIP_QCAP], qs[HIP_QCAP];  // cos, sin of 32 r dk: rotation between 32-edge chunks
+    SeriesQueue<T, NCH> sq;
 };
 
 static __constant__ int c_shift[HIP_NSHIFT][3] = {{0, 0, 0},  {1, -1, -1}, {1, -1, 0}, {1, -1, 1}, {1, 0, -1},
                                            {1, 0, 0},  {1, 0, 1},   {1, 1, -1}, {1, 1, 0},  {1, 1, 1},
                                            {0, 1, -1}, {0, 1, 0},   {0, 1, 1},  {0, 0, 1}};
 
-
-// Bin pass over the n queued pairs of a warp: lanes over bin edges (edge
-// lane + 32 t in chunk t), pairs broadcast.  sin/cos of u = r k_e come from one
-// accurate sincos in chunk 0 and, for uniformly spaced edges, a rotation by the
-// pair's 32 r dk for every later chunk.  When the last used chunk (index tl)
-// holds tw <= 16 edges it is "packed": lane l handles edge 32 tl + l % tw of
-// pair q0 + l / tw, so 32 / tw pairs share one pass instead of leaving most
-// lanes idle.
-__device__ __forceinline__ void hip_edge_acc(float u, float ul, float s, float c, bool need_sc, float o0, float o2,
-                                             float o4, int mask, float &H0, float &H2, float &H4, float &C0,
-                                             float &C2, float &C4)
-{
-    float Fm[5], Fc[5];
-    if (u < HIP_F32_USMALL) {
-        if (mask & 16)
-            hip_F_f32_series<21>(u, c_coeffs, Fm, Fc);
-        else if (mask & 4)
-            hip_F_f32_series<5>(u, c_coeffs, Fm, Fc);
-        else
-            hip_F_f32_series<1>(u, c_coeffs, Fm, Fc);
-        H0 = fmaf(o0, c_coeffs.ser32[0][0], H0);
-        C0 = fmaf(o0, Fc[0], C0);
-        if (mask & 4) C2 = fmaf(o2, Fc[2], C2);
-        if (mask & 16) C4 = fmaf(o4, Fc[4], C4);
-    } else {
-        if (need_sc) {
-            // sin, cos of u + ul: first order in the low part ul (|ul| <~ 1e-5)
-            float s0, c0;
-            sincosf(u, &s0, &c0);
-            s = fmaf(c0, ul, s0);
-            c = fmaf(-s0, ul, c0);
-        }
-        if (mask & 16)
-            hip_F_f32_closed<21>(u, s, c, c_coeffs, Fm);
-        else if (mask & 4)
-            hip_F_f32_closed<5>(u, s, c, c_coeffs, Fm);
-        else
-            hip_F_f32_closed<1>(u, s, c, c_coeffs, Fm);
-    }
-    H0 = fmaf(o0, Fm[0], H0);
-    if (mask & 4) H2 = fmaf(o2, Fm[2], H2);
-    if (mask & 16) H4 = fmaf(o4, Fm[4], H4);
-}
-
-__device__ __forceinline__ void hip_edge_acc(double u, double, double s, double c, bool need_sc, double o0,
-                                             double o2, double o4, int mask, double &H0, double &H2, double &H4, double &,
-                                             double &, double &)
-{
-    double F[5];
-    if (u < HIP_F64_USMALL) {
-        if (mask & 16)
-            hip_F_f64_series<21>(u, c_coeffs, F);
-        else if (mask & 4)
-            hip_F_f64_series<5>(u, c_coeffs, F);
-        else
-            hip_F_f64_series<1>(u, c_coeffs, F);
-    } else {
-        if (need_sc) sincos(u, &s, &c);
-        if (mask & 16)
-            hip_F_f64_closed<21>(u, s, c, c_coeffs, F);
-        else if (mask & 4)
-            hip_F_f64_closed<5>(u, s, c, c_coeffs, F);
-        else
-            hip_F_f64_closed<1>(u, s, c, c_coeffs, F);
-    }
-    H0 = fma(o0, F[0], H0);
-    if (mask & 4) H2 = fma(o2, F[2], H2);
-    if (mask & 16) H4 = fma(o4, F[4], H4);
-}
 
 __device__ __forceinline__ float hip_arg(float r, float khi, float klo) { return fmaf(r, khi, r * klo); }
 __device__ __forceinline__ double hip_arg(double r, double khi, double) { return r * khi; }
@@ -161,19 +107,100 @@ __device__ __forceinline__ int hip_lane_edge(int lane, int t, int n_e, int tl, i
     return (t <= tl && e < n_e) ? e : -1;
 }
 
-template <typename T, int NCH, int MASK>
-__device__ __forceinline__ void hip_drain(const WarpSmem<T> &sm, int n, const T *kk, const T *kl, int lane, int n_e,
-                                          bool LIN, int tl, int tw, T (&H)[3][NCH], T (&Hc)[3][NCH])
+// Bin pass over the n queued pairs of a warp: lanes over bin edges (edge
+// lane + 32 t in chunk t), pairs broadcast.  sin/cos of u = r k_e come from one
+// accurate sincos in chunk 0 and, for uniformly spaced edges, a rotation by the
+// pair's 32 r dk for every later chunk.  When the last used chunk (index tl)
+// holds tw <= 16 edges it is "packed": lane l handles edge 32 tl + l % tw of
+// pair q0 + l / tw, so 32 / tw pairs share one pass instead of leaving most
+// lanes idle.
+//
+// FP32: every lane accumulates omega_l D_l(u) / r^3 (the weights in the queue
+// are already divided by r^3).  Lanes whose u is below HIP_F32_USMALL do not
+// branch into the series: they append (u, pair, edge) to the series queue, which
+// is evaluated 32 entries at a time, one entry per lane.  The closed forms take
+// the asymptotic Si auxiliaries when every closed-form lane of the warp has
+// u >= HIP_F32_UASYM (a warp-uniform choice) and the fitted ones otherwise.
+template <int NCH, int MASK>
+__device__ __forceinline__ void hip_series_eval(WarpSmem<float, NCH> &sm, int n, int lane)
 {
+    if (lane < n) {
+        const float u = sm.sq.u[lane];
+        const int q = sm.sq.q[lane], e = sm.sq.e[lane];
+        float D[5];
+        hip_D_f32_series<MASK>(u, c_coeffs, D);
+        atomicAdd(&sm.sq.acc[0][e], sm.qo[0][q] * D[0]);
+        if (MASK & 4) atomicAdd(&sm.sq.acc[1][e], sm.qo[1][q] * D[2]);
+        if (MASK & 16) atomicAdd(&sm.sq.acc[2][e], sm.qo[2][q] * D[4]);
+    }
+}
+
+template <int NCH, int MASK>
+__device__ __forceinline__ void hip_series_push(WarpSmem<float, NCH> &sm, int &sn, bool need, float u, int q, int e,
+                                                int lane)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (m == 0u) return;
+    if (need) {
+        const int slot = sn + __popc(m & ((1u << lane) - 1u));
+        sm.sq.u[slot] = u;
+        sm.sq.q[slot] = (unsigned char)q;
+        sm.sq.e[slot] = (unsigned char)e;
+    }
+    sn += __popc(m);  // < HIP_SQCAP: sn was < 32 before this push
+    if (sn >= 32) {
+        __syncwarp();
+        hip_series_eval<NCH, MASK>(sm, 32, lane);
+        const int rest = sn - 32;
+        float mu = 0.0f;
+        int mq = 0, me = 0;
+        if (lane < rest) {
+            mu = sm.sq.u[32 + lane];
+            mq = sm.sq.q[32 + lane];
+            me = sm.sq.e[32 + lane];
+        }
+        __syncwarp();
+        if (lane < rest) {
+            sm.sq.u[lane] = mu;
+            sm.sq.q[lane] = (unsigned char)mq;
+            sm.sq.e[lane] = (unsigned char)me;
+        }
+        sn = rest;
+        __syncwarp();
+    }
+}
+
+template <int MASK>
+__device__ __forceinline__ void hip_closed_acc(float u, float w, float s, float c, bool asym, float o0, float o2,
+                                               float o4, float &H0, float &H2, float &H4)
+{
+    float D[5];
+    if (asym)
+        hip_D_f32_closed<MASK, true>(u, w, s, c, c_coeffs, D);
+    else
+        hip_D_f32_closed<MASK, false>(u, w, s, c, c_coeffs, D);
+    H0 = fmaf(o0, D[0], H0);
+    if (MASK & 4) H2 = fmaf(o2, D[2], H2);
+    if (MASK & 16) H4 = fmaf(o4, D[4], H4);
+}
+
+template <int NCH, int MASK>
+__device__ __forceinline__ void hip_drain(WarpSmem<float, NCH> &sm, int n, const float *kk, const float *kl,
+                                          const float *, int lane, int n_e, bool LIN, int tl, int tw,
+                                          float (&H)[3][NCH])
+{
+    int sn = 0;
     for (int q = 0; q < n; ++q) {
-        const T r = sm.qr[q], rl = sm.qrl[q];
-        const T o0 = sm.qo[0][q], o2 = sm.qo[1][q], o4 = sm.qo[2][q];
-        const T rc = sm.qc[q], rs = sm.qs[q];
-        T s = T(0), c = T(1);
+        const float r = sm.qr[q], rl = sm.qrl[q];
+        const float o0 = sm.qo[0][q], o2 = sm.qo[1][q], o4 = sm.qo[2][q];
+        const float rc = sm.qc[q], rs = sm.qs[q];
+        float s = 0.0f, c = 1.0f;
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
             if (t < tl || (t == tl && tw == 0)) {
-                T u, ul = T(0);
+                const int e = lane + 32 * t;
+                const bool act = e < n_e;
+                float u, ul = 0.0f;
                 if (t == 0 || !LIN) {
                     hip_arg2(r, rl, kk[t], kl[t], u, ul);
                 } else {
@@ -183,14 +210,104 @@ __device__ __forceinline__ void hip_drain(const WarpSmem<T> &sm, int n, const T 
                     if (t == 0) {
                         hip_sincos2(u, ul, &s, &c);
                     } else {
-                        const T s2 = fma(s, rc, c * rs);
+                        const float s2 = fmaf(s, rc, c * rs);
+                        c = fmaf(c, rc, -s * rs);
+                        s = s2;
+                    }
+                }
+                const bool ser = act && u < HIP_F32_USMALL;
+                hip_series_push<NCH, MASK>(sm, sn, ser, u, q, e, lane);
+                const bool clo = act && !ser;
+                const bool asym = __all_sync(0xffffffffu, !clo || u >= HIP_F32_UASYM);
+                if (clo) {
+                    if (!LIN) hip_sincos2(u, ul, &s, &c);
+                    hip_closed_acc<MASK>(u, __fdividef(1.0f, u), s, c, asym, o0, o2, o4, H[0][t], H[1][t], H[2][t]);
+                }
+            }
+        }
+    }
+    if (tw > 0) {
+        const int per = 32 / tw, sub = lane / tw;
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+            if (t != tl) continue;
+            const int e = 32 * tl + lane % tw;
+            for (int q0 = 0; q0 < n; q0 += per) {
+                const int q = q0 + sub;
+                const bool act = sub < per && q < n;
+                float u = 0.0f, ul = 0.0f;
+                if (act) hip_arg2(sm.qr[q], sm.qrl[q], kk[t], kl[t], u, ul);
+                const bool ser = act && u < HIP_F32_USMALL;
+                hip_series_push<NCH, MASK>(sm, sn, ser, u, q, e, lane);
+                const bool clo = act && !ser;
+                const bool asym = __all_sync(0xffffffffu, !clo || u >= HIP_F32_UASYM);
+                if (clo) {
+                    float s, c;
+                    hip_sincos2(u, ul, &s, &c);
+                    hip_closed_acc<MASK>(u, __fdividef(1.0f, u), s, c, asym, sm.qo[0][q], sm.qo[1][q], sm.qo[2][q],
+                                         H[0][t], H[1][t], H[2][t]);
+                }
+            }
+        }
+    }
+    if (sn > 0) {
+        __syncwarp();
+        hip_series_eval<NCH, MASK>(sm, sn, lane);
+    }
+}
+
+// FP64: the series / closed-form branch is taken per lane; every lane
+// accumulates omega_l k_e^3 F_l(u).
+__device__ __forceinline__ void hip_edge_acc64(double u, double k3, double s, double c, bool need_sc, double o0,
+                                               double o2, double o4, int mask, double &H0, double &H2, double &H4)
+{
+    double F[5];
+    if (u < HIP_F64_USMALL) {
+        if (mask & 16)
+            hip_F_f64_series<21>(u, c_coeffs, F);
+        else if (mask & 4)
+            hip_F_f64_series<5>(u, c_coeffs, F);
+        else
+            hip_F_f64_series<1>(u, c_coeffs, F);
+    } else {
+        if (need_sc) sincos(u, &s, &c);
+        if (mask & 16)
+            hip_F_f64_closed<21>(u, s, c, c_coeffs, F);
+        else if (mask & 4)
+            hip_F_f64_closed<5>(u, s, c, c_coeffs, F);
+        else
+            hip_F_f64_closed<1>(u, s, c, c_coeffs, F);
+    }
+    H0 = fma(o0 * k3, F[0], H0);
+    if (mask & 4) H2 = fma(o2 * k3, F[2], H2);
+    if (mask & 16) H4 = fma(o4 * k3, F[4], H4);
+}
+
+template <int NCH, int MASK>
+__device__ __forceinline__ void hip_drain(WarpSmem<double, NCH> &sm, int n, const double *kk, const double *,
+                                          const double *k3, int lane, int n_e, bool LIN, int tl, int tw,
+                                          double (&H)[3][NCH])
+{
+    for (int q = 0; q < n; ++q) {
+        const double r = sm.qr[q];
+        const double o0 = sm.qo[0][q], o2 = sm.qo[1][q], o4 = sm.qo[2][q];
+        const double rc = sm.qc[q], rs = sm.qs[q];
+        double s = 0.0, c = 1.0;
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+            if (t < tl || (t == tl && tw == 0)) {
+                const double u = r * kk[t];
+                if (LIN) {
+                    if (t == 0) {
+                        sincos(u, &s, &c);
+                    } else {
+                        const double s2 = fma(s, rc, c * rs);
                         c = fma(c, rc, -s * rs);
                         s = s2;
                     }
                 }
                 if (lane + 32 * t < n_e)
-                    hip_edge_acc(u, ul, s, c, !LIN, o0, o2, o4, MASK, H[0][t], H[1][t], H[2][t], Hc[0][t], Hc[1][t],
-                                 Hc[2][t]);
+                    hip_edge_acc64(u, k3[t], s, c, !LIN, o0, o2, o4, MASK, H[0][t], H[1][t], H[2][t]);
             }
         }
     }
@@ -201,12 +318,9 @@ __device__ __forceinline__ void hip_drain(const WarpSmem<T> &sm, int n, const T 
             if (t != tl) continue;
             for (int q0 = 0; q0 < n; q0 += per) {
                 const int q = q0 + sub;
-                if (sub < per && q < n) {
-                    T u, ul;
-                    hip_arg2(sm.qr[q], sm.qrl[q], kk[t], kl[t], u, ul);
-                    hip_edge_acc(u, ul, T(0), T(1), true, sm.qo[0][q], sm.qo[1][q], sm.qo[2][q], MASK, H[0][t],
-                                 H[1][t], H[2][t], Hc[0][t], Hc[1][t], Hc[2][t]);
-                }
+                if (sub < per && q < n)
+                    hip_edge_acc64(sm.qr[q] * kk[t], k3[t], 0.0, 1.0, true, sm.qo[0][q], sm.qo[1][q], sm.qo[2][q],
+                                   MASK, H[0][t], H[1][t], H[2][t]);
             }
         }
     }
@@ -265,35 +379,95 @@ __device__ __forceinline__ void hip_pair_sep(double, double, double, double, dou
     *rl = 0.0;
 }
 
-// Drain a warp's queue and fold the FP32 register sums into the FP64 ones.
+// Drain a warp's queue and fold the register sums (and, for FP32, the series
+// sums in shared memory) into the FP64 registers.
+template <int NCH>
+__device__ __forceinline__ void hip_fold_series(WarpSmem<float, NCH> &sm, int lane, int n_e, int tl, double (&R)[3][NCH])
+{
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+        const int e = lane + 32 * t;
+        if (t <= tl && e < n_e) {
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                R[l][t] += (double)sm.sq.acc[l][e];
+                sm.sq.acc[l][e] = 0.0f;
+            }
+        }
+    }
+}
+template <int NCH>
+__device__ __forceinline__ void hip_fold_series(WarpSmem<double, NCH> &, int, int, int, double (&)[3][NCH])
+{
+}
+
+// kx: per-lane k_e^3 (FP64 path; unused by the FP32 path).
 template <typename T, int NCH, int MASK>
-__device__ __forceinline__ void hip_drain_fold(const WarpSmem<T> &sm, int &qn, const T *kk, const T *kl, int lane,
-                                               int n_e, bool lin, int tl, int tw, T (&H)[3][NCH], T (&Hc)[3][NCH],
+__device__ __forceinline__ void hip_drain_fold(WarpSmem<T, NCH> &sm, int &qn, const T *kk, const T *kl, const T *kx,
+                                               int lane, int n_e, bool lin, int tl, int tw, T (&H)[3][NCH],
                                                double (&R)[3][NCH])
 {
     __syncwarp();
-    hip_drain<T, NCH, MASK>(sm, qn, kk, kl, lane, n_e, lin, tl, tw, H, Hc);
+    hip_drain<NCH, MASK>(sm, qn, kk, kl, kx, lane, n_e, lin, tl, tw, H);
+    __syncwarp();
 #pragma unroll
     for (int l = 0; l < 3; ++l)
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
-            R[l][t] += (double)H[l][t] + (double)Hc[l][t];
+            R[l][t] += (double)H[l][t];
             H[l][t] = T(0);
-            Hc[l][t] = T(0);
         }
+    hip_fold_series<NCH>(sm, lane, n_e, tl, R);
     qn = 0;
     __syncwarp();
 }
+
+// Per-lane edge constants: the edge as khi + klo and kx = k_e^3 (FP64 path).
+__device__ __forceinline__ float hip_kx(float, float) { return 0.0f; }
+__device__ __forceinline__ double hip_kx(double k, double) { return k * k * k; }
+
+template <typename T, int NCH>
+__device__ __forceinline__ void hip_lane_edges(const T *k, const T *klo, int lane, int n_e, int tl, int tw, T (&kk)[NCH],
+                                               T (&kl)[NCH], T (&kx)[NCH])
+{
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+        const int e = hip_lane_edge(lane, t, n_e, tl, tw);
+        kk[t] = e >= 0 ? k[e] : T(0);
+        kl[t] = e >= 0 ? klo[e] : T(0);
+        kx[t] = hip_kx(kk[t], kl[t]);
+    }
+}
+
+// Zero the series sums of a warp (FP32) before its first item.
+template <int NCH>
+__device__ __forceinline__ void hip_series_clear(WarpSmem<float, NCH> &sm, int lane)
+{
+    for (int i = lane; i < 3 * HIP_MAX_EDGES; i += 32) (&sm.sq.acc[0][0])[i] = 0.0f;
+    __syncwarp();
+}
+template <int NCH>
+__device__ __forceinline__ void hip_series_clear(WarpSmem<double, NCH> &, int)
+{
+}
+
+// Weight of a queued pair: omega L_l(mu), divided by r^3 on the FP32 path
+// (which accumulates D_l(r k) / r^3 = k^3 F_l(r k)).
+__device__ __forceinline__ float hip_qscale(float r)
+{
+    const float ir = 1.0f / r;
+    return ir * ir * ir;
+}
+__device__ __forceinline__ double hip_qscale(double) { return 1.0; }
 
 // One work item (home cell, half-shell shift) of one catalog, processed by one
 // warp: stage 64-particle tiles of both cells in the warp's shared memory, test
 // candidates one per lane, queue accepted pairs, drain the queue at 32 pairs.
 template <typename T, int NCH, int MASK>
 __device__ __forceinline__ void hip_pair_item(const CellList<T> &cl, int item, long long p0, long long p1, int los,
-                                              T R0sq, T invR0, bool lin, T dk32hi, T dk32lo, WarpSmem<T> &sm,
-                                              int lane, const T *kk, const T *kl, int n_e, int tl, int tw,
-                                              T (&H)[3][NCH],
-                                              T (&Hc)[3][NCH], double (&R)[3][NCH], int &qn,
+                                              T R0sq, T invR0, bool lin, T dk32hi, T dk32lo, WarpSmem<T, NCH> &sm,
+                                              int lane, const T *kk, const T *kl, const T *kx, int n_e, int tl,
+                                              int tw, T (&H)[3][NCH], double (&R)[3][NCH], int &qn,
                                               unsigned long long &cnt)
 {
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -363,7 +537,7 @@ __device__ __forceinline__ void hip_pair_item(const CellList<T> &cl, int item, l
                         const T mu = dl / r;
                         T l2, l4;
                         hip_legendre24<T>(mu, l2, l4);
-                        const T om = T(wi) * T(sm.nw[jl]) * hip_W<T>(r * invR0) * T(mult);
+                        const T om = T(wi) * T(sm.nw[jl]) * hip_W<T>(r * invR0) * T(mult) * hip_qscale(r);
                         const int slot = qn + __popc(m & lt_mask);
                         sm.qr[slot] = r;
                         sm.qrl[slot] = rl;
@@ -379,7 +553,8 @@ __device__ __forceinline__ void hip_pair_item(const CellList<T> &cl, int item, l
                         cnt += (unsigned long long)mult;
                     }
                     qn += __popc(m);
-                    if (qn >= 32) hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, lane, n_e, lin, tl, tw, H, Hc, R);
+                    if (qn >= 32)
+                        hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, kx, lane, n_e, lin, tl, tw, H, R);
                 }
             }
         }
@@ -395,32 +570,31 @@ template <typename T, int NCH, int MASK, bool LIN>
 __global__ void __launch_bounds__(HIP_PAIR_THREADS)
     k_power_pairs(CellList<T> cl, PowerKernelArgs a, EdgeTable<T> ed, T R0, T dk32hi, T dk32lo)
 {
-    __shared__ WarpSmem<T> smem[HIP_PAIR_WARPS];
+    __shared__ WarpSmem<T, NCH> smem[HIP_PAIR_WARPS];
     __shared__ double red[3][HIP_MAX_EDGES];
+    __shared__ int done;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSmem<T> &sm = smem[warp];
+    WarpSmem<T, NCH> &sm = smem[warp];
+    for (int i = threadIdx.x; i < 3 * HIP_MAX_EDGES; i += HIP_PAIR_THREADS) (&red[0][0])[i] = 0.0;
+    if (threadIdx.x == 0) done = 0;
+    __syncthreads();
     const T R0sq = R0 * R0, invR0 = T(1) / R0;
     const int n_e = a.n_e;
     const int n_ell = (MASK & 16) ? 3 : ((MASK & 4) ? 2 : 1);
     const int tl = (n_e - 1) / 32, tw = (n_e - 32 * tl <= 16) ? n_e - 32 * tl : 0;
 
-    T kk[NCH], kl[NCH];
-#pragma unroll
-    for (int t = 0; t < NCH; ++t) {
-        const int e = hip_lane_edge(lane, t, n_e, tl, tw);
-        kk[t] = e >= 0 ? ed.k[e] : T(0);
-        kl[t] = e >= 0 ? ed.klo[e] : T(0);
-    }
-    T H[3][NCH], Hc[3][NCH];
+    T kk[NCH], kl[NCH], kx[NCH];
+    hip_lane_edges<T, NCH>(ed.k, ed.klo, lane, n_e, tl, tw, kk, kl, kx);
+    T H[3][NCH];
     double R[3][NCH];
 #pragma unroll
     for (int l = 0; l < 3; ++l)
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
             H[l][t] = T(0);
-            Hc[l][t] = T(0);
             R[l][t] = 0.0;
         }
+    hip_series_clear(sm, lane);
     unsigned long long cnt = 0;
     int qn = 0;
     for (;;) {
@@ -429,11 +603,9 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.n_items) break;
         hip_pair_item<T, NCH, MASK>(cl, item, a.p0, a.p1, a.los, R0sq, invR0, LIN, dk32hi, dk32lo, sm, lane, kk, kl,
-                                    n_e, tl, tw, H, Hc, R, qn, cnt);
+                                    kx, n_e, tl, tw, H, R, qn, cnt);
     }
-    if (qn > 0) hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, lane, n_e, LIN, tl, tw, H, Hc, R);
-    // CTA reduction of the per-lane FP64 sums into one partial row.
-    for (int i = threadIdx.x; i < 3 * HIP_MAX_EDGES; i += HIP_PAIR_THREADS) (&red[0][0])[i] = 0.0;
+    if (qn > 0) hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, kx, lane, n_e, LIN, tl, tw, H, R);
     __syncthreads();
     for (int wv = 0; wv < HIP_PAIR_WARPS; ++wv) {
         if (warp == wv) {
@@ -442,7 +614,7 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
 #pragma unroll
                 for (int t = 0; t < NCH; ++t) {
                     const int e = hip_lane_edge(lane, t, n_e, tl, tw);
-                    if (e >= 0) atomicAdd(&red[l][e], R[l][t]);  // packed-tail lanes share edges
+                    if (e >= 0) atomicAdd(&red[l][e], R[l][t]);
                 }
         }
         __syncthreads();
@@ -465,25 +637,25 @@ template <typename T, int NCH>
 __global__ void __launch_bounds__(HIP_PAIR_THREADS)
     k_power_pairs_batched(const BatchCat<T> *__restrict__ cats, int n_cats, int n_items, int *work_counter)
 {
-    __shared__ WarpSmem<T> smem[HIP_PAIR_WARPS];
+    __shared__ WarpSmem<T, NCH> smem[HIP_PAIR_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSmem<T> &sm = smem[warp];
-    T kk[NCH], kl[NCH];
-    T H[3][NCH], Hc[3][NCH];
+    WarpSmem<T, NCH> &sm = smem[warp];
+    T kk[NCH], kl[NCH], kx[NCH];
+    T H[3][NCH];
     double R[3][NCH];
 #pragma unroll
     for (int l = 0; l < 3; ++l)
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
             H[l][t] = T(0);
-            Hc[l][t] = T(0);
             R[l][t] = 0.0;
         }
+    hip_series_clear(sm, lane);
     unsigned long long cnt = 0;
     int qn = 0, cur = -1, tl = 0, tw = 0;
     auto leave = [&](int c) {
         if (qn > 0)
-            hip_drain_fold<T, NCH, 21>(sm, qn, kk, kl, lane, cats[c].n_e, cats[c].lin != 0, tl, tw, H, Hc, R);
+            hip_drain_fold<T, NCH, 21>(sm, qn, kk, kl, kx, lane, cats[c].n_e, cats[c].lin != 0, tl, tw, H, R);
         const int ne = cats[c].n_e;
 #pragma unroll
         for (int l = 0; l < 3; ++l)
@@ -511,17 +683,12 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
             const int ne = cats[c].n_e;
             tl = (ne - 1) / 32;
             tw = (ne - 32 * tl <= 16) ? ne - 32 * tl : 0;
-#pragma unroll
-            for (int t = 0; t < NCH; ++t) {
-                const int e = hip_lane_edge(lane, t, ne, tl, tw);
-                kk[t] = e >= 0 ? cats[c].k[e] : T(0);
-                kl[t] = e >= 0 ? cats[c].klo[e] : T(0);
-            }
+            hip_lane_edges<T, NCH>(cats[c].k, cats[c].klo, lane, ne, tl, tw, kk, kl, kx);
         }
         const BatchCat<T> &bc = cats[c];
         hip_pair_item<T, NCH, 21>(bc.cl, item - bc.item_begin, bc.p0, bc.p1, bc.los, bc.R0 * bc.R0, T(1) / bc.R0,
-                                  bc.lin != 0, bc.dk32hi, bc.dk32lo, sm, lane, kk, kl, bc.n_e, tl, tw, H, Hc, R, qn,
-                                  cnt);
+                                  bc.lin != 0, bc.dk32hi, bc.dk32lo, sm, lane, kk, kl, kx, bc.n_e, tl, tw, H, R,
+                                  qn, cnt);
     }
     if (cur >= 0) leave(cur);
 }

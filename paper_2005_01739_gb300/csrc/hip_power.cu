@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(1024) k_power_final(FinalArgs f, const double 
     for (int i = threadIdx.x; i < n_ell * n_k; i += blockDim.x) {
         const int il = i / n_k, a = i - il * n_k;
         const double k3lo = f.k[a] * f.k[a] * f.k[a], k3hi = f.k[a + 1] * f.k[a + 1] * f.k[a + 1];
-        const double dd = 3.0 * (k3hi * H[il][a + 1] - k3lo * H[il][a]) / (k3hi - k3lo);
+        const double dd = 3.0 * (H[il][a + 1] - H[il][a]) / (k3hi - k3lo);
         const int l = 2 * il;
         const double sign = (il & 1) ? -1.0 : 1.0;
         double p = sign * (2.0 * l + 1.0) * dd / (nw * nw * V);
@@ -328,7 +328,7 @@ __global__ void k_power_final_batched(const FinalCat *__restrict__ cats)
     for (int i = threadIdx.x; i < f.n_ell * n_k; i += blockDim.x) {
         const int il = i / n_k, a = i - il * n_k;
         const double k3lo = f.k[a] * f.k[a] * f.k[a], k3hi = f.k[a + 1] * f.k[a + 1] * f.k[a + 1];
-        const double dd = 3.0 * (k3hi * f.acc[il * n_e + a + 1] - k3lo * f.acc[il * n_e + a]) / (k3hi - k3lo);
+        const double dd = 3.0 * (f.acc[il * n_e + a + 1] - f.acc[il * n_e + a]) / (k3hi - k3lo);
         const int l = 2 * il;
         double p = ((il & 1) ? -1.0 : 1.0) * (2.0 * l + 1.0) * dd / (nw * nw * V);
         if (il == 0) p -= f.Wt[a];

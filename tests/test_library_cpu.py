@@ -96,3 +96,21 @@ def test_kernel_F_fp32_error_budget(lib, l):
         env = 1.0 / 3.0 if u < 1 else 1.0 / u ** 2
         bound = env * (4e-6 + 1.2e-7 * u)
         assert abs(binding.debug_F("mixed", l, u) - ref) < bound, (l, u)
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant,lo,hi", [("series", 1e-4, 6.0), ("fit", 6.0, 3000.0), ("asym", 24.0, 3000.0)])
+def test_kernel_D_fp32_branches(lib, variant, lo, hi, l):
+    # D_l(u) = u^3 F_l(u) as the FP32 pair kernels accumulate it, each branch on
+    # its whole domain: the series below 6, the closed form with fitted Si
+    # auxiliaries (any u >= 6: the kernel uses it whenever a warp straddles
+    # u = 24) and with the four-term asymptotic auxiliaries (u >= 24).  sin and
+    # cos are correctly rounded here, so the bound is on the D-form arithmetic:
+    # a few FP32 ulps of the envelope u^3 (1/3 if u < 1 else 1/u^2), more for the
+    # alternating series near its upper end.
+    us = np.geomspace(lo, hi, 400) if variant == "series" else np.linspace(lo, hi, 600)
+    bound = 3e-6 if variant == "series" else 5e-7
+    for u in us:
+        uf = float(np.float32(u))
+        env = uf ** 3 * (1.0 / 3.0 if uf < 1 else 1.0 / uf ** 2)
+        assert abs(binding.debug_D(variant, l, uf) - oracle.dhat(l, uf)) < bound * env, (variant, l, uf)
