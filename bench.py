@@ -153,14 +153,32 @@ def oracle_sample(wl, seconds: float):
     m = 32
     while True:
         t0 = time.perf_counter()
-        _, npairs = oracle.power_pair_sum(pos, w, wl["L"], wl["R0"], wl["edges"], 4, 2, primaries=np.arange(m))
+        DD, npairs = oracle.power_pair_sum(pos, w, wl["L"], wl["R0"], wl["edges"], 4, 2, primaries=np.arange(m))
         dt = time.perf_counter() - t0
         if dt > 0.5 * seconds or m >= len(pos):
             break
         m = min(len(pos), max(2 * m, int(m * seconds / max(dt, 1e-3))))
     nk = len(wl["edges"]) - 1
     return {"value": npairs * nk / dt, "seconds": dt, "primaries": m, "ordered_pairs": npairs,
-            "cores": oracle.num_threads()}
+            "cores": oracle.num_threads(), "DD": DD}
+
+
+def sample_parity(binding, dpos, dw, wl, cpu):
+    """Error of the GPU paths on the oracle's sample (the same primaries), per
+    multipole: max over bins of |DD - DD_ref| / max(|DD_ref,l|, |DD_ref,0|,
+    1e-2 max |DD_ref,0|), the metric of the parity tests."""
+    ref = cpu["DD"]
+    floor = 1e-2 * np.max(np.abs(ref[0]))
+    scale = np.maximum(np.maximum(np.abs(ref), np.abs(ref[0])[None, :]), floor)
+    out = {}
+    for prec in ("mixed", "fp64"):
+        _, DD, _ = binding.hip_power(dpos, dw, wl["L"], wl["R0"], wl["edges"], 4, 2, prec,
+                                     prim_range=(0, cpu["primaries"]))
+        out[prec] = [float(x) for x in np.max(np.abs(DD - ref) / scale, axis=1)]
+    return {"metric": "max over k bins of |DD_l - DD_l,oracle| / max(|DD_l|, |DD_0|, 1e-2 max|DD_0|)",
+            "ell": [0, 2, 4], "mixed_max_rel_err": out["mixed"], "fp64_max_rel_err": out["fp64"],
+            "tolerance": {"mixed": 1e-5, "fp64": 1e-10},
+            "sample": f"the cpu_baseline sample: pair sums of the first {cpu['primaries']} primaries"}
 
 
 def bispectrum_rate(binding, stream, reps: int = 2, scale: float = 1.0):
@@ -377,6 +395,8 @@ def run_ours(args):
         "fp64_plain": fp64,
         "bispectrum": bisp,
     }
+    # after stage_ms is read: these calls replace the recorded stage times
+    line["parity"] = sample_parity(binding, dpos, dw, wl, cpu) if cpu else None
     if cpu:
         line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
                                 "sample": (f"FP64 brute force, ordered pair sums of the first {cpu['primaries']} "
