@@ -32,6 +32,10 @@ METRIC = "pairs×k-bins/s for P_ℓ(k), B_ℓ; mixed-prec batched vs FP64 GPU at
 UNIT = "pairs*kbins/s"
 WORKLOAD = "pk_mixed_n2e6"
 FLOPS_PER_PAIR_BIN = 12.0  # nominal algorithmic FP32 flops per (unordered pair, k bin)
+# DRAM bytes (read + write) of one pair-kernel launch on the 2e6-particle workload: ncu measured
+# 5.18 MB on the same workload shrunk to 2.5e5 particles (profiles/k_power_pairs_pk_mixed_scale0.125.md);
+# the traffic is the particle data read once, so it scales with N: x 8.
+PAIR_KERNEL_DRAM_BYTES = 5.18e6 * 8
 
 
 def _peaks():
@@ -384,7 +388,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_max},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_power_pairs<float,4,21>",
+                     "frac": achieved / peak, "traffic": PAIR_KERNEL_DRAM_BYTES, "kernel": "k_power_pairs<float,4,21>",
                      "kernel_ms": kern_ms, "flops_per_pair_bin": FLOPS_PER_PAIR_BIN,
                      "peak_note": "derived FP32 FMA peak: 152 SM x 128 lanes x 2 x max SM clock"},
         "gpu_launches": 6 * args.steps,
