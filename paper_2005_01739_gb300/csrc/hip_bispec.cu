@@ -107,9 +107,11 @@ struct BWarpSmem {
     T qr[HIP_BQCAP], qw[HIP_BQCAP], qpsi[HIP_BQCAP];
     alignas(16) T qy[HIP_BQCAP][HIP_NLMP];  // R_lm of each queued neighbour (row padded to 16 bytes)
     union {
-        // jbar^a_l of each drained neighbour (C term); rows padded by 4 so that the
-        // MMA fragment loads (8 rows x 4 columns per instruction) hit 32 banks
-        T J[HIP_LMAX + 1][HIP_BQ][NKMAX + 4];
+        // jbar^a_l of each drained neighbour (C term); a fragment load reads
+        // J[q = 8 ks + t (+4)][col + g] for t = lane % 4, g = lane / 4, so the bank
+        // is (stride t + g) mod 32: a row stride = 8 (mod 32) makes the 32 lanes hit
+        // 32 different banks
+        T J[HIP_LMAX + 1][HIP_BQ][NKMAX + 8];
         T X[NKMAX + 1][HIP_NLM];           // at the end of a primary: k_e^3 E_e, then A^a_lm
     };
 };
@@ -184,16 +186,22 @@ __device__ __forceinline__ void hip_bdrain(BWarpSmem<T, NKMAX> &sm, int n, const
     }
 }
 
-// Tc[l][a][b] -= s_p sum_q psi_q J[l][q][a] J[l][q][b]  (the C term).
+// The CTA accumulator Tc holds, per l, the upper triangle a <= b of the
+// symmetric n_k x n_k matrix (both the C term and the contraction are symmetric
+// in a, b), row a starting at a nk - a (a - 1) / 2.
+__device__ __forceinline__ int hip_tri(int a, int b, int nk) { return a * nk - (a * (a - 1)) / 2 + (b - a); }
+
+// Tc[l][a<=b] -= s_p sum_q psi_q J[l][q][a] J[l][q][b]  (the C term).
 template <typename T, int NKMAX>
 __device__ __forceinline__ void hip_cterm(const BWarpSmem<T, NKMAX> &sm, int n, int nk, T sp, int lane, T *Tc)
 {
-    const int per_l = nk * nk;
+    const int per_l = nk * nk, ntri = nk * (nk + 1) / 2;
     for (int i = lane; i < (HIP_LMAX + 1) * per_l; i += 32) {
         const int l = i / per_l, ab = i - l * per_l, a = ab / nk, b = ab - a * nk;
+        if (a > b) continue;
         T acc = T(0);
         for (int q = 0; q < n; ++q) acc += sm.qpsi[q] * sm.J[l][q][a] * sm.J[l][q][b];
-        atomicAdd(&Tc[i], -sp * acc);
+        atomicAdd(&Tc[l * ntri + hip_tri(a, b, nk)], -sp * acc);
     }
 }
 
@@ -255,6 +263,7 @@ __device__ __forceinline__ void hip_cterm_mma(const BWarpSmem<float, NKMAX> &sm,
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt) {
                     if (8 * nt >= nk) break;
+                    if (8 * nt + 7 < 16 * mt) continue;  // below the diagonal: not needed
                     const float y0 = q0 < n ? sm.J[l][q0][8 * nt + g] : 0.f;
                     const float y1 = q1 < n ? sm.J[l][q1][8 * nt + g] : 0.f;
                     unsigned bh[2] = {hip_tf32(y0), hip_tf32(y1)};
@@ -267,12 +276,13 @@ __device__ __forceinline__ void hip_cterm_mma(const BWarpSmem<float, NKMAX> &sm,
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
                 if (8 * nt >= nk) break;
+                if (8 * nt + 7 < 16 * mt) continue;  // tile entirely below the diagonal
                 const int r0 = 16 * mt + g, r1 = r0 + 8, c0 = 8 * nt + 2 * t, c1 = c0 + 1;
-                float *T = Tc + (size_t)l * nk * nk;
-                if (r0 < nk && c0 < nk) atomicAdd(&T[r0 * nk + c0], acc[nt][0]);
-                if (r0 < nk && c1 < nk) atomicAdd(&T[r0 * nk + c1], acc[nt][1]);
-                if (r1 < nk && c0 < nk) atomicAdd(&T[r1 * nk + c0], acc[nt][2]);
-                if (r1 < nk && c1 < nk) atomicAdd(&T[r1 * nk + c1], acc[nt][3]);
+                float *T = Tc + (size_t)l * (nk * (nk + 1) / 2);
+                if (c0 < nk && r0 <= c0) atomicAdd(&T[hip_tri(r0, c0, nk)], acc[nt][0]);
+                if (c1 < nk && r0 <= c1) atomicAdd(&T[hip_tri(r0, c1, nk)], acc[nt][1]);
+                if (c0 < nk && r1 <= c0) atomicAdd(&T[hip_tri(r1, c0, nk)], acc[nt][2]);
+                if (c1 < nk && r1 <= c1) atomicAdd(&T[hip_tri(r1, c1, nk)], acc[nt][3]);
             }
         }
     }
@@ -298,7 +308,8 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
     const int n_e = a.n_e, nk = n_e - 1, n_c = a.data.n_c;
     const unsigned lt_mask = (1u << lane) - 1u;
     const T R0sq = a.R0 * a.R0, invR0 = T(1) / a.R0;
-    for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) Tc[i] = T(0);
+    const int ntri = nk * (nk + 1) / 2;
+    for (int i = threadIdx.x; i < (HIP_LMAX + 1) * ntri; i += HIP_BTHREADS) Tc[i] = T(0);
     __syncthreads();
 
     T kk[NCH], kl[NCH], k3[NCH], k3n[NCH], jfac[NCH];
@@ -449,18 +460,18 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
                     for (int i = 0; i < HIP_NLM; ++i) sm.X[e][i] = Aa[t][i];
             }
             __syncwarp();
-            // contraction: Tc[l][a][b] += s_p sum_m A^a_lm A^b_lm  (lane owns rows a)
+            // contraction: Tc[l][a<=b] += s_p sum_m A^a_lm A^b_lm  (lane owns rows a)
 #pragma unroll
             for (int t = 0; t < NCH; ++t) {
                 const int aa = lane + 32 * t;
                 if (aa < nk) {
-                    for (int b = 0; b < nk; ++b) {
+                    for (int b = aa; b < nk; ++b) {
 #pragma unroll
                         for (int l = 0; l <= HIP_LMAX; ++l) {
                             T d = T(0);
 #pragma unroll
                             for (int mm = -l; mm <= l; ++mm) d += Aa[t][l * l + l + mm] * sm.X[b][l * l + l + mm];
-                            atomicAdd(&Tc[(l * nk + aa) * nk + b], sp * d);
+                            atomicAdd(&Tc[l * ntri + hip_tri(aa, b, nk)], sp * d);
                         }
                     }
                 }
@@ -470,7 +481,10 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
     }
     __syncthreads();
     double *out = a.partials + (size_t)blockIdx.x * (HIP_LMAX + 1) * nk * nk;
-    for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) out[i] = (double)Tc[i];
+    for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) {
+        const int l = i / (nk * nk), ab = i - l * nk * nk, x = ab / nk, y = ab - x * nk;
+        out[i] = (double)Tc[l * ntri + (x <= y ? hip_tri(x, y, nk) : hip_tri(y, x, nk))];
+    }
     // cnt_d, cnt_r are warp-uniform (every lane added each ballot's count)
     if (lane == 0) {
         if (cnt_d) atomicAdd(a.npairs, cnt_d);
@@ -482,7 +496,7 @@ template <typename T, int NCH, int NKMAX>
 static cudaError_t launch_bispec(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st)
 {
     const int nk = a.n_e - 1;
-    const size_t dyn = sizeof(T) * (HIP_LMAX + 1) * nk * nk;
+    const size_t dyn = sizeof(T) * (HIP_LMAX + 1) * (nk * (nk + 1) / 2);
     cudaError_t e = cudaFuncSetAttribute(k_bispec<T, NCH, NKMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)dyn);
     if (e != cudaSuccess) return e;
