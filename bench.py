@@ -268,13 +268,77 @@ def run_batched(args):
             ts.append(a.elapsed_time(b))
     work = sum((n // 2) * (len(c["edges"]) - 1) for c, (_, _, n) in zip(cats, res))
     ms = float(np.mean(ts))
+    launches = plan.launches
+    plan.close()
+    # the same batch through the plain FP64 path (one replay after one warm-up)
+    fp64 = None
+    if not args.skip_fp64:
+        plan64 = binding.BatchPlan(cats, "fp64", stream=stream)
+        plan64.run(stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan64.run(stream)
+        b.record(stream)
+        b.synchronize()
+        ms64 = a.elapsed_time(b)
+        plan64.close()
+        fp64 = {"value": work / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "mixed_over_fp64": ms64 / ms}
     print(json.dumps({"metric": METRIC, "value": work / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
                       "data": "synthetic", "config": {"workload": "batched64", "catalogs": len(cats),
                                                       "particles": int(sum(int(c["pos"].shape[0]) for c in cats)),
                                                       "pair_bins": int(work)},
-                      "gpu_launches": plan.launches * args.steps, "clocks": clk.summary()}), flush=True)
-    plan.close()
+                      "gpu_launches": launches * args.steps, "clocks": clk.summary(), "fp64_plain": fp64}),
+          flush=True)
+    return 0
+
+
+def run_large(args):
+    """The 256^3 Zel'dovich lattice: P (R0 = 20, 200 bins to k = 10, l = 0,2,4) and
+    B (R0 = 15, 40 bins, l = 0..4, 3x randoms), mixed path, one timed call each
+    after one warm-up."""
+    import torch
+
+    from paper_2005_01739_gb300 import binding, build, catalogs
+    build.build()
+    binding.load()
+    wl = catalogs.workload("large_zeldovich")
+    stream = torch.cuda.Stream()
+    dpos = torch.from_numpy(wl["pos"]).cuda()
+
+    def timed(fn):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return out, a.elapsed_time(b)
+
+    def pk():
+        with torch.cuda.stream(stream):
+            return binding.hip_power(dpos, None, wl["L"], wl["R0"], wl["edges"], 4, 2, "mixed", stream=stream)
+
+    (_, _, npairs), ms_p = timed(pk)
+    nk = len(wl["edges"]) - 1
+    out = {"workload": "large_zeldovich", "N": int(len(wl["pos"])),
+           "power": {"value": (npairs // 2) * nk / (ms_p / 1e3), "unit": UNIT, "ms": ms_p,
+                     "unordered_pairs": int(npairs // 2), "n_k": nk, "R0": wl["R0"]}}
+    if not args.skip_bispectrum:
+        rnd = catalogs.uniform(3 * len(wl["pos"]), wl["L"], 1004 + 7919)
+        drnd = torch.from_numpy(rnd).cuda()
+        nkb = len(wl["edges_b"]) - 1
+
+        def bk():
+            with torch.cuda.stream(stream):
+                return binding.hip_bispectrum(dpos, None, drnd, wl["L"], wl["R0_b"], wl["edges_b"], 4, "mixed",
+                                              stream=stream)
+
+        (_, (nd, nr)), ms_b = timed(bk)
+        out["bispectrum"] = {"value": (nd + nr) * nkb / (ms_b / 1e3), "unit": UNIT, "ms": ms_b,
+                             "pairs_data_primaries": int(nd), "pairs_random_primaries": int(nr), "n_k": nkb,
+                             "R0": wl["R0_b"], "randoms": int(len(rnd))}
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -381,6 +445,13 @@ def run_ours(args):
     kern_ms = float(np.mean(pair_ms))
     achieved = FLOPS_PER_PAIR_BIN * work / (kern_ms / 1e3) / 1e12
     cpu = oracle_sample(wl, args.ref_seconds) if not args.skip_cpu else None
+    cpu1 = None
+    if cpu:  # the same oracle on one core, a shorter sample
+        import oracle
+        nthr = oracle.num_threads()
+        oracle.set_threads(1)
+        cpu1 = oracle_sample(wl, 3.0)
+        oracle.set_threads(nthr)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -405,7 +476,9 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
                                 "sample": (f"FP64 brute force, ordered pair sums of the first {cpu['primaries']} "
                                            f"primaries against all {n} particles, {nk} bins, l=0,2,4 "
-                                           f"({cpu['seconds']:.1f} s)")}
+                                           f"({cpu['seconds']:.1f} s)"),
+                                "single_core_value": cpu1["value"],
+                                "single_core_sample": f"first {cpu1['primaries']} primaries ({cpu1['seconds']:.1f} s)"}
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -424,6 +497,7 @@ def main():
     ap.add_argument("--skip-bispectrum", action="store_true")
     ap.add_argument("--bk-only", action="store_true", help="time only the bispectrum workload")
     ap.add_argument("--batched", action="store_true", help="time the 64-catalog batched workload")
+    ap.add_argument("--large", action="store_true", help="time P and B on the 256^3 Zel'dovich lattice")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the catalog volume at fixed density (profiler captures only)")
     args = ap.parse_args()
@@ -431,6 +505,8 @@ def main():
         return run_reference(args)
     if args.bk_only:
         return run_bispectrum_only(args)
+    if args.large:
+        return run_large(args)
     if args.batched:
         return run_batched(args)
     return run_ours(args)

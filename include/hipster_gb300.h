@@ -122,6 +122,33 @@ hip_status hip_bispectrum_partial(const float *pos, const float *w, int64_t N, c
                                   hip_precision prec, const int64_t *prim_ranges, double *T_out, int64_t *npairs_out,
                                   void *cuda_stream);
 
+/* One catalog of a batched bispectrum computation: the arguments of
+ * hip_bispectrum for that catalog (host or device inputs; host outputs). */
+typedef struct {
+    const float *pos;      /* [N][3] float32 */
+    const float *w;        /* [N] float32 or NULL */
+    int64_t N;
+    const float *rand_pos; /* [N_r][3] float32 */
+    int64_t N_r;
+    double L, R0;
+    const double *k_edges; /* [n_k+1] host */
+    int n_k, lmax;
+    double *B_out;         /* [(lmax+1) * n_k * n_k] host */
+    int64_t *npairs_out;   /* [2] or NULL */
+} hip_bcatalog;
+
+/* Batched bispectra (the estimator of hip_bispectrum, Sec. 4, for many
+ * catalogs of uneven N, L, R0 and bins).  Every catalog's cell lists and its
+ * l = 0 pair sum S^a are built first; then ONE persistent kernel launch runs the
+ * primaries of all catalogs (work items of 32 primaries, the catalogs' items laid
+ * end to end), accumulating each catalog's primary sums in FP64; a FP64 finalize
+ * per catalog follows.  Per catalog the result equals hip_bispectrum's up to the
+ * order of the FP32 / FP64 sums.  All catalogs must satisfy hip_bispectrum's
+ * argument rules (n_k <= 63 MIXED, <= 31 FP64); errors as in hip_bispectrum (the
+ * first failing catalog decides).  The call synchronises cuda_stream once after
+ * the cell builds and once at the end.  1 <= n_cats <= 4096. */
+hip_status hip_bispectrum_batched(const hip_bcatalog *cats, int n_cats, hip_precision prec, void *cuda_stream);
+
 /* One catalog of a batched power-spectrum computation: the arguments of
  * hip_power for that catalog (host or device inputs; host outputs). */
 typedef struct {

@@ -34,6 +34,13 @@ class HipCatalog(ctypes.Structure):
                 ("npairs_out", ctypes.c_void_p)]
 
 
+class HipBCatalog(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("w", ctypes.c_void_p), ("N", ctypes.c_int64),
+                ("rand_pos", ctypes.c_void_p), ("N_r", ctypes.c_int64), ("L", ctypes.c_double),
+                ("R0", ctypes.c_double), ("k_edges", ctypes.c_void_p), ("n_k", ctypes.c_int), ("lmax", ctypes.c_int),
+                ("B_out", ctypes.c_void_p), ("npairs_out", ctypes.c_void_p)]
+
+
 class HipError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(msg)
@@ -77,6 +84,8 @@ def load(path: str | None = None):
         L.hip_power_batched.argtypes = [P, i, i, P]
         L.hip_batch_message.restype = ctypes.c_char_p
         L.hip_batch_message.argtypes = []
+        L.hip_bispectrum_batched.restype = i
+        L.hip_bispectrum_batched.argtypes = [P, i, i, P]
         L.hip_bispectrum_partial.restype = i
         L.hip_bispectrum_partial.argtypes = [P, P, i64, P, i64, d, d, i, P, i, i, i, P, P, P, P]
         L.hip_status_string.restype = ctypes.c_char_p
@@ -264,6 +273,35 @@ def hip_bispectrum(pos, w, rand_pos, L, R0, k_edges, lmax=4, prec="mixed", strea
     _check(lib, rc, "hip_bispectrum")
     del keep_p, keep_w, keep_r
     return B, (int(npairs[0]), int(npairs[1]))
+
+
+def hip_bispectrum_batched(catalogs, prec="mixed", stream=None):
+    """Bispectra of many catalogs with one persistent kernel launch over all
+    their primaries.  `catalogs`: dicts with pos, w (or None), rand, L, R0, edges
+    and optionally lmax (default 4).  Returns a list of (B, (pairs from data
+    primaries, pairs from random primaries)) in catalog order."""
+    lib = load()
+    n = len(catalogs)
+    arr = (HipBCatalog * n)()
+    keep, outs = [], []
+    for i, c in enumerate(catalogs):
+        pp, k1 = _ptr(c["pos"])
+        wp, k2 = _ptr(c.get("w"))
+        rp, k3 = _ptr(c["rand"])
+        edges = np.ascontiguousarray(np.asarray(c["edges"], dtype=np.float64))
+        n_k = len(edges) - 1
+        lmax = int(c.get("lmax", 4))
+        B = np.zeros((lmax + 1, n_k, n_k))
+        npairs = np.zeros(2, dtype=np.int64)
+        keep += [k1, k2, k3, edges]
+        outs.append((B, npairs))
+        arr[i] = HipBCatalog(pp.value, wp.value if wp is not None else None, int(c["pos"].shape[0]), rp.value,
+                             int(c["rand"].shape[0]), float(c["L"]),
+                             float(c["R0"]), edges.ctypes.data, n_k, lmax, B.ctypes.data, npairs.ctypes.data)
+    rc = lib.hip_bispectrum_batched(ctypes.cast(arr, ctypes.c_void_p), n, PREC[prec], _stream_handle(stream))
+    _check(lib, rc, "hip_bispectrum_batched")
+    del keep
+    return [(B, (int(np_[0]), int(np_[1]))) for B, np_ in outs]
 
 
 def hip_bispectrum_partial(pos, w, rand_pos, L, R0, k_edges, lmax=4, prec="mixed", data_range=None,

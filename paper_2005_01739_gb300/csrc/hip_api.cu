@@ -1,5 +1,6 @@
 // C ABI of the library: argument validation, the per-device workspace, and the
 // sequencing of the kernels for hip_power (Sec. 3 of arXiv:2005.01739).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -468,6 +469,236 @@ extern "C" hip_status hip_bispectrum(const float *pos, const float *w, int64_t N
                                   nullptr, false);
     return bispec_impl<double>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, lmax, B_out, npairs_out, st, dev,
                                nullptr, false);
+}
+
+// Batched bispectra: per catalog the buffers of bispec_impl (one workspace
+// carve for all), one persistent bispectrum launch over every catalog's
+// primaries, FP64 finalize per catalog.
+template <typename T>
+static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStream_t st, int dev)
+{
+    Workspace &ws = hip_workspace(dev);
+    const int pgrid = hip_power_grid<T>();
+    struct Lay {
+        int n_c, n_cells, n_k, n_e;
+        bool dpos, dw, drp;
+        size_t o_pos, o_w, o_rp, o_dx, o_dy, o_dz, o_dw, o_didx, o_dcid, o_rx, o_ry, o_rz, o_rw, o_ridx, o_rcid;
+        size_t o_ds, o_df, o_dsc, o_rsc, o_rs, o_rf, o_small, o_wt, o_dd, o_p, o_b, o_acc;
+    };
+    std::vector<Lay> lay(nc);
+    Carve cv;
+    int nk_max = 0, ne_max = 0;
+    for (int i = 0; i < nc; ++i) {
+        const hip_bcatalog &c = cats[i];
+        Lay &y = lay[i];
+        y.n_c = hip_cells_per_side(c.L, c.R0);
+        y.n_cells = y.n_c * y.n_c * y.n_c;
+        y.n_k = c.n_k;
+        y.n_e = c.n_k + 1;
+        nk_max = std::max(nk_max, y.n_k);
+        ne_max = std::max(ne_max, y.n_e);
+        y.dpos = hip_is_device_ptr(c.pos);
+        y.dw = c.w && hip_is_device_ptr(c.w);
+        y.drp = hip_is_device_ptr(c.rand_pos);
+        const int64_t N = c.N, Nr = c.N_r;
+        const size_t tsz = (size_t)(HIP_LMAX + 1) * c.n_k * c.n_k;
+        y.o_pos = y.dpos ? 0 : cv.take(sizeof(float) * 3 * N);
+        y.o_w = (c.w && !y.dw) ? cv.take(sizeof(float) * N) : 0;
+        y.o_rp = y.drp ? 0 : cv.take(sizeof(float) * 3 * Nr);
+        y.o_dx = cv.take(sizeof(T) * N), y.o_dy = cv.take(sizeof(T) * N), y.o_dz = cv.take(sizeof(T) * N);
+        y.o_dw = cv.take(sizeof(float) * N), y.o_didx = cv.take(sizeof(int) * N), y.o_dcid = cv.take(sizeof(int) * N);
+        y.o_rx = cv.take(sizeof(T) * Nr), y.o_ry = cv.take(sizeof(T) * Nr), y.o_rz = cv.take(sizeof(T) * Nr);
+        y.o_rw = cv.take(sizeof(float) * Nr), y.o_ridx = cv.take(sizeof(int) * Nr);
+        y.o_rcid = cv.take(sizeof(int) * Nr);
+        y.o_ds = cv.take(sizeof(int) * (y.n_cells + 1)), y.o_df = cv.take(sizeof(int) * y.n_cells);
+        y.o_dsc = cv.take(sizeof(int) * N), y.o_rsc = cv.take(sizeof(int) * Nr);
+        y.o_rs = cv.take(sizeof(int) * (y.n_cells + 1)), y.o_rf = cv.take(sizeof(int) * y.n_cells);
+        y.o_small = cv.take(sizeof(double) * 16);
+        y.o_wt = cv.take(sizeof(double) * c.n_k), y.o_dd = cv.take(sizeof(double) * 3 * c.n_k);
+        y.o_p = cv.take(sizeof(double) * 3 * c.n_k), y.o_b = cv.take(sizeof(double) * tsz);
+        y.o_acc = cv.take(sizeof(double) * tsz);
+    }
+    const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * ne_max);
+    const size_t o_desc = cv.take(sizeof(BispecCat<T>) * nc);
+    const size_t o_cnt = cv.take(sizeof(int) * 4);
+    hip_status hs = ws.reserve(cv.total, st);
+    if (hs != HIP_OK) return hs;
+    char *b = (char *)ws.base;
+    cudaError_t e;
+#define HIP_CK(call, what)                                                                                           \
+    do {                                                                                                             \
+        if ((e = (call)) != cudaSuccess) {                                                                           \
+            set_err(what, e);                                                                                        \
+            return HIP_ERR_CUDA;                                                                                     \
+        }                                                                                                            \
+    } while (0)
+    std::vector<CellList<T>> dcl(nc), rcl(nc);
+    for (int i = 0; i < nc; ++i) {
+        const hip_bcatalog &c = cats[i];
+        const Lay &y = lay[i];
+        const float *dposp = c.pos, *dwp = c.w, *drpp = c.rand_pos;
+        if (!y.dpos) {
+            HIP_CK(cudaMemcpyAsync(b + y.o_pos, c.pos, sizeof(float) * 3 * c.N, cudaMemcpyHostToDevice, st),
+                   "H2D positions");
+            dposp = (const float *)(b + y.o_pos);
+        }
+        if (c.w && !y.dw) {
+            HIP_CK(cudaMemcpyAsync(b + y.o_w, c.w, sizeof(float) * c.N, cudaMemcpyHostToDevice, st), "H2D weights");
+            dwp = (const float *)(b + y.o_w);
+        }
+        if (!y.drp) {
+            HIP_CK(cudaMemcpyAsync(b + y.o_rp, c.rand_pos, sizeof(float) * 3 * c.N_r, cudaMemcpyHostToDevice, st),
+                   "H2D randoms");
+            drpp = (const float *)(b + y.o_rp);
+        }
+        double *small = (double *)(b + y.o_small);
+        int *err = (int *)(small + 5);
+        T *dx = (T *)(b + y.o_dx), *dy = (T *)(b + y.o_dy), *dz = (T *)(b + y.o_dz);
+        T *rx = (T *)(b + y.o_rx), *ry = (T *)(b + y.o_ry), *rz = (T *)(b + y.o_rz);
+        int *dstart = (int *)(b + y.o_ds), *rstart = (int *)(b + y.o_rs);
+        HIP_CK(hip_build_cells<T>(dposp, dwp, c.N, c.L, y.n_c, dx, dy, dz, (float *)(b + y.o_dw), (int *)(b + y.o_didx),
+                                  (int *)(b + y.o_dcid), dstart, (int *)(b + y.o_df), small, err, st),
+               "cell build (data)");
+        HIP_CK(hip_build_cells<T>(drpp, nullptr, c.N_r, c.L, y.n_c, rx, ry, rz, (float *)(b + y.o_rw),
+                                  (int *)(b + y.o_ridx), (int *)(b + y.o_rcid), rstart, (int *)(b + y.o_rf), small + 1,
+                                  err + 1, st),
+               "cell build (randoms)");
+        HIP_CK(hip_sorted_cells(dstart, y.n_cells, (int *)(b + y.o_dsc), st), "sorted cells (data)");
+        HIP_CK(hip_sorted_cells(rstart, y.n_cells, (int *)(b + y.o_rsc), st), "sorted cells (randoms)");
+        dcl[i] = CellList<T>{dx, dy, dz, (const float *)(b + y.o_dw), (const int *)(b + y.o_didx), dstart, y.n_c, c.L,
+                             c.L / y.n_c};
+        rcl[i] = CellList<T>{rx, ry, rz, (const float *)(b + y.o_rw), (const int *)(b + y.o_ridx), rstart, y.n_c, c.L,
+                             c.L / y.n_c};
+    }
+    // S1 of every catalog (for the random primaries' weight) and the error words
+    std::vector<double> hsm((size_t)nc * 6);
+    for (int i = 0; i < nc; ++i)
+        HIP_CK(cudaMemcpyAsync(&hsm[(size_t)i * 6], b + lay[i].o_small, sizeof(double) * 6, cudaMemcpyDeviceToHost,
+                               st),
+               "D2H S1");
+    HIP_CK(cudaStreamSynchronize(st), "cell build sync");
+    for (int i = 0; i < nc; ++i) {
+        int herr[2];
+        std::memcpy(herr, &hsm[(size_t)i * 6 + 5], sizeof(herr));
+        if (herr[0] || herr[1]) return HIP_ERR_NONFINITE;
+    }
+    // S^a of every catalog: the l = 0 power pair sum (one launch each; the
+    // partial rows are reused in stream order)
+    std::vector<BispecCat<T>> desc(nc);
+    int items = 0;
+    for (int i = 0; i < nc; ++i) {
+        const hip_bcatalog &c = cats[i];
+        const Lay &y = lay[i];
+        double *small = (double *)(b + y.o_small);
+        unsigned long long *npairs = (unsigned long long *)(small + 2);
+        int *counter = (int *)(small + 6);
+        HIP_CK(cudaMemsetAsync(npairs, 0, 3 * sizeof(unsigned long long), st), "memset");
+        HIP_CK(cudaMemsetAsync(counter, 0, sizeof(int), st), "memset");
+        HIP_CK(cudaMemsetAsync(b + y.o_acc, 0, sizeof(double) * (HIP_LMAX + 1) * c.n_k * c.n_k, st), "memset");
+        PowerKernelArgs ka;
+        ka.n_e = y.n_e;
+        ka.los = 2;
+        ka.p0 = 0;
+        ka.p1 = c.N;
+        ka.n_items = y.n_cells * HIP_NSHIFT;
+        ka.work_counter = counter;
+        ka.partials = (double *)(b + o_pp);
+        ka.npairs = npairs;
+        HIP_CK(hip_power_pairs<T>(dcl[i], ka, c.k_edges, 1, c.R0, pgrid, st), "pair kernel (S)");
+        HIP_CK(hip_power_finalize(ka.partials, pgrid, y.n_e, 1, c.k_edges, c.R0, c.L, small,
+                                  (double *)(b + y.o_wt), (double *)(b + y.o_dd), (double *)(b + y.o_p), st),
+               "finalize (S)");
+        BispecCat<T> &d = desc[i];
+        std::memset(&d, 0, sizeof(d));
+        BispecArgs<T> &ba = d.a;
+        ba.data = dcl[i];
+        ba.rand = rcl[i];
+        ba.n_cells = y.n_cells;
+        ba.dcell = (const int *)(b + y.o_dsc);
+        ba.rcell = (const int *)(b + y.o_rsc);
+        ba.n_data = (int)c.N;
+        ba.n_rand = (int)c.N_r;
+        ba.n_e = y.n_e;
+        ba.R0 = (T)c.R0;
+        ba.rand_weight = (T)(-hsm[(size_t)i * 6] / (double)c.N_r);
+        ba.npairs = npairs + 1;
+        ba.dp0 = 0;
+        ba.dp1 = c.N;
+        ba.rp0 = 0;
+        ba.rp1 = c.N_r;
+        for (int q = 0; q < HIP_BMAXE; ++q) {
+            const double k = q < y.n_e ? c.k_edges[q] : 0.0;
+            ba.k[q] = (T)k;
+            ba.klo[q] = (T)(k - (double)ba.k[q]);
+            ba.k3[q] = (T)(k * k * k);
+            ba.jfac[q] = q + 1 < y.n_e
+                             ? (T)(3.0 / (c.k_edges[q + 1] * c.k_edges[q + 1] * c.k_edges[q + 1] - k * k * k))
+                             : T(0);
+        }
+        const int64_t n_prim = c.N + c.N_r;
+        d.item_begin = items;
+        items += (int)((n_prim + HIP_BCTA_PRIM - 1) / HIP_BCTA_PRIM);
+        d.item_end = items;
+        d.acc = (double *)(b + y.o_acc);
+    }
+    BispecCat<T> *ddesc = (BispecCat<T> *)(b + o_desc);
+    int *bcounter = (int *)(b + o_cnt);
+    HIP_CK(cudaMemcpyAsync(ddesc, desc.data(), sizeof(BispecCat<T>) * nc, cudaMemcpyHostToDevice, st),
+           "H2D descriptors");
+    HIP_CK(cudaMemsetAsync(bcounter, 0, sizeof(int), st), "memset");
+    int bgrid = 0;
+    HIP_CK(hip_bispec_pairs_batched<T>(ddesc, nc, items, nk_max, bcounter, &bgrid, st), "batched bispectrum kernel");
+    std::vector<std::vector<double>> hB(nc);
+    std::vector<unsigned long long> hn((size_t)nc * 3);
+    for (int i = 0; i < nc; ++i) {
+        const hip_bcatalog &c = cats[i];
+        const Lay &y = lay[i];
+        double *small = (double *)(b + y.o_small);
+        double *B = (double *)(b + y.o_b);
+        HIP_CK(hip_bispec_finalize((double *)(b + y.o_acc), 1, c.n_k, c.lmax, c.L, small, (double *)(b + y.o_dd),
+                                   (double *)(b + y.o_wt), B, st),
+               "bispectrum finalize");
+        hB[i].resize((size_t)(c.lmax + 1) * c.n_k * c.n_k);
+        HIP_CK(cudaMemcpyAsync(hB[i].data(), B, sizeof(double) * hB[i].size(), cudaMemcpyDeviceToHost, st), "D2H B");
+        HIP_CK(cudaMemcpyAsync(&hn[(size_t)i * 3], small + 2, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               st),
+               "D2H npairs");
+    }
+    HIP_CK(cudaStreamSynchronize(st), "stream sync");
+#undef HIP_CK
+    for (int i = 0; i < nc; ++i) {
+        std::memcpy(cats[i].B_out, hB[i].data(), sizeof(double) * hB[i].size());
+        if (cats[i].npairs_out) {
+            cats[i].npairs_out[0] = (int64_t)hn[(size_t)i * 3 + 1];
+            cats[i].npairs_out[1] = (int64_t)hn[(size_t)i * 3 + 2];
+        }
+    }
+    return HIP_OK;
+}
+
+extern "C" hip_status hip_bispectrum_batched(const hip_bcatalog *cats, int n_cats, hip_precision prec,
+                                             void *cuda_stream)
+{
+    g_errbuf[0] = 0;
+    if (!cats || n_cats < 1 || n_cats > 4096) return HIP_ERR_ARG;
+    if (prec != HIP_PREC_FP64 && prec != HIP_PREC_MIXED) return HIP_ERR_ARG;
+    for (int i = 0; i < n_cats; ++i) {
+        const hip_bcatalog &c = cats[i];
+        if (!c.pos || !c.rand_pos || !c.B_out) return HIP_ERR_ARG;
+        if (c.N < 1 || c.N > 2000000000LL || c.N_r < 1 || c.N_r > 2000000000LL) return HIP_ERR_ARG;
+        if (c.lmax < 0 || c.lmax > HIP_LMAX) return HIP_ERR_ARG;
+        if (!(c.L > 0.0) || !std::isfinite(c.L) || !(c.R0 > 0.0) || !(c.R0 < 0.5 * c.L)) return HIP_ERR_RANGE;
+        hip_status hs = hip_check_edges(c.k_edges, c.n_k);
+        if (hs != HIP_OK) return hs;
+        if (c.n_k > (prec == HIP_PREC_MIXED ? HIP_BMAXE - 2 : 31)) return HIP_ERR_RANGE;
+    }
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    int dev = 0;
+    hip_status hs;
+    if ((hs = hip_device_setup(&dev)) != HIP_OK) return hs;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (prec == HIP_PREC_MIXED) return bispec_batched_impl<float>(cats, n_cats, st, dev);
+    return bispec_batched_impl<double>(cats, n_cats, st, dev);
 }
 
 extern "C" hip_status hip_bispectrum_partial(const float *pos, const float *w, int64_t N, const float *rand_pos,

@@ -297,6 +297,166 @@ __device__ __forceinline__ void hip_cterm_any(const BWarpSmem<T, NKMAX> &sm, int
         hip_cterm<T, NKMAX>(sm, n, nk, sp, lane, Tc);
 }
 
+// One primary g (data first, then randoms) of the catalog described by a: the
+// 27-cell neighbour scan, the queued drains (edge sums, C term) and, at the end,
+// the contraction of its A^a_lm into the CTA accumulator Tc (upper triangle).
+template <typename T, int NCH, int NKMAX>
+__device__ __forceinline__ void hip_bispec_primary(const BispecArgs<T> &a, int g, BWarpSmem<T, NKMAX> &sm, T *Tc,
+                                                   const T (&kk)[NCH], const T (&kl)[NCH], const T (&k3)[NCH],
+                                                   const T (&k3n)[NCH], const T (&jfac)[NCH], int lane,
+                                                   unsigned long long &cnt_d, unsigned long long &cnt_r)
+{
+    const int n_e = a.n_e, nk = n_e - 1, n_c = a.data.n_c;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const T R0sq = a.R0 * a.R0, invR0 = T(1) / a.R0;
+    const int ntri = nk * (nk + 1) / 2;
+    const bool is_rand = g >= a.n_data;
+    const CellList<T> &pl = is_rand ? a.rand : a.data;
+    const int p = is_rand ? g - a.n_data : g;
+    const int c = is_rand ? a.rcell[p] : a.dcell[p];
+    const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
+    const T px = pl.x[p], py = pl.y[p], pz = pl.z[p];
+    const T sp = is_rand ? a.rand_weight : T(pl.w[p]);
+    const int self = is_rand ? -1 : p;
+    {
+        const long long oi = pl.idx[p];
+        if (is_rand ? (oi < a.rp0 || oi >= a.rp1) : (oi < a.dp0 || oi >= a.dp1)) return;
+    }
+    T E[NCH][HIP_NLM];
+#pragma unroll
+    for (int t = 0; t < NCH; ++t)
+#pragma unroll
+        for (int i = 0; i < HIP_NLM; ++i) E[t][i] = T(0);
+    int qn = 0;
+    // cell shifts of this primary: lane 3 axis + d + 1 holds the shift
+    // of neighbour offset d along that axis (the shift's low part, below
+    // 1e-6 of the cell side, is under the FP32 B budget and dropped)
+    T shl = T(0);
+    if (lane < 9) {
+        const int ax = lane / 3, cc = ax == 0 ? cx : (ax == 1 ? cy : cz);
+        T lo;
+        hip_cell_shift(a.data, cc, lane % 3 - 1, shl, lo);
+    }
+    for (int s = 0; s < 27; ++s) {
+        const int dx = s / 9 - 1, dy = (s / 3) % 3 - 1, dz = s % 3 - 1;
+        const int nb = (((cx + dx + n_c) % n_c) * n_c + (cy + dy + n_c) % n_c) * n_c + (cz + dz + n_c) % n_c;
+        const int b0 = a.data.cell_start[nb], b1 = a.data.cell_start[nb + 1];
+        const T shx = __shfl_sync(0xffffffffu, shl, dx + 1), shy = __shfl_sync(0xffffffffu, shl, dy + 4),
+                shz = __shfl_sync(0xffffffffu, shl, dz + 7);
+        const T ox = px - shx, oy = py - shy, oz = pz - shz;
+        for (int jb = b0; jb < b1; jb += 32) {
+            const int j = jb + lane;
+            bool ok = false;
+            T ddx = T(0), ddy = T(0), ddz = T(0), r2 = T(0);
+            if (j < b1) {
+                ddx = ox - a.data.x[j];
+                ddy = oy - a.data.y[j];
+                ddz = oz - a.data.z[j];
+                r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                ok = (r2 < R0sq) && (r2 > T(0)) && (j != self);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const T r = hip_sqrt_b(r2);
+                const T ir = T(1) / r;
+                const T W = hip_W<T>(r * invR0);
+                const T wj = T(a.data.w[j]);
+                const int slot = qn + __popc(m & lt_mask);
+                T R[HIP_NLM];
+                hip_real_ylm<T>(ddx * ir, ddy * ir, ddz * ir, R);
+                sm.qr[slot] = r;
+                sm.qw[slot] = wj * W;
+                sm.qpsi[slot] = wj * wj * W * W;
+#pragma unroll
+                for (int i = 0; i < HIP_NLM; ++i) sm.qy[slot][i] = R[i];
+            }
+            const int nq = __popc(m);
+            if (is_rand)
+                cnt_r += nq;
+            else
+                cnt_d += nq;
+            qn += nq;
+            while (qn >= HIP_BQ) {
+                // drain the first HIP_BQ entries, move the rest (< 32) down
+                __syncwarp();
+                hip_bdrain<T, NCH, NKMAX>(sm, HIP_BQ, kk, kl, k3, k3n, jfac, lane, n_e, E);
+                __syncwarp();
+                hip_cterm_any<T, NKMAX>(sm, HIP_BQ, nk, sp, lane, Tc);
+                const int rest = qn - HIP_BQ;
+                T mv[3] = {T(0), T(0), T(0)};
+                if (lane < rest) {
+                    mv[0] = sm.qr[HIP_BQ + lane];
+                    mv[1] = sm.qw[HIP_BQ + lane];
+                    mv[2] = sm.qpsi[HIP_BQ + lane];
+                }
+                T my[HIP_NLM];
+#pragma unroll
+                for (int i = 0; i < HIP_NLM; ++i) my[i] = lane < rest ? sm.qy[HIP_BQ + lane][i] : T(0);
+                __syncwarp();
+                if (lane < rest) {
+                    sm.qr[lane] = mv[0];
+                    sm.qw[lane] = mv[1];
+                    sm.qpsi[lane] = mv[2];
+#pragma unroll
+                    for (int i = 0; i < HIP_NLM; ++i) sm.qy[lane][i] = my[i];
+                }
+                qn = rest;
+                __syncwarp();
+            }
+        }
+    }
+    if (qn > 0) {
+        __syncwarp();
+        hip_bdrain<T, NCH, NKMAX>(sm, qn, kk, kl, k3, k3n, jfac, lane, n_e, E);
+        __syncwarp();
+        hip_cterm_any<T, NKMAX>(sm, qn, nk, sp, lane, Tc);
+        qn = 0;
+    }
+    // edge sums -> A^a_lm = jfac_a (k_{a+1}^3 E_{a+1} - k_a^3 E_a)
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+        const int e = lane + 32 * t;
+        if (e < n_e)
+#pragma unroll
+            for (int i = 0; i < HIP_NLM; ++i) sm.X[e][i] = k3[t] * E[t][i];
+    }
+    __syncwarp();
+    T Aa[NCH][HIP_NLM];
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+        const int e = lane + 32 * t;
+#pragma unroll
+        for (int i = 0; i < HIP_NLM; ++i) Aa[t][i] = e < nk ? jfac[t] * (sm.X[e + 1][i] - sm.X[e][i]) : T(0);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+        const int e = lane + 32 * t;
+        if (e < nk)
+#pragma unroll
+            for (int i = 0; i < HIP_NLM; ++i) sm.X[e][i] = Aa[t][i];
+    }
+    __syncwarp();
+    // contraction: Tc[l][a<=b] += s_p sum_m A^a_lm A^b_lm  (lane owns rows a)
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+        const int aa = lane + 32 * t;
+        if (aa < nk) {
+            for (int b = aa; b < nk; ++b) {
+#pragma unroll
+                for (int l = 0; l <= HIP_LMAX; ++l) {
+                    T d = T(0);
+#pragma unroll
+                    for (int mm = -l; mm <= l; ++mm) d += Aa[t][l * l + l + mm] * sm.X[b][l * l + l + mm];
+                    atomicAdd(&Tc[l * ntri + hip_tri(aa, b, nk)], sp * d);
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
 template <typename T, int NCH, int NKMAX>
 __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
 {
@@ -305,9 +465,7 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
     T *Tc = reinterpret_cast<T *>(tc_raw);  // [5][nk][nk] CTA accumulator
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BWarpSmem<T, NKMAX> &sm = smem[warp];
-    const int n_e = a.n_e, nk = n_e - 1, n_c = a.data.n_c;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const T R0sq = a.R0 * a.R0, invR0 = T(1) / a.R0;
+    const int n_e = a.n_e, nk = n_e - 1;
     const int ntri = nk * (nk + 1) / 2;
     for (int i = threadIdx.x; i < (HIP_LMAX + 1) * ntri; i += HIP_BTHREADS) Tc[i] = T(0);
     __syncthreads();
@@ -331,153 +489,8 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         const int g0 = item * HIP_BPRIM, g1 = min(g0 + HIP_BPRIM, n_prim);
-        for (int g = g0; g < g1; ++g) {
-            const bool is_rand = g >= a.n_data;
-            const CellList<T> &pl = is_rand ? a.rand : a.data;
-            const int p = is_rand ? g - a.n_data : g;
-            const int c = is_rand ? a.rcell[p] : a.dcell[p];
-            const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
-            const T px = pl.x[p], py = pl.y[p], pz = pl.z[p];
-            const T sp = is_rand ? a.rand_weight : T(pl.w[p]);
-            const int self = is_rand ? -1 : p;
-            {
-                const long long oi = pl.idx[p];
-                if (is_rand ? (oi < a.rp0 || oi >= a.rp1) : (oi < a.dp0 || oi >= a.dp1)) continue;
-            }
-            T E[NCH][HIP_NLM];
-#pragma unroll
-            for (int t = 0; t < NCH; ++t)
-#pragma unroll
-                for (int i = 0; i < HIP_NLM; ++i) E[t][i] = T(0);
-            int qn = 0;
-            // cell shifts of this primary: lane 3 axis + d + 1 holds the shift
-            // of neighbour offset d along that axis (the shift's low part, below
-            // 1e-6 of the cell side, is under the FP32 B budget and dropped)
-            T shl = T(0);
-            if (lane < 9) {
-                const int ax = lane / 3, cc = ax == 0 ? cx : (ax == 1 ? cy : cz);
-                T lo;
-                hip_cell_shift(a.data, cc, lane % 3 - 1, shl, lo);
-            }
-            for (int s = 0; s < 27; ++s) {
-                const int dx = s / 9 - 1, dy = (s / 3) % 3 - 1, dz = s % 3 - 1;
-                const int nb = (((cx + dx + n_c) % n_c) * n_c + (cy + dy + n_c) % n_c) * n_c + (cz + dz + n_c) % n_c;
-                const int b0 = a.data.cell_start[nb], b1 = a.data.cell_start[nb + 1];
-                const T shx = __shfl_sync(0xffffffffu, shl, dx + 1), shy = __shfl_sync(0xffffffffu, shl, dy + 4),
-                        shz = __shfl_sync(0xffffffffu, shl, dz + 7);
-                const T ox = px - shx, oy = py - shy, oz = pz - shz;
-                for (int jb = b0; jb < b1; jb += 32) {
-                    const int j = jb + lane;
-                    bool ok = false;
-                    T ddx = T(0), ddy = T(0), ddz = T(0), r2 = T(0);
-                    if (j < b1) {
-                        ddx = ox - a.data.x[j];
-                        ddy = oy - a.data.y[j];
-                        ddz = oz - a.data.z[j];
-                        r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        ok = (r2 < R0sq) && (r2 > T(0)) && (j != self);
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, ok);
-                    if (ok) {
-                        const T r = hip_sqrt_b(r2);
-                        const T ir = T(1) / r;
-                        const T W = hip_W<T>(r * invR0);
-                        const T wj = T(a.data.w[j]);
-                        const int slot = qn + __popc(m & lt_mask);
-                        T R[HIP_NLM];
-                        hip_real_ylm<T>(ddx * ir, ddy * ir, ddz * ir, R);
-                        sm.qr[slot] = r;
-                        sm.qw[slot] = wj * W;
-                        sm.qpsi[slot] = wj * wj * W * W;
-#pragma unroll
-                        for (int i = 0; i < HIP_NLM; ++i) sm.qy[slot][i] = R[i];
-                    }
-                    const int nq = __popc(m);
-                    if (is_rand)
-                        cnt_r += nq;
-                    else
-                        cnt_d += nq;
-                    qn += nq;
-                    while (qn >= HIP_BQ) {
-                        // drain the first HIP_BQ entries, move the rest (< 32) down
-                        __syncwarp();
-                        hip_bdrain<T, NCH, NKMAX>(sm, HIP_BQ, kk, kl, k3, k3n, jfac, lane, n_e, E);
-                        __syncwarp();
-                        hip_cterm_any<T, NKMAX>(sm, HIP_BQ, nk, sp, lane, Tc);
-                        const int rest = qn - HIP_BQ;
-                        T mv[3] = {T(0), T(0), T(0)};
-                        if (lane < rest) {
-                            mv[0] = sm.qr[HIP_BQ + lane];
-                            mv[1] = sm.qw[HIP_BQ + lane];
-                            mv[2] = sm.qpsi[HIP_BQ + lane];
-                        }
-                        T my[HIP_NLM];
-#pragma unroll
-                        for (int i = 0; i < HIP_NLM; ++i) my[i] = lane < rest ? sm.qy[HIP_BQ + lane][i] : T(0);
-                        __syncwarp();
-                        if (lane < rest) {
-                            sm.qr[lane] = mv[0];
-                            sm.qw[lane] = mv[1];
-                            sm.qpsi[lane] = mv[2];
-#pragma unroll
-                            for (int i = 0; i < HIP_NLM; ++i) sm.qy[lane][i] = my[i];
-                        }
-                        qn = rest;
-                        __syncwarp();
-                    }
-                }
-            }
-            if (qn > 0) {
-                __syncwarp();
-                hip_bdrain<T, NCH, NKMAX>(sm, qn, kk, kl, k3, k3n, jfac, lane, n_e, E);
-                __syncwarp();
-                hip_cterm_any<T, NKMAX>(sm, qn, nk, sp, lane, Tc);
-                qn = 0;
-            }
-            // edge sums -> A^a_lm = jfac_a (k_{a+1}^3 E_{a+1} - k_a^3 E_a)
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < NCH; ++t) {
-                const int e = lane + 32 * t;
-                if (e < n_e)
-#pragma unroll
-                    for (int i = 0; i < HIP_NLM; ++i) sm.X[e][i] = k3[t] * E[t][i];
-            }
-            __syncwarp();
-            T Aa[NCH][HIP_NLM];
-#pragma unroll
-            for (int t = 0; t < NCH; ++t) {
-                const int e = lane + 32 * t;
-#pragma unroll
-                for (int i = 0; i < HIP_NLM; ++i) Aa[t][i] = e < nk ? jfac[t] * (sm.X[e + 1][i] - sm.X[e][i]) : T(0);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < NCH; ++t) {
-                const int e = lane + 32 * t;
-                if (e < nk)
-#pragma unroll
-                    for (int i = 0; i < HIP_NLM; ++i) sm.X[e][i] = Aa[t][i];
-            }
-            __syncwarp();
-            // contraction: Tc[l][a<=b] += s_p sum_m A^a_lm A^b_lm  (lane owns rows a)
-#pragma unroll
-            for (int t = 0; t < NCH; ++t) {
-                const int aa = lane + 32 * t;
-                if (aa < nk) {
-                    for (int b = aa; b < nk; ++b) {
-#pragma unroll
-                        for (int l = 0; l <= HIP_LMAX; ++l) {
-                            T d = T(0);
-#pragma unroll
-                            for (int mm = -l; mm <= l; ++mm) d += Aa[t][l * l + l + mm] * sm.X[b][l * l + l + mm];
-                            atomicAdd(&Tc[l * ntri + hip_tri(aa, b, nk)], sp * d);
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-        }
+        for (int g = g0; g < g1; ++g)
+            hip_bispec_primary<T, NCH, NKMAX>(a, g, sm, Tc, kk, kl, k3, k3n, jfac, lane, cnt_d, cnt_r);
     }
     __syncthreads();
     double *out = a.partials + (size_t)blockIdx.x * (HIP_LMAX + 1) * nk * nk;
@@ -491,6 +504,112 @@ __global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
         if (cnt_r) atomicAdd(a.npairs + 1, cnt_r);
     }
 }
+
+// Many catalogs in one persistent launch: CTA work items of HIP_BCTA_PRIM
+// primaries (8 per warp) of one catalog, the catalogs' items laid end to end.
+// All warps of a CTA work on the same catalog, so the CTA accumulator Tc serves
+// one catalog at a time: when the CTA moves to another catalog it adds Tc to the
+// previous catalog's FP64 sums (FP64 atomics), clears it and loads the new
+// catalog's edges.
+template <typename T, int NCH, int NKMAX>
+__global__ void __launch_bounds__(HIP_BTHREADS)
+    k_bispec_batched(const BispecCat<T> *__restrict__ cats, int n_cats, int n_items, int *counter)
+{
+    __shared__ BWarpSmem<T, NKMAX> smem[HIP_BWARPS];
+    __shared__ int s_item;
+    extern __shared__ __align__(16) unsigned char tc_raw[];
+    T *Tc = reinterpret_cast<T *>(tc_raw);  // [5][upper triangle of n_k x n_k]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    BWarpSmem<T, NKMAX> &sm = smem[warp];
+    T kk[NCH], kl[NCH], k3[NCH], k3n[NCH], jfac[NCH];
+    unsigned long long cnt_d = 0, cnt_r = 0;
+    int cur = -1;
+    auto leave = [&](int c) {
+        __syncthreads();
+        const int nk = cats[c].a.n_e - 1, ntri = nk * (nk + 1) / 2;
+        double *acc = cats[c].acc;
+        for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) {
+            const int l = i / (nk * nk), ab = i - l * nk * nk, x = ab / nk, y = ab - x * nk;
+            const T v = Tc[l * ntri + (x <= y ? hip_tri(x, y, nk) : hip_tri(y, x, nk))];
+            if (v != T(0)) atomicAdd(&acc[i], (double)v);
+        }
+        if (lane == 0) {  // cnt_d, cnt_r are warp-uniform
+            if (cnt_d) atomicAdd(cats[c].a.npairs, cnt_d);
+            if (cnt_r) atomicAdd(cats[c].a.npairs + 1, cnt_r);
+        }
+        cnt_d = cnt_r = 0;
+        __syncthreads();
+    };
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        int c = cur < 0 ? 0 : cur;
+        while (item >= cats[c].item_end) ++c;
+        while (item < cats[c].item_begin) --c;
+        if (c != cur) {
+            if (cur >= 0) leave(cur);
+            cur = c;
+            const BispecArgs<T> &a = cats[c].a;
+            const int n_e = a.n_e, nk = n_e - 1, ntri = nk * (nk + 1) / 2;
+            for (int i = threadIdx.x; i < (HIP_LMAX + 1) * ntri; i += HIP_BTHREADS) Tc[i] = T(0);
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                const int e = lane + 32 * t;
+                kk[t] = e < n_e ? a.k[e] : T(0);
+                kl[t] = e < n_e ? a.klo[e] : T(0);
+                k3[t] = e < n_e ? a.k3[e] : T(0);
+                k3n[t] = e + 1 < n_e ? a.k3[e + 1] : T(0);
+                jfac[t] = e + 1 < n_e ? a.jfac[e] : T(0);
+            }
+            __syncthreads();
+        }
+        const BispecArgs<T> &a = cats[c].a;
+        const int n_prim = a.n_data + a.n_rand;
+        const int g0 = (item - cats[c].item_begin) * HIP_BCTA_PRIM + warp * HIP_BPRIM;
+        const int g1 = min(g0 + HIP_BPRIM, n_prim);
+        for (int g = g0; g < g1; ++g)
+            hip_bispec_primary<T, NCH, NKMAX>(a, g, sm, Tc, kk, kl, k3, k3n, jfac, lane, cnt_d, cnt_r);
+    }
+    if (cur >= 0) leave(cur);
+}
+
+template <typename T, int NCH, int NKMAX>
+static cudaError_t launch_bispec_batched(const BispecCat<T> *cats, int n_cats, int n_items, int nk_max, int *counter,
+                                         int *grid_out, cudaStream_t st)
+{
+    const size_t dyn = sizeof(T) * (HIP_LMAX + 1) * (nk_max * (nk_max + 1) / 2);
+    cudaError_t e = cudaFuncSetAttribute(k_bispec_batched<T, NCH, NKMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dyn);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bispec_batched<T, NCH, NKMAX>, HIP_BTHREADS, dyn);
+    int grid = sms * (nb < 1 ? 1 : nb);
+    if (grid > n_items) grid = n_items < 1 ? 1 : n_items;
+    *grid_out = grid;
+    k_bispec_batched<T, NCH, NKMAX><<<grid, HIP_BTHREADS, dyn, st>>>(cats, n_cats, n_items, counter);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t hip_bispec_pairs_batched(const BispecCat<T> *cats, int n_cats, int n_items, int nk_max, int *counter,
+                                     int *grid_out, cudaStream_t st)
+{
+    if (nk_max <= 31) return launch_bispec_batched<T, 1, 32>(cats, n_cats, n_items, nk_max, counter, grid_out, st);
+    if constexpr (sizeof(T) == 4) {
+        if (nk_max <= 63)
+            return launch_bispec_batched<T, 2, 64>(cats, n_cats, n_items, nk_max, counter, grid_out, st);
+    }
+    return cudaErrorInvalidValue;
+}
+template cudaError_t hip_bispec_pairs_batched<float>(const BispecCat<float> *, int, int, int, int *, int *,
+                                                     cudaStream_t);
+template cudaError_t hip_bispec_pairs_batched<double>(const BispecCat<double> *, int, int, int, int *, int *,
+                                                      cudaStream_t);
 
 template <typename T, int NCH, int NKMAX>
 static cudaError_t launch_bispec(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st)

@@ -22,11 +22,26 @@ struct BispecArgs {
     T k[HIP_BMAXE], klo[HIP_BMAXE], k3[HIP_BMAXE], jfac[HIP_BMAXE];
 };
 
+// One catalog of a batched bispectrum launch (device-resident descriptor).
+template <typename T>
+struct BispecCat {
+    BispecArgs<T> a;           // the catalog (work_counter and partials unused)
+    int item_begin, item_end;  // CTA work items [begin, end): HIP_BCTA_PRIM primaries each
+    double *acc;               // [5][n_k][n_k] FP64 primary sums of this catalog (atomically added)
+};
+#define HIP_BCTA_PRIM 32       // primaries per CTA work item of the batched launch (4 warps x 8)
+
 // Cell index of every sorted particle from the cell start table.
 cudaError_t hip_sorted_cells(const int *cell_start, int n_cells, int *scell, cudaStream_t st);
 
 template <typename T>
 cudaError_t hip_bispec_pairs(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st);
+
+// One persistent launch over the catalogs' work items laid end to end; nk_max
+// is the largest n_k (<= 31 for FP64, <= 63 for FP32).
+template <typename T>
+cudaError_t hip_bispec_pairs_batched(const BispecCat<T> *cats, int n_cats, int n_items, int nk_max, int *counter,
+                                     int *grid_out, cudaStream_t st);
 
 // T^ab_l = sum of the partial rows (the primary sum before normalisation).
 cudaError_t hip_bispec_sum(const double *partials, int nparts, int nk, int lmax, double *T, cudaStream_t st);

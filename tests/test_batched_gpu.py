@@ -1,5 +1,6 @@
 """Batched power spectra (many catalogs, one persistent pair launch inside a CUDA
-graph) against the FP64 oracle and against single-catalog hip_power calls."""
+graph) and batched bispectra (one persistent launch over all catalogs'
+primaries) against the FP64 oracle and against single-catalog calls."""
 import numpy as np
 import pytest
 
@@ -83,3 +84,35 @@ def test_batched_fp64_host_inputs_and_nonfinite():
     with pytest.raises(binding.HipError) as ei:
         binding.hip_power_batched(bad, "mixed")
     assert ei.value.status == binding.HIP_ERR_NONFINITE
+
+
+def test_bispectrum_batched_matches_single_calls_and_oracle():
+    # three catalogs of different N, L, R0 and bins through ONE batched launch;
+    # each must equal its own hip_bispectrum call (same estimator, other
+    # summation order) and, for one of them, the FP64 oracle
+    import torch
+    specs = [(1200, 60.0, 12.0, (0.3, 2.4, 12), 71), (900, 50.0, 10.0, (0.4, 3.0, 9), 72),
+             (1500, 70.0, 14.0, (0.25, 2.0, 14), 73)]
+    cats = []
+    for N, L, R0, (k0, k1, nk), seed in specs:
+        pos, w = catalogs.thomas(N, L, N // 25, 1.5, seed=seed, background_frac=0.2, weights="u05_15")
+        rnd = catalogs.uniform(3 * N, L, seed=seed + 1)
+        cats.append(dict(pos=torch.from_numpy(pos).cuda(), w=torch.from_numpy(w).cuda(), rand=rnd, L=L, R0=R0,
+                         edges=catalogs.linear_edges(k0, k1, nk), lmax=4, hpos=pos, hw=w))
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-5)):
+        res = binding.hip_bispectrum_batched(cats, prec)
+        for c, (B, (nd, nr)) in zip(cats, res):
+            Bs, (nds, nrs) = binding.hip_bispectrum(c["pos"], c["w"], c["rand"], c["L"], c["R0"], c["edges"], 4, prec)
+            assert (nd, nr) == (nds, nrs)
+            assert _berr(B, Bs) < tol, prec
+    c = cats[1]
+    Bref, _ = oracle.bispectrum(c["hpos"].astype(np.float64), c["hw"].astype(np.float64),
+                                c["rand"].astype(np.float64), c["L"], c["R0"], c["edges"], 4)
+    res = binding.hip_bispectrum_batched(cats, "mixed")
+    assert _berr(res[1][0], Bref) < 1e-4
+
+
+def _berr(B, Bref):
+    floor = 1e-2 * np.max(np.abs(Bref), axis=(1, 2))[:, None, None]
+    scale = np.maximum(np.maximum(np.abs(Bref), np.abs(Bref[0])[None]), floor)
+    return float(np.max(np.abs(B - Bref) / scale))
