@@ -255,6 +255,10 @@ def run_batched(args):
         c["w"] = torch.from_numpy(c["w"]).cuda()
     stream = torch.cuda.Stream()
     plan = binding.BatchPlan(cats, "mixed", stream=stream)
+    tuned = None
+    if args.tune:  # pick the cell shape by timing each candidate once (not part of the timed steps)
+        chosen, tms = plan.tune(stream)
+        tuned = {"chosen_particles_per_cell": chosen, "replay_ms": {str(k): v for k, v in tms.items()}}
     for _ in range(max(1, args.warmup)):
         res = plan.run(stream)
     ts = []
@@ -311,7 +315,8 @@ def run_batched(args):
                       "data": "synthetic", "config": {"workload": "batched64", "catalogs": len(cats),
                                                       "particles": int(sum(int(c["pos"].shape[0]) for c in cats)),
                                                       "pair_bins": int(work)},
-                      "gpu_launches": launches * args.steps, "clocks": clk.summary(), "fp64_plain": fp64}),
+                      "gpu_launches": launches * args.steps, "clocks": clk.summary(), "fp64_plain": fp64,
+                      "autotune": tuned}),
           flush=True)
     return 0
 
@@ -521,6 +526,7 @@ def main():
     ap.add_argument("--bk-only", action="store_true", help="time only the bispectrum workload")
     ap.add_argument("--batched", action="store_true", help="time the 64-catalog batched workload")
     ap.add_argument("--large", action="store_true", help="time P and B on the 256^3 Zel'dovich lattice")
+    ap.add_argument("--tune", action="store_true", help="--batched: autotune the plan's cell shape first")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the catalog volume at fixed density (profiler captures only)")
     args = ap.parse_args()

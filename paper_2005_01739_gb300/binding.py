@@ -84,6 +84,8 @@ def load(path: str | None = None):
         L.hip_power_batched.argtypes = [P, i, i, P]
         L.hip_batch_message.restype = ctypes.c_char_p
         L.hip_batch_message.argtypes = []
+        L.hip_batch_plan_tune.restype = i
+        L.hip_batch_plan_tune.argtypes = [P, P, P, P]
         L.hip_bispectrum_batched.restype = i
         L.hip_bispectrum_batched.argtypes = [P, i, i, P]
         L.hip_bispectrum_partial.restype = i
@@ -231,6 +233,17 @@ class BatchPlan:
             raise HipError(rc, f"hip_batch_plan_run: {self._lib.hip_status_string(rc).decode()} "
                                f"({self._lib.hip_batch_message().decode()})")
         return [(P.copy(), DD.copy(), int(n[0])) for P, DD, n in self.results]
+
+    def tune(self, stream=None):
+        """Autotune the plan's cell shape (hip_batch_plan_tune): returns (chosen
+        target particles per cell, 0 = cells R0 wide; {candidate: replay ms})."""
+        chosen = ctypes.c_int(0)
+        ms = (ctypes.c_float * 6)()
+        rc = self._lib.hip_batch_plan_tune(self._plan, _stream_handle(stream), ctypes.byref(chosen), ms)
+        if rc != 0:
+            raise HipError(rc, f"hip_batch_plan_tune: {self._lib.hip_status_string(rc).decode()} "
+                               f"({self._lib.hip_batch_message().decode()})")
+        return int(chosen.value), dict(zip((4, 8, 16, 32, 64, 0), (float(x) for x in ms)))
 
     def close(self):
         if self._plan:

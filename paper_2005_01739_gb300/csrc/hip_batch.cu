@@ -31,12 +31,14 @@ struct CatLayout {
 };
 
 // Cells per side for a batched catalog: at least R0 wide, and no more cells
-// than about one per 16 particles (sparse catalogs otherwise spend their time
-// on empty work items).
-int batch_cells_per_side(const hip_catalog &c)
+// than about one per `occ` particles (sparse catalogs otherwise spend their time
+// on empty work items; occ = 0: cells R0 wide whatever the occupancy).  occ is
+// the plan's tunable (hip_batch_plan_tune).
+int batch_cells_per_side(const hip_catalog &c, int occ)
 {
     int n = hip_cells_per_side(c.L, c.R0);
-    const int by_occ = std::max(1, (int)std::floor(std::cbrt((double)c.N / 16.0)));
+    if (occ <= 0) return n;
+    const int by_occ = std::max(1, (int)std::floor(std::cbrt((double)c.N / (double)occ)));
     return std::max(1, std::min(n, by_occ));
 }
 
@@ -66,6 +68,7 @@ struct hip_batch_plan {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;
     int launches = 0;
+    int occ = 16;  // target particles per cell (see batch_cells_per_side)
 };
 
 extern "C" const char *hip_batch_message(void) { return g_batch_msg; }
@@ -91,7 +94,7 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
         CatLayout &L = pl->lay[i];
         L.dev_pos = hip_is_device_ptr(c.pos);
         L.dev_w = c.w && hip_is_device_ptr(c.w);
-        L.n_c = batch_cells_per_side(c);
+        L.n_c = batch_cells_per_side(c, pl->occ);
         L.n_cells = L.n_c * L.n_c * L.n_c;
         L.n_e = c.n_k + 1;
         L.n_ell = c.ell_max / 2 + 1;
@@ -263,14 +266,27 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
     return HIP_OK;
 }
 
-static void plan_free(hip_batch_plan *pl)
+// Release what plan_build made (graph, buffers, capture stream); the catalogs stay.
+static void plan_release(hip_batch_plan *pl)
 {
-    if (!pl) return;
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->buf) cudaFree(pl->buf);
     if (pl->h_out) cudaFreeHost(pl->h_out);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    pl->exec = nullptr;
+    pl->graph = nullptr;
+    pl->buf = nullptr;
+    pl->h_out = nullptr;
+    pl->cap_stream = nullptr;
+    pl->out_off.clear();
+    pl->launches = 0;
+}
+
+static void plan_free(hip_batch_plan *pl)
+{
+    if (!pl) return;
+    plan_release(pl);
     delete pl;
 }
 
@@ -307,13 +323,12 @@ extern "C" hip_status hip_batch_plan_create(const hip_catalog *cats, int n_cats,
 
 extern "C" int hip_batch_plan_launches(const hip_batch_plan *plan) { return plan ? plan->launches : 0; }
 
-extern "C" hip_status hip_batch_plan_run(hip_batch_plan *pl, void *cuda_stream)
+// Copy host inputs, replay the graph, check and unpack (caller holds the API lock).
+// If ms is given, the graph replay alone is timed with events on st.
+static hip_status plan_run_locked(hip_batch_plan *pl, cudaStream_t st, float *ms)
 {
-    g_batch_msg[0] = 0;
-    if (!pl) return HIP_ERR_ARG;
-    std::lock_guard<std::mutex> lk(hip_api_mutex());
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     cudaError_t e;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     char *b = (char *)pl->buf;
     const int nc = (int)pl->cats.size();
     for (int i = 0; i < nc; ++i) {
@@ -326,8 +341,20 @@ extern "C" hip_status hip_batch_plan_run(hip_batch_plan *pl, void *cuda_stream)
             (e = cudaMemcpyAsync(b + L.o_w, c.w, sizeof(float) * c.N, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             goto fail;
     }
+    if (ms) {
+        if ((e = cudaEventCreate(&ev0)) != cudaSuccess || (e = cudaEventCreate(&ev1)) != cudaSuccess ||
+            (e = cudaEventRecord(ev0, st)) != cudaSuccess)
+            goto fail;
+    }
     if ((e = cudaGraphLaunch(pl->exec, st)) != cudaSuccess) goto fail;
+    if (ms && (e = cudaEventRecord(ev1, st)) != cudaSuccess) goto fail;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) goto fail;
+    if (ms) {
+        if ((e = cudaEventElapsedTime(ms, ev0, ev1)) != cudaSuccess) goto fail;
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        ev0 = ev1 = nullptr;
+    }
     for (int i = 0; i < nc; ++i) {
         const size_t n = (size_t)pl->lay[i].n_ell * pl->cats[i].n_k;
         int errw;
@@ -349,8 +376,53 @@ extern "C" hip_status hip_batch_plan_run(hip_batch_plan *pl, void *cuda_stream)
     }
     return HIP_OK;
 fail:
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
     std::snprintf(g_batch_msg, sizeof(g_batch_msg), "run: %s", cudaGetErrorString(e));
     return HIP_ERR_CUDA;
+}
+
+extern "C" hip_status hip_batch_plan_run(hip_batch_plan *pl, void *cuda_stream)
+{
+    g_batch_msg[0] = 0;
+    if (!pl) return HIP_ERR_ARG;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    return plan_run_locked(pl, (cudaStream_t)cuda_stream, nullptr);
+}
+
+// Candidate target occupancies of the autotuner (particles per cell; 0 = cells
+// exactly R0 wide).
+static const int k_tune_occ[] = {4, 8, 16, 32, 64, 0};
+
+extern "C" hip_status hip_batch_plan_tune(hip_batch_plan *pl, void *cuda_stream, int *chosen_out, float *ms_out)
+{
+    g_batch_msg[0] = 0;
+    if (!pl) return HIP_ERR_ARG;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int nt = (int)(sizeof(k_tune_occ) / sizeof(k_tune_occ[0]));
+    int best = -1;
+    float best_ms = 0.0f;
+    for (int i = 0; i < nt; ++i) {
+        plan_release(pl);
+        pl->occ = k_tune_occ[i];
+        hip_status hs = pl->prec == HIP_PREC_MIXED ? plan_build<float>(pl, st) : plan_build<double>(pl, st);
+        if (hs == HIP_OK) hs = plan_run_locked(pl, st, nullptr);  // warm-up
+        float ms = 0.0f;
+        if (hs == HIP_OK) hs = plan_run_locked(pl, st, &ms);
+        if (hs != HIP_OK) return hs;
+        if (ms_out) ms_out[i] = ms;
+        if (best < 0 || ms < best_ms) {
+            best = i;
+            best_ms = ms;
+        }
+    }
+    plan_release(pl);
+    pl->occ = k_tune_occ[best];
+    hip_status hs = pl->prec == HIP_PREC_MIXED ? plan_build<float>(pl, st) : plan_build<double>(pl, st);
+    if (hs != HIP_OK) return hs;
+    if (chosen_out) *chosen_out = pl->occ;
+    return HIP_OK;
 }
 
 extern "C" void hip_batch_plan_destroy(hip_batch_plan *plan)

@@ -116,3 +116,20 @@ def _berr(B, Bref):
     floor = 1e-2 * np.max(np.abs(Bref), axis=(1, 2))[:, None, None]
     scale = np.maximum(np.maximum(np.abs(Bref), np.abs(Bref[0])[None]), floor)
     return float(np.max(np.abs(B - Bref) / scale))
+
+
+def test_plan_autotune_keeps_results():
+    # the autotuner only changes the cell shape; every candidate gives the same
+    # estimator, so the tuned plan's output matches the untuned one
+    cats = [c for c, _, _ in _batch(True)]
+    plan = binding.BatchPlan(cats, "mixed")
+    try:
+        before = [(P, n) for P, _, n in plan.run()]
+        chosen, ms = plan.tune()
+        assert chosen in (4, 8, 16, 32, 64, 0) and all(v > 0 for v in ms.values())
+        after = plan.run()
+        for (P0, n0), (P1, _, n1) in zip(before, after):
+            assert _err(P1, P0) < 1e-5
+            assert abs(n1 - n0) <= max(2, int(2e-6 * n0))
+    finally:
+        plan.close()
