@@ -17,7 +17,10 @@ What is computed, and where each piece comes from:
   AC-def, binned form of Sec. 4.4).
 * this module -- the analytic random-pair terms and the final estimators:
   the binned window transform W~^a (Eq. wka-def) by composite Gauss-Legendre
-  quadrature, P^a_l (binned estimator of Sec. 3) and B^ab_l (summary, Sec. 4.5).
+  quadrature, P^a_l (binned estimator of Sec. 3) and B^ab_l (summary, Sec. 4.5);
+  and the random-free DDR^II term of App. A: omega^a_l (Eq. omega-ell-a-def),
+  the kernel E^{II,ab}_l(r) = int p^2 dp/(2 pi^2) j_0(p r) omega^a_l omega^b_l and
+  the pair sum over it, with the bipolar form of App. B for cross-checks.
 """
 from __future__ import annotations
 
@@ -262,3 +265,127 @@ def bispectrum(pos, w, rand_pos, L, R0, edges, lmax=4, data_primaries=None, rand
     S1 = float(np.sum(wv))
     B = bispectrum_from_sums(Td, Tr, DD[0], S1, rp.shape[0], L, Wt)
     return B, dict(Tdata=Td, Trand=Tr, S=DD[0], Wt=Wt, npairs_data=npd, npairs_rand=npr)
+
+
+# ------------------------------------------------ random-free DDR^II (App. A) --
+def _sph_jn_vec(l: int, z):
+    """Spherical Bessel j_l (library routine, vectorised)."""
+    from scipy.special import spherical_jn
+    return spherical_jn(l, z)
+
+
+def _jbar_table(l: int, edges, rs) -> np.ndarray:
+    """jbar^a_l(r) for every bin a at the nodes rs: [n_k][len(rs)]."""
+    edges = np.asarray(edges, dtype=np.float64)
+    return np.array([[jbar(l, r, edges[a], edges[a + 1]) for r in rs] for a in range(len(edges) - 1)])
+
+
+def _r_nodes(R0: float, hmax: float):
+    """Composite Gauss-Legendre nodes on the three polynomial pieces of W."""
+    pts, wts = [], []
+    for lo, hi in ((0.0, 0.5 * R0), (0.5 * R0, 0.75 * R0), (0.75 * R0, R0)):
+        x, wq = _gl_panels(lo, hi, hmax)
+        pts.append(x)
+        wts.append(wq)
+    return np.concatenate(pts), np.concatenate(wts)
+
+
+def e2_p_nodes(edges, R0: float, pmax_factor: float = 1.0):
+    """The p quadrature of the E^II integrals: composite Gauss-Legendre on
+    [0, p_max], p_max = k_hi + 120/R0 (times pmax_factor), panels no wider than
+    pi/(8 R0) (j_0(p r) with r < 2 R0 oscillates at most once per 2 pi/(2 R0))."""
+    k_hi = float(np.max(edges))
+    pmax = pmax_factor * (k_hi + 120.0 / R0)
+    return _gl_panels(0.0, pmax, np.pi / (8.0 * R0))
+
+
+def omega_binned(l: int, edges, R0: float, p) -> np.ndarray:
+    """omega^a_l(p) = 4 pi int_0^R0 r^2 j_l(p r) jbar^a_l(r) W(r/R0) dr
+    (Eq. omega-ell-a-def): [n_k][len(p)], composite Gauss-Legendre in r."""
+    p = np.atleast_1d(np.asarray(p, dtype=np.float64))
+    kmax = max(float(np.max(edges)), float(np.max(p)) if p.size else 0.0)
+    rs, rw = _r_nodes(R0, np.pi / (4.0 * max(kmax, 1.0 / R0)))
+    Wr = np.array([window(r / R0) for r in rs])
+    JB = _jbar_table(l, edges, rs)
+    jl = _sph_jn_vec(l, np.outer(p, rs))  # [p][r]
+    return 4.0 * np.pi * np.einsum("pr,ar,r->ap", jl, JB * (Wr * rs * rs)[None, :], rw)
+
+
+def e2_kernel(l: int, edges, R0: float, x, pmax_factor: float = 1.0) -> np.ndarray:
+    """E^{II,ab}_l(x) = int p^2 dp/(2 pi^2) j_0(p x) omega^a_l(p) omega^b_l(p)
+    (binned kernel of App. A): [len(x)][n_k][n_k]."""
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    ps, pw = e2_p_nodes(edges, R0, pmax_factor)
+    om = omega_binned(l, edges, R0, ps)
+    j0 = np.sinc(np.outer(x, ps) / np.pi)  # j_0(p x)
+    return np.einsum("xp,p,ap,bp->xab", j0, pw * ps * ps / (2.0 * np.pi ** 2), om, om)
+
+
+def e2_kernel_bipolar(l: int, edges, R0: float, x: float, n_panel: int = 24) -> np.ndarray:
+    """The same kernel from the bipolar double integral of App. B:
+    2 pi int int dr1 dr2 (r1 r2 / x) jbar^a_l(r1) jbar^b_l(r2) W(r1) W(r2) L_l(Delta),
+    Delta = (r1^2 + r2^2 - x^2)/(2 r1 r2), over |r1 - r2| <= x <= r1 + r2
+    (cross-check only; slow)."""
+    edges = np.asarray(edges, dtype=np.float64)
+    nk = len(edges) - 1
+    out = np.zeros((nk, nk))
+    lo1 = max(0.0, x - R0)
+    r1s, w1s = _gl_panels(lo1, R0, (R0 - lo1) / n_panel)
+    for r1, w1 in zip(r1s, w1s):
+        lo, hi = abs(x - r1), min(R0, x + r1)
+        if hi <= lo:
+            continue
+        r2s, w2s = _gl_panels(lo, hi, (hi - lo) / max(2, n_panel // 2))
+        f1 = np.array([jbar(l, r1, edges[a], edges[a + 1]) for a in range(nk)]) * window(r1 / R0)
+        f2 = _jbar_table(l, edges, r2s) * np.array([window(r / R0) for r in r2s])[None, :]
+        D = np.clip((r1 * r1 + r2s ** 2 - x * x) / (2.0 * r1 * r2s), -1.0, 1.0)
+        Ll = np.array([legendre(l, d) for d in D])
+        out += w1 * np.outer(f1, f2 @ (w2s * r1 * r2s / x * Ll))
+    return 2.0 * np.pi * out
+
+
+def ddr2_pair_sum(pos, w, L, R0, edges, lmax=4, pmax_factor: float = 1.0) -> np.ndarray:
+    """sum over ordered pairs i != j of w_i w_j E^{II,ab}_l(|x_i - x_j|) (minimum
+    image; E^II vanishes beyond 2 R0, so only pairs closer than 2 R0 enter):
+    [lmax+1][n_k][n_k].  The sum over pairs is taken inside the p integral:
+    sum_ij w_i w_j E(r_ij) = int p^2 dp/(2 pi^2) S(p) omega^a omega^b with
+    S(p) = sum_ij w_i w_j j_0(p r_ij).  Brute force over all pairs (small N)."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    N = pos.shape[0]
+    wv = np.ones(N) if w is None else np.asarray(w, dtype=np.float64)
+    rr, ww = [], []
+    for i in range(N):
+        d = pos[i + 1:] - pos[i]
+        d -= L * np.round(d / L)
+        r = np.sqrt(np.sum(d * d, axis=1))
+        m = (r < 2.0 * R0) & (r > 0.0)
+        rr.append(r[m])
+        ww.append(2.0 * wv[i] * wv[i + 1:][m])  # both orders
+    rr = np.concatenate(rr)
+    ww = np.concatenate(ww)
+    ps, pw = e2_p_nodes(edges, R0, pmax_factor)
+    S = np.array([np.sum(ww * np.sinc(p * rr / np.pi)) for p in ps])
+    nk = len(edges) - 1
+    out = np.zeros((lmax + 1, nk, nk))
+    for l in range(lmax + 1):
+        om = omega_binned(l, edges, R0, ps)
+        out[l] = np.einsum("p,ap,bp->ab", pw * ps * ps / (2.0 * np.pi ** 2) * S, om, om)
+    return out
+
+
+def bispectrum_analytic(pos, w, L, R0, edges, lmax=4):
+    """B^ab_l with the DDR^II term from the E^II kernel instead of a random
+    catalog (App. A): the random primaries' sum (S1/N_r) sum_r G(x_r) -> its
+    expectation (S1/V) sum_{i != j} w_i w_j E^{II,ab}_l(r_ij)."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    N = pos.shape[0]
+    wv = np.ones(N) if w is None else np.asarray(w, dtype=np.float64)
+    Td, npd = bispectrum_primary_sum(pos, wv, np.arange(N), pos, w, L, R0, edges, lmax)
+    E2 = ddr2_pair_sum(pos, w, L, R0, edges, lmax)
+    DD, _ = power_pair_sum(pos, w, L, R0, edges, 0, 2)
+    Wt = window_transform_binned(edges, R0)
+    S1 = float(np.sum(wv))
+    V = float(L) ** 3
+    # bispectrum_from_sums subtracts (S1/N_r) Trand; pass Trand = E2 N_r / V with N_r = 1
+    B = bispectrum_from_sums(Td, E2 / V, DD[0], S1, 1.0, L, Wt)
+    return B, dict(Tdata=Td, E2=E2, S=DD[0], Wt=Wt, npairs_data=npd)

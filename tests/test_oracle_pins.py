@@ -388,3 +388,78 @@ def test_bispectrum_null_mean():
     bias = 5.0 * np.abs(np.outer(Wt, Wt)) / N
     assert np.all(np.abs(mean[0]) < 4 * se[0] + bias)
     assert np.all(np.abs(mean[1:]) < 4 * se[1:] + 1e-12 * np.max(np.abs(Bs)))
+
+
+# ------------------------------------------- random-free DDR^II (App. A / B) --
+_E2_EDGES = np.linspace(0.4, 2.0, 7)
+
+
+def test_e2_kernel_fourier_matches_bipolar_and_origin():
+    # App. A (p integral over omega^a omega^b) and App. B (bipolar double integral)
+    # are two derivations of the same kernel; at x = 0 both reduce to
+    # 4 pi int r^2 jbar^a jbar^b W^2 dr (L_l(1) = 1).
+    R0 = 8.0
+    for l, x in ((0, 2.0), (2, 7.5), (4, 12.0)):
+        Ef = oracle.e2_kernel(l, _E2_EDGES, R0, [x])[0]
+        Eb = oracle.e2_kernel_bipolar(l, _E2_EDGES, R0, x)
+        assert np.max(np.abs(Ef - Eb)) < 1e-7 * np.max(np.abs(Ef)), (l, x)
+    for l in (0, 3):
+        E0 = oracle.e2_kernel(l, _E2_EDGES, R0, [0.0])[0]
+        rs, wq = oracle._gl_panels(0.0, R0, R0 / 64)
+        f = np.array([[oracle.jbar(l, r, _E2_EDGES[a], _E2_EDGES[a + 1]) * oracle.window(r / R0) for r in rs]
+                      for a in range(6)])
+        direct = 4.0 * np.pi * np.einsum("ar,br,r->ab", f, f, wq * rs * rs)
+        assert np.max(np.abs(E0 - direct)) < 1e-8 * np.max(np.abs(direct)), l
+
+
+def test_e2_kernel_vanishes_beyond_two_R0_and_converges_in_p():
+    R0 = 8.0
+    E0 = np.max(np.abs(oracle.e2_kernel(0, _E2_EDGES, R0, [0.0])[0]))
+    far = oracle.e2_kernel(2, _E2_EDGES, R0, [2.05 * R0, 2.5 * R0])
+    assert np.max(np.abs(far)) < 1e-7 * E0
+    a = oracle.e2_kernel(4, _E2_EDGES, R0, [3.0, 9.0])
+    b = oracle.e2_kernel(4, _E2_EDGES, R0, [3.0, 9.0], pmax_factor=2.0)
+    assert np.max(np.abs(a - b)) < 1e-9 * E0
+
+
+def test_ddr2_pair_sum_is_the_kernel_summed_over_pairs():
+    rng = np.random.default_rng(3)
+    L, R0 = 30.0, 6.0
+    pos = rng.uniform(0, L, (25, 3))
+    w = rng.uniform(0.5, 1.5, 25)
+    S = oracle.ddr2_pair_sum(pos, w, L, R0, _E2_EDGES, lmax=2)
+    rs, ws = [], []
+    for i in range(25):
+        for j in range(25):
+            d = pos[i] - pos[j]
+            d -= L * np.round(d / L)
+            r = float(np.sqrt(d @ d))
+            if i != j and r < 2 * R0:
+                rs.append(r)
+                ws.append(w[i] * w[j])
+    direct = np.array([np.einsum("x,xab->ab", np.array(ws), oracle.e2_kernel(l, _E2_EDGES, R0, rs))
+                       for l in range(3)])
+    assert np.max(np.abs(S - direct)) < 1e-10 * np.max(np.abs(direct))
+
+
+def test_ddr2_is_the_expectation_of_the_random_catalog_term():
+    # the random primaries' sum (1/N_r) sum_r G(x_r) is a Monte Carlo estimate of
+    # (1/V) sum_{i != j} w_i w_j E^II(r_ij): they must agree within the sampling
+    # error (estimated from independent batches of randoms)
+    L, R0 = 30.0, 6.0
+    rng = np.random.default_rng(11)
+    parents = rng.uniform(0, L, (8, 3))
+    pos = np.mod(parents[rng.integers(0, 8, 70)] + rng.normal(0, 1.5, (70, 3)), L)
+    w = rng.uniform(0.5, 1.5, 70)
+    edges = np.linspace(0.4, 2.0, 5)
+    E2 = oracle.ddr2_pair_sum(pos, w, L, R0, edges, lmax=4) / L ** 3
+    batches = []
+    for b in range(6):
+        rnd = rng.uniform(0, L, (40000, 3))
+        T, _ = oracle.bispectrum_primary_sum(rnd, np.ones(len(rnd)), None, pos, w, L, R0, edges, 4)
+        batches.append(T / len(rnd))
+    batches = np.array(batches)
+    mean, err = batches.mean(axis=0), batches.std(axis=0, ddof=1) / np.sqrt(len(batches))
+    z = np.abs(mean - E2) / np.maximum(err, 1e-12 * np.max(np.abs(E2)))
+    assert np.max(z) < 5.0, float(np.max(z))
+    assert np.max(np.abs(mean - E2)) < 0.05 * np.max(np.abs(E2))
