@@ -109,6 +109,22 @@ hip_status hip_bispectrum(const float *pos, const float *w, int64_t N, const flo
                           double R0, hip_window window, const double *k_edges, int n_k, int lmax, hip_precision prec,
                           double *B_out, int64_t *npairs_out, void *cuda_stream);
 
+/* Isotropic bispectrum multipoles without a random catalog (App. A of the paper):
+ * as hip_bispectrum, but the random primaries' term (S1/N_r) sum_r G(x_r) is
+ * replaced by its expectation (S1/V) sum_{j != k} w_j w_k E^{II,ab}_l(r_jk), with
+ * the kernel E^{II,ab}_l(r) = int p^2 dp/(2 pi^2) j_0(p r) omega^a_l(p) omega^b_l(p)
+ * (omega^a_l of Eq. omega-ell-a-def), which vanishes beyond 2 R0.  The pair sum is
+ * taken inside the p integral from a 16384-bin histogram of the separations below
+ * 2 R0 that keeps the first two moments of r in each bin (FP64), so the result is
+ * exact to third order in the bin width 2 R0 / 16384.
+ *   pos, w, N, L, R0, window, k_edges, n_k, lmax, prec, B_out, cuda_stream  as in
+ *                    hip_bispectrum (no randoms), except R0 < L/4 (HIP_ERR_RANGE)
+ *   npairs_out       [1] or NULL: ordered (primary, data) pairs within R0
+ */
+hip_status hip_bispectrum_analytic(const float *pos, const float *w, int64_t N, double L, double R0,
+                                   hip_window window, const double *k_edges, int n_k, int lmax, hip_precision prec,
+                                   double *B_out, int64_t *npairs_out, void *cuda_stream);
+
 /* The bispectrum's primary sum over chosen primaries, for sharding and sampled
  * checks: T_out = sum_{i in data range} w_i G^ab_l(x_i) - (S1/N_r) sum_{r in random
  * range} G^ab_l(x_r), with G as in hip_bispectrum (before the normalisation and

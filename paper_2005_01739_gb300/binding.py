@@ -86,6 +86,8 @@ def load(path: str | None = None):
         L.hip_batch_message.argtypes = []
         L.hip_batch_plan_tune.restype = i
         L.hip_batch_plan_tune.argtypes = [P, P, P, P]
+        L.hip_bispectrum_analytic.restype = i
+        L.hip_bispectrum_analytic.argtypes = [P, P, i64, d, d, i, P, i, i, i, P, P, P]
         L.hip_bispectrum_batched.restype = i
         L.hip_bispectrum_batched.argtypes = [P, i, i, P]
         L.hip_bispectrum_partial.restype = i
@@ -286,6 +288,25 @@ def hip_bispectrum(pos, w, rand_pos, L, R0, k_edges, lmax=4, prec="mixed", strea
     _check(lib, rc, "hip_bispectrum")
     del keep_p, keep_w, keep_r
     return B, (int(npairs[0]), int(npairs[1]))
+
+
+def hip_bispectrum_analytic(pos, w, L, R0, k_edges, lmax=4, prec="mixed", stream=None):
+    """B^ab_l with the random-free DDR^II term (App. A; no random catalog).
+    Returns (B [lmax+1, n_k, n_k], ordered (primary, data) pairs within R0)."""
+    lib = load()
+    n = int(pos.shape[0]) if hasattr(pos, "shape") else len(pos)
+    pp, keep_p = _ptr(pos)
+    wp, keep_w = _ptr(w)
+    edges = np.ascontiguousarray(np.asarray(k_edges, dtype=np.float64))
+    n_k = len(edges) - 1
+    B = np.zeros((lmax + 1, n_k, n_k))
+    npairs = (ctypes.c_int64 * 1)()
+    rc = lib.hip_bispectrum_analytic(pp, wp, n, float(L), float(R0), 0, edges.ctypes.data_as(ctypes.c_void_p), n_k,
+                                     int(lmax), PREC[prec], B.ctypes.data_as(ctypes.c_void_p), npairs,
+                                     _stream_handle(stream))
+    _check(lib, rc, "hip_bispectrum_analytic")
+    del keep_p, keep_w
+    return B, int(npairs[0])
 
 
 def hip_bispectrum_batched(catalogs, prec="mixed", stream=None):

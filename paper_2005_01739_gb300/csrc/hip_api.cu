@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "hip_bispec.h"
+#include "hip_e2.h"
 #include "hip_internal.h"
 #include "hip_workspace.h"
 
@@ -54,7 +55,8 @@ hip_status hip_device_setup(int *dev_out)
     }
     if (dev < 0 || dev >= 64) return HIP_ERR_ARG;
     if (!g_coeffs_ready[dev]) {
-        if ((e = hip_upload_coeffs_power()) != cudaSuccess || (e = hip_upload_coeffs_bispec()) != cudaSuccess) {
+        if ((e = hip_upload_coeffs_power()) != cudaSuccess || (e = hip_upload_coeffs_bispec()) != cudaSuccess ||
+            (e = hip_upload_coeffs_e2()) != cudaSuccess) {
             set_err("coefficient upload", e);
             return HIP_ERR_CUDA;
         }
@@ -699,6 +701,169 @@ extern "C" hip_status hip_bispectrum_batched(const hip_bcatalog *cats, int n_cat
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (prec == HIP_PREC_MIXED) return bispec_batched_impl<float>(cats, n_cats, st, dev);
     return bispec_batched_impl<double>(cats, n_cats, st, dev);
+}
+
+// Bispectrum with the random-free DDR^II term (App. A): data primaries only,
+// plus one FP64 partial row -(S1/V) sum_{j != k} w_j w_k E^{II}(r_jk) from
+// hip_e2_term (pairs to 2 R0 on a second cell list of cells >= 2 R0 wide).
+template <typename T>
+static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t N, double L, double R0,
+                                       const double *k_edges, int n_k, int lmax, double *B_out, int64_t *npairs_out,
+                                       cudaStream_t st, int dev)
+{
+    Workspace &ws = hip_workspace(dev);
+    const int n_c = hip_cells_per_side(L, R0), n_cells = n_c * n_c * n_c;
+    const int n_c2 = hip_cells_per_side(L, 2.0 * R0), n_cells2 = n_c2 * n_c2 * n_c2;
+    const int n_e = n_k + 1;
+    const int pgrid = hip_power_grid<T>();
+    const bool dpos = hip_is_device_ptr(pos), dw = w && hip_is_device_ptr(w);
+    const int bparts_max = 152 * 8;
+    const size_t tsz = (size_t)(HIP_LMAX + 1) * n_k * n_k;
+    E2Nodes nodes;
+    hip_e2_nodes(k_edges, n_k, R0, nodes);
+
+    Carve cv;
+    const size_t o_pos = dpos ? 0 : cv.take(sizeof(float) * 3 * N);
+    const size_t o_w = (w && !dw) ? cv.take(sizeof(float) * N) : 0;
+    const size_t o_dx = cv.take(sizeof(T) * N), o_dy = cv.take(sizeof(T) * N), o_dz = cv.take(sizeof(T) * N);
+    const size_t o_dw = cv.take(sizeof(float) * N), o_didx = cv.take(sizeof(int) * N), o_dcid = cv.take(sizeof(int) * N);
+    const size_t o_ds = cv.take(sizeof(int) * (n_cells + 1)), o_df = cv.take(sizeof(int) * n_cells);
+    const size_t o_dsc = cv.take(sizeof(int) * N);
+    const size_t o_x2 = cv.take(sizeof(float) * N), o_y2 = cv.take(sizeof(float) * N), o_z2 = cv.take(sizeof(float) * N);
+    const size_t o_w2 = cv.take(sizeof(float) * N), o_i2 = cv.take(sizeof(int) * N), o_c2 = cv.take(sizeof(int) * N);
+    const size_t o_s2 = cv.take(sizeof(int) * (n_cells2 + 1)), o_f2 = cv.take(sizeof(int) * n_cells2);
+    const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * n_e);
+    const size_t o_bp = cv.take(sizeof(double) * (bparts_max + 1) * tsz);
+    const size_t o_small = cv.take(sizeof(double) * 16);
+    const size_t o_wt = cv.take(sizeof(double) * n_k), o_dd = cv.take(sizeof(double) * 3 * n_k);
+    const size_t o_p = cv.take(sizeof(double) * 3 * n_k), o_b = cv.take(sizeof(double) * tsz);
+    const size_t o_e2 = cv.take(hip_e2_scratch_bytes(nodes, n_k));
+    hip_status hs = ws.reserve(cv.total, st);
+    if (hs != HIP_OK) return hs;
+    char *b = (char *)ws.base;
+    cudaError_t e;
+#define HIP_CK(call, what)                                                                                           \
+    do {                                                                                                             \
+        if ((e = (call)) != cudaSuccess) {                                                                           \
+            set_err(what, e);                                                                                        \
+            return HIP_ERR_CUDA;                                                                                     \
+        }                                                                                                            \
+    } while (0)
+    const float *dposp = pos, *dwp = w;
+    if (!dpos) {
+        HIP_CK(cudaMemcpyAsync(b + o_pos, pos, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st), "H2D positions");
+        dposp = (const float *)(b + o_pos);
+    }
+    if (w && !dw) {
+        HIP_CK(cudaMemcpyAsync(b + o_w, w, sizeof(float) * N, cudaMemcpyHostToDevice, st), "H2D weights");
+        dwp = (const float *)(b + o_w);
+    }
+    double *small = (double *)(b + o_small);
+    double *S1 = small, *S1b = small + 1;
+    unsigned long long *npairs = (unsigned long long *)(small + 2);  // [0]: P pass; [1], [2]: B pass
+    int *err = (int *)(small + 5), *err2 = err + 1;
+    int *counter = (int *)(small + 6), *bcounter = counter + 1, *hcounter = counter + 2;
+    T *dx = (T *)(b + o_dx), *dy = (T *)(b + o_dy), *dz = (T *)(b + o_dz);
+    int *dstart = (int *)(b + o_ds);
+    HIP_CK(hip_build_cells<T>(dposp, dwp, N, L, n_c, dx, dy, dz, (float *)(b + o_dw), (int *)(b + o_didx),
+                              (int *)(b + o_dcid), dstart, (int *)(b + o_df), S1, err, st),
+           "cell build (R0)");
+    HIP_CK(hip_build_cells<float>(dposp, dwp, N, L, n_c2, (float *)(b + o_x2), (float *)(b + o_y2),
+                                  (float *)(b + o_z2), (float *)(b + o_w2), (int *)(b + o_i2), (int *)(b + o_c2),
+                                  (int *)(b + o_s2), (int *)(b + o_f2), S1b, err2, st),
+           "cell build (2 R0)");
+    HIP_CK(hip_sorted_cells(dstart, n_cells, (int *)(b + o_dsc), st), "sorted cells");
+    int herr[2] = {0, 0};
+    HIP_CK(cudaMemcpyAsync(herr, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "D2H error word");
+    HIP_CK(cudaStreamSynchronize(st), "cell build sync");
+    if (herr[0] || herr[1]) return HIP_ERR_NONFINITE;
+
+    CellList<T> dcl{dx, dy, dz, (const float *)(b + o_dw), (const int *)(b + o_didx), dstart, n_c, L, L / n_c};
+    HIP_CK(cudaMemsetAsync(npairs, 0, 3 * sizeof(unsigned long long), st), "memset");
+    HIP_CK(cudaMemsetAsync(counter, 0, 3 * sizeof(int), st), "memset");
+    PowerKernelArgs ka;
+    ka.n_e = n_e;
+    ka.los = 2;
+    ka.p0 = 0;
+    ka.p1 = N;
+    ka.n_items = n_cells * HIP_NSHIFT;
+    ka.work_counter = counter;
+    ka.partials = (double *)(b + o_pp);
+    ka.npairs = npairs;
+    HIP_CK(hip_power_pairs<T>(dcl, ka, k_edges, 1, R0, pgrid, st), "pair kernel (S)");
+    double *Wt = (double *)(b + o_wt), *DD = (double *)(b + o_dd), *P = (double *)(b + o_p);
+    HIP_CK(hip_power_finalize(ka.partials, pgrid, n_e, 1, k_edges, R0, L, S1, Wt, DD, P, st), "finalize (S)");
+
+    BispecArgs<T> ba;
+    std::memset(&ba, 0, sizeof(ba));
+    ba.data = dcl;
+    ba.rand = dcl;  // no random primaries
+    ba.n_cells = n_cells;
+    ba.dcell = (const int *)(b + o_dsc);
+    ba.rcell = (const int *)(b + o_dsc);
+    ba.n_data = (int)N;
+    ba.n_rand = 0;
+    ba.n_e = n_e;
+    ba.R0 = (T)R0;
+    ba.rand_weight = T(0);
+    ba.work_counter = bcounter;
+    ba.partials = (double *)(b + o_bp);
+    ba.npairs = npairs + 1;
+    ba.dp0 = 0;
+    ba.dp1 = N;
+    ba.rp0 = 0;
+    ba.rp1 = 0;
+    for (int q = 0; q < HIP_BMAXE; ++q) {
+        const double k = q < n_e ? k_edges[q] : 0.0;
+        ba.k[q] = (T)k;
+        ba.klo[q] = (T)(k - (double)ba.k[q]);
+        ba.k3[q] = (T)(k * k * k);
+        ba.jfac[q] = q + 1 < n_e ? (T)(3.0 / (k_edges[q + 1] * k_edges[q + 1] * k_edges[q + 1] - k * k * k)) : T(0);
+    }
+    int bgrid = 0;
+    HIP_CK(hip_bispec_pairs<T>(ba, bparts_max, &bgrid, st), "bispectrum kernel");
+    CellList<float> cl2{(const float *)(b + o_x2), (const float *)(b + o_y2), (const float *)(b + o_z2),
+                        (const float *)(b + o_w2), (const int *)(b + o_i2), (const int *)(b + o_s2), n_c2, L,
+                        L / n_c2};
+    HIP_CK(hip_e2_term(cl2, n_cells2 * HIP_NSHIFT, hcounter, R0, L, k_edges, n_k, lmax, S1, nodes, b + o_e2,
+                       ba.partials + (size_t)bgrid * tsz, nullptr, st),
+           "DDR^II term");
+    double *B = (double *)(b + o_b);
+    HIP_CK(hip_bispec_finalize(ba.partials, bgrid + 1, n_k, lmax, L, S1, DD, Wt, B, st), "bispectrum finalize");
+    const size_t nout = (size_t)(lmax + 1) * n_k * n_k;
+    std::vector<double> hB(nout);
+    unsigned long long hn[3] = {0, 0, 0};
+    HIP_CK(cudaMemcpyAsync(hB.data(), B, sizeof(double) * nout, cudaMemcpyDeviceToHost, st), "D2H B");
+    HIP_CK(cudaMemcpyAsync(hn, npairs, sizeof(hn), cudaMemcpyDeviceToHost, st), "D2H npairs");
+    HIP_CK(cudaStreamSynchronize(st), "stream sync");
+#undef HIP_CK
+    std::memcpy(B_out, hB.data(), sizeof(double) * nout);
+    if (npairs_out) npairs_out[0] = (int64_t)hn[1];
+    return HIP_OK;
+}
+
+extern "C" hip_status hip_bispectrum_analytic(const float *pos, const float *w, int64_t N, double L, double R0,
+                                              hip_window window, const double *k_edges, int n_k, int lmax,
+                                              hip_precision prec, double *B_out, int64_t *npairs_out,
+                                              void *cuda_stream)
+{
+    g_errbuf[0] = 0;
+    if (!pos || !B_out) return HIP_ERR_ARG;
+    if (N < 2 || N > 2000000000LL) return HIP_ERR_ARG;
+    if (window != HIP_WINDOW_PHILCOX) return HIP_ERR_ARG;
+    if (prec != HIP_PREC_FP64 && prec != HIP_PREC_MIXED) return HIP_ERR_ARG;
+    if (lmax < 0 || lmax > HIP_LMAX) return HIP_ERR_ARG;
+    if (!(L > 0.0) || !std::isfinite(L) || !(R0 > 0.0) || !(R0 < 0.25 * L)) return HIP_ERR_RANGE;
+    hip_status hs = hip_check_edges(k_edges, n_k);
+    if (hs != HIP_OK) return hs;
+    if (n_k > (prec == HIP_PREC_MIXED ? HIP_BMAXE - 2 : 31)) return HIP_ERR_RANGE;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    int dev = 0;
+    if ((hs = hip_device_setup(&dev)) != HIP_OK) return hs;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (prec == HIP_PREC_MIXED)
+        return bispec_analytic_impl<float>(pos, w, N, L, R0, k_edges, n_k, lmax, B_out, npairs_out, st, dev);
+    return bispec_analytic_impl<double>(pos, w, N, L, R0, k_edges, n_k, lmax, B_out, npairs_out, st, dev);
 }
 
 extern "C" hip_status hip_bispectrum_partial(const float *pos, const float *w, int64_t N, const float *rand_pos,

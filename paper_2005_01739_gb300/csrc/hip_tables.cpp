@@ -164,6 +164,9 @@ void hip_build_coeffs(HipCoeffs *C)
     for (int q = 0; q <= HIP_F64_SIDEG; ++q) C->sig64[q] = m[q];
 }
 
+// Nodes and weights of n-point Gauss-Legendre quadrature on [-1, 1].
+void hip_gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) { gauss_legendre(n, x, w); }
+
 const HipCoeffs &hip_host_coeffs()
 {
     static HipCoeffs C;

@@ -114,3 +114,30 @@ def test_bispectrum_argument_checks():
     with pytest.raises(binding.HipError) as ei:
         binding.hip_bispectrum(pos, None, bad, L, R0, edges, 4, "mixed")
     assert ei.value.status == binding.HIP_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_bispectrum_analytic_ddr2_matches_oracle(prec):
+    # the random-free estimator (App. A): data primaries plus the E^II pair sum to
+    # 2 R0; the oracle takes the pair sum inside the p integral over exact pair
+    # distances, the library over a 16384-bin moment histogram (third-order in the
+    # bin width) with coarser (still converged) quadrature
+    L, R0 = 60.0, 12.0
+    pos, w = catalogs.thomas(600, L, 24, 1.5, seed=49, background_frac=0.3, weights="u05_15")
+    edges = catalogs.linear_edges(0.3, 2.4, 12)
+    key = "analytic"
+    if key not in _cache:
+        _cache[key] = oracle.bispectrum_analytic(pos.astype(np.float64), w.astype(np.float64), L, R0, edges, 4)
+    Bref, info = _cache[key]
+    B, nd = binding.hip_bispectrum_analytic(_dev(pos), _dev(w), L, R0, edges, 4, prec)
+    slack = 0 if prec == "fp64" else max(2, int(2e-6 * info["npairs_data"]))
+    assert abs(nd - info["npairs_data"]) <= slack
+    assert _err(B, Bref) < {"fp64": 1e-7, "mixed": 1e-4}[prec], _err(B, Bref)
+
+
+def test_bispectrum_analytic_rejects_large_R0():
+    pos, w, rnd, L, R0 = _case(N=200)
+    edges = catalogs.linear_edges(0.3, 2.4, 12)
+    with pytest.raises(binding.HipError) as ei:
+        binding.hip_bispectrum_analytic(pos, None, L, 0.26 * L, edges, 4, "mixed")
+    assert ei.value.status == binding.HIP_ERR_RANGE
