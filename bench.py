@@ -212,7 +212,21 @@ def bispectrum_rate(binding, stream, reps: int = 2, scale: float = 1.0):
         b.synchronize()
         ts.append(a.elapsed_time(b))
     ms = float(np.mean(ts))
+    # the same estimator without randoms: the DDR^II term from the E^II kernel (App. A)
+    with torch.cuda.stream(stream):
+        binding.hip_bispectrum_analytic(dpos, None, wl["L"], wl["R0"], wl["edges"], 4, "mixed", stream=stream)
+    ta = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            binding.hip_bispectrum_analytic(dpos, None, wl["L"], wl["R0"], wl["edges"], 4, "mixed", stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ta.append(a.elapsed_time(b))
+    analytic = {"ms_per_call": float(np.mean(ta)), "note": "same B without the random catalog (E^II kernel, App. A)"}
     return {"workload": "bk_n5e5", "value": (nd + nr) * nk / (ms / 1e3), "unit": UNIT, "ms_per_call": ms,
+            "analytic_ddr2": analytic,
             "pairs_data_primaries": nd, "pairs_random_primaries": nr, "n_k": nk, "ell": [0, 1, 2, 3, 4]}
 
 
