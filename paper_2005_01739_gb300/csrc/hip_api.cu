@@ -9,6 +9,7 @@
 
 #include "hip_bispec.h"
 #include "hip_e2.h"
+#include "hip_moments.h"
 #include "hip_internal.h"
 #include "hip_workspace.h"
 
@@ -200,6 +201,9 @@ static hip_status power_impl(const float *pos, const float *w, int64_t N, double
     size_t o_small = cv.take(sizeof(double) * 8);
     size_t o_wt = cv.take(sizeof(double) * n_k);
     size_t o_dd = cv.take(sizeof(double) * 3 * n_k), o_p = cv.take(sizeof(double) * 3 * n_k);
+    // the moment pass (Legendre moments of the separation) where it applies, else the direct one
+    const bool moments = hip_pm_applicable(R0, k_edges[n_k], sizeof(T) == 4);
+    const size_t o_pm = moments ? cv.take(hip_pm_scratch_bytes(n_e, hip_pm_intervals(R0, k_edges[n_k]))) : 0;
     hip_status hs = ws.reserve(cv.total, st);
     if (hs != HIP_OK) return hs;
     char *b = (char *)ws.base;
@@ -257,9 +261,13 @@ static hip_status power_impl(const float *pos, const float *w, int64_t N, double
     ka.partials = partials;
     ka.npairs = npairs;
     tm.mark(3);
-    HIP_CK(hip_power_pairs<T>(cl, ka, k_edges, n_ell, R0, grid, st), "pair kernel");
+    if (moments)
+        HIP_CK(hip_power_moments<T>(cl, ka, k_edges, n_ell, R0, b + o_pm, partials, st), "moment pair pass");
+    else
+        HIP_CK(hip_power_pairs<T>(cl, ka, k_edges, n_ell, R0, grid, st), "pair kernel");
     tm.mark(4);
-    HIP_CK(hip_power_finalize(partials, grid, n_e, n_ell, k_edges, R0, L, S1, Wt, DD, P, st), "finalize");
+    HIP_CK(hip_power_finalize(partials, moments ? 1 : grid, n_e, n_ell, k_edges, R0, L, S1, Wt, DD, P, st),
+           "finalize");
     tm.mark(5);
     std::vector<double> hP(n_ell * n_k), hDD(n_ell * n_k);
     unsigned long long hn = 0;

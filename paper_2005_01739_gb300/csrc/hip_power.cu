@@ -7,6 +7,7 @@
 #include <cstdio>
 
 #include "hip_internal.h"
+#include "hip_moments.h"
 
 static __constant__ HipCoeffs c_coeffs;
 
@@ -17,6 +18,8 @@ cudaError_t hip_upload_coeffs_power()
     if (e == cudaSuccess) e = hip_upload_coeffs_pairs_f32_gen();
     if (e == cudaSuccess) e = hip_upload_coeffs_pairs_f64();
     if (e == cudaSuccess) e = hip_upload_coeffs_pairs_batched();
+    if (e == cudaSuccess) e = hip_upload_coeffs_moments();
+    if (e == cudaSuccess) e = hip_upload_pm_tables();
     return e;
 }
 
