@@ -32,10 +32,15 @@ METRIC = "pairs×k-bins/s for P_ℓ(k), B_ℓ; mixed-prec batched vs FP64 GPU at
 UNIT = "pairs*kbins/s"
 WORKLOAD = "pk_mixed_n2e6"
 FLOPS_PER_PAIR_BIN = 12.0  # nominal algorithmic FP32 flops per (unordered pair, k bin)
-# DRAM bytes (read + write) of one pair-kernel launch on the 2e6-particle workload: ncu measured
-# 5.18 MB on the same workload shrunk to 2.5e5 particles (profiles/k_power_pairs_pk_mixed_scale0.125.md);
+# DRAM bytes (read + write) of one pair-pass launch on the 2e6-particle workload: ncu measured
+# 5.16 MB for the moment pass (5.18 MB for the direct pass) on the same workload shrunk to 2.5e5
+# particles (profiles/k_power_moments_pk_mixed_scale0.125.md, profiles/k_power_pairs_pk_mixed_scale0.125.md);
 # the traffic is the particle data read once, so it scales with N: x 8.
-PAIR_KERNEL_DRAM_BYTES = 5.18e6 * 8
+PAIR_KERNEL_DRAM_BYTES = {1: 5.16e6 * 8, 0: 5.18e6 * 8}
+PAIR_KERNEL_NAME = {1: "k_power_moments<float,21>", 0: "k_power_pairs<float,4,21>"}
+# kernels one hip_power call launches: cell build 3, pair pass (moments: coefficients, pairs, contraction)
+# 3 or 1, finalize 2
+PAIR_PASS_LAUNCHES = {1: 8, 0: 6}
 
 
 def _peaks():
@@ -486,6 +491,7 @@ def run_ours(args):
     peak = fp32_peak_tflops(pk)
     kern_ms = float(np.mean(pair_ms))
     achieved = FLOPS_PER_PAIR_BIN * work / (kern_ms / 1e3) / 1e12
+    pair_pass = binding.power_pair_pass(wl["R0"], float(wl["edges"][-1]), "mixed")
     cpu = oracle_sample(wl, args.ref_seconds) if not args.skip_cpu else None
     cpu1 = None
     if cpu:  # the same oracle on one core, a shorter sample
@@ -501,10 +507,10 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_max},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": PAIR_KERNEL_DRAM_BYTES, "kernel": "k_power_pairs<float,4,21>",
+                     "frac": achieved / peak, "traffic": PAIR_KERNEL_DRAM_BYTES[pair_pass], "kernel": PAIR_KERNEL_NAME[pair_pass],
                      "kernel_ms": kern_ms, "flops_per_pair_bin": FLOPS_PER_PAIR_BIN,
                      "peak_note": "derived FP32 FMA peak: 152 SM x 128 lanes x 2 x max SM clock"},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": PAIR_PASS_LAUNCHES[pair_pass] * args.steps,
         "clocks": clk.summary(),
         "pairs": int(pairs),
         "stage_ms": dict(zip(["upload", "cells", "pairs", "finalize", "download"],

@@ -41,7 +41,8 @@ typedef enum { HIP_WINDOW_PHILCOX = 0 } hip_window;
 
 /* Arithmetic of the pair kernels.  FP64: every per-pair and per-bin quantity in
  * double precision (the plain baseline).  MIXED: pair geometry, bin-averaged
- * Bessel functions and per-warp accumulation in FP32; cross-warp reduction,
+ * Bessel functions and per-warp (moment pass: per-CTA) accumulation in FP32,
+ * folded into FP64 every few ten thousand pairs; cross-warp reduction,
  * normalisation and the analytic random-pair terms in FP64. */
 typedef enum { HIP_PREC_FP64 = 0, HIP_PREC_MIXED = 1 } hip_precision;
 
@@ -250,13 +251,27 @@ const char *hip_noalloc_message(void);
  * measurement.  When enabled (on != 0), each call records CUDA events on its
  * stream around its stages; hip_stage_times then writes, in milliseconds,
  *   ms[0] input upload (0 for device-resident inputs),  ms[1] cell-list build,
- *   ms[2] pair kernel,  ms[3] FP64 finalize (W~, reduction, normalisation),
+ *   ms[2] pair pass (the pair kernel; for the moment pass also its FP64
+ *         coefficient and contraction kernels),  ms[3] FP64 finalize (W~,
+ *         reduction, normalisation),
  *   ms[4] result download,
  * for the first min(n, 5) entries.  Returns the number of entries written
  * (0 if profiling was off during the last call).  Not thread-safe with
  * respect to concurrent calls (calls are serialised anyway). */
 void hip_set_profiling(int on);
 int hip_stage_times(double *ms, int n);
+
+/* The pair pass hip_power uses for these arguments (k_max = k_edges[n_k]):
+ *   0  direct: every bin edge's function k^3 F_l(r k) (App. C) evaluated per pair;
+ *   1  Legendre moments: per separation interval of width R0/n_c,
+ *      n_c = max(8, ceil(R0 k_max / 4)), the pair loop sums omega L_l P_m(t)
+ *      for m < 16 (t the position in the interval), and the edge sums are the
+ *      FP64 contraction of those moments with the edge functions' Legendre
+ *      coefficients (truncation below 1e-12 relative: the same edge sums).
+ * The moment pass is taken while n_c <= 256 and its shared-memory array fits
+ * (R0 k_max <= 1024).  Returns -1 for invalid arguments (R0 <= 0, k_max <= 0,
+ * unknown prec). */
+int hip_power_pair_pass(double R0, double k_max, hip_precision prec);
 
 /* Human-readable name of a status code (static string). */
 const char *hip_status_string(hip_status s);

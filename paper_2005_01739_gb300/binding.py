@@ -97,6 +97,8 @@ def load(path: str | None = None):
         L.hip_last_error.restype = ctypes.c_char_p
         L.hip_last_error.argtypes = []
         L.hip_debug_F.restype = d
+        L.hip_power_pair_pass.argtypes = [d, d, i]
+        L.hip_power_pair_pass.restype = i
         L.hip_debug_F.argtypes = [i, i, d]
         L.hip_debug_D.restype = d
         L.hip_debug_D.argtypes = [i, i, d]
@@ -387,6 +389,14 @@ def debug_F_array(prec: str, l: int, u) -> np.ndarray:
 def set_profiling(on: bool) -> None:
     """Record CUDA events around the stages of each call (see hip_stage_times)."""
     load().hip_set_profiling(1 if on else 0)
+
+
+def power_pair_pass(R0, k_max, prec="mixed"):
+    """0: the direct pair pass, 1: the Legendre-moment pass (see hip_power_pair_pass)."""
+    r = load().hip_power_pair_pass(float(R0), float(k_max), PREC[prec])
+    if r < 0:
+        raise ValueError("hip_power_pair_pass: invalid arguments")
+    return r
 
 
 def stage_times():

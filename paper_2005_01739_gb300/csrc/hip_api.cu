@@ -169,6 +169,12 @@ struct StageTimer {
 
 extern "C" void hip_set_profiling(int on) { g_prof = on != 0; }
 
+extern "C" int hip_power_pair_pass(double R0, double k_max, hip_precision prec)
+{
+    if (!(R0 > 0.0) || !(k_max > 0.0) || (prec != HIP_PREC_FP64 && prec != HIP_PREC_MIXED)) return -1;
+    return hip_pm_applicable(R0, k_max, prec == HIP_PREC_MIXED) ? 1 : 0;
+}
+
 extern "C" int hip_stage_times(double *ms, int n)
 {
     if (!g_prof_valid || !ms) return 0;

@@ -10,11 +10,14 @@
 // and the pair loop only accumulates the moments M (HIP_PM_M per bin and l)
 // instead of evaluating every edge: O(M n_l) per pair instead of O(n_e n_l).
 // The coefficients a come from 24-point Gauss-Legendre projection of f_e in FP64
-// (once per call), the final contraction is FP64.  With dc = R0 / n_c and
-// n_c >= R0 k_max / 2, k dc / 2 <= 1 and the truncation after 16 terms is below
-// ~1 / 16! ~ 5e-14 of f, i.e. exact for both precisions; the FP32 path keeps
-// FP32 moments per warp in shared memory and folds them into FP64 every
-// HIP_PM_FOLD pairs.
+// (once per call), the final contraction is FP64.  f_e is band-limited (F_l(u)
+// is an average of j_l(u y) over y in [0, 1], so its spectrum in r lies in
+// [-k_e, k_e]); on an interval of half-width h its m-th Legendre coefficient is
+// therefore at most (2m+1) max|j_m(k h)| ~ (2m+1) (k h)^m / (2m+1)!! times the
+// spectral mass.  With dc = R0 / n_c and n_c >= R0 k_max / 4, k h <= 2 and the
+// first neglected term (m = 16) is below ~4e-13 of f: exact for both
+// precisions.  The FP32 path keeps FP32 moments per CTA in shared memory and
+// folds them into FP64 every HIP_PM_FOLD pairs.
 #define HIP_PAIR_UPLOAD hip_upload_coeffs_moments
 #include "hip_pair_kernel.cuh"
 
@@ -24,7 +27,10 @@
 
 #define HIP_PM_NG 24
 #define HIP_PM_WARPS 4
-#define HIP_PM_FOLD 65536  // pairs a warp adds into its FP32 moments before folding them to FP64
+#define HIP_PM_FOLD 65536  // pairs a CTA adds into its FP32 moments before folding them to FP64
+#define HIP_PM_TILE 128    // particles per staged tile of a cell
+#define HIP_PM_QCAP 64     // queue ring: < 32 pairs plus one ballot round of <= 32
+#define HIP_PM_PST 17      // row stride of the P_m(t) table (odd: conflict-free stores by row)
 
 __constant__ double c_pm_gw[HIP_PM_NG];           // Gauss-Legendre weights on [-1, 1]
 __constant__ double c_pm_gx[HIP_PM_NG];           // and nodes
@@ -80,100 +86,166 @@ __global__ void k_pm_coeffs(const double *__restrict__ kedge, int n_e, int n_c, 
             a[(((size_t)il * n_e + e) * n_c + c) * HIP_PM_M + m] = 0.5 * (2.0 * m + 1.0) * acc[il][m];
 }
 
-// Per-warp staging of the pair kernel: tiles of the two cells and the queue of
-// accepted pairs (separation hi + lo, line-of-sight component, weight).
+// Staging of the pair pass: tiles of the two cells (shared by the CTA), a ring
+// queue of accepted pairs per warp (separation hi + lo, line-of-sight
+// component, weight) and, per warp, the stage of one drain: the pairs in
+// interval order with omega L_l, their interval, and the table P_m(t).
 template <typename T>
-struct PmWarp {
-    T hx[HIP_WTILE], hy[HIP_WTILE], hz[HIP_WTILE];
-    float hw[HIP_WTILE];
-    int hin[HIP_WTILE];
-    T nx[HIP_WTILE], ny[HIP_WTILE], nz[HIP_WTILE];
-    float nw[HIP_WTILE];
-    int nin[HIP_WTILE];
-    T qr[HIP_QCAP], qrl[HIP_QCAP], qdl[HIP_QCAP];
-    T qw[HIP_QCAP];  // w_i w_j times the ordered pairs counted (formed in T: FP64 keeps the product exact)
+struct PmTiles {
+    T hx[HIP_PM_TILE], hy[HIP_PM_TILE], hz[HIP_PM_TILE];
+    float hw[HIP_PM_TILE];
+    int hin[HIP_PM_TILE];
+    T nx[HIP_PM_TILE], ny[HIP_PM_TILE], nz[HIP_PM_TILE];
+    float nw[HIP_PM_TILE];
+    int nin[HIP_PM_TILE];
+};
+template <typename T>
+struct PmQueue {
+    T qr[HIP_PM_QCAP], qrl[HIP_PM_QCAP], qdl[HIP_PM_QCAP];
+    T qw[HIP_PM_QCAP];  // w_i w_j times the ordered pairs counted (formed in T: FP64 keeps the product exact)
+};
+template <typename T>
+struct __align__(16) PmRow {
+    T o0, o2, o4;  // omega L_0, omega L_2, omega L_4
+    int c;         // interval
+};
+template <typename T>
+struct PmStage {
+    PmRow<T> row[32];
+    T P[32 * HIP_PM_PST];  // P_m(t) of row s at s HIP_PM_PST + m
 };
 
 __device__ __forceinline__ void hip_pm_add(float *M, float v) { atomicAdd(M, v); }
 __device__ __forceinline__ void hip_pm_add(double *M, double v) { atomicAdd(M, v); }
 
-// Moments of the n queued pairs, one pair per lane: M[(il M + m) n_c + c] += omega L_l P_m(t).
+// Moments of the n (1..32) queued pairs at ring positions head, head + 1, ...:
+// M[(il M + m) n_cp + c] += omega L_l P_m(t).  The pairs are sorted by interval
+// across the warp (bitonic network on (interval, lane) keys); lane s then
+// evaluates the s-th pair (omega, L_l, t and P_m(t) into the stage); finally the
+// lanes run over the moments (lane = 16 g + m: g = 0 sums l = 0 and l = 4,
+// g = 1 sums l = 2), walk the sorted pairs with register sums, and add a sum to
+// the shared array once per interval run, at 48 distinct addresses.
 template <typename T, int MASK>
-__device__ __forceinline__ void hip_pm_drain(const PmWarp<T> &sm, int n, int lane, T *M, int n_c, T dc, T inv_hdc,
-                                             T invR0)
+__device__ __forceinline__ void hip_pm_drain(const PmQueue<T> &sq, PmStage<T> &sg, int head, int n, int lane, T *M,
+                                             int n_cp, int n_c, T dc, T inv_dc, T inv_hdc, T invR0)
 {
-    for (int i = lane; i < n; i += 32) {
-        const T r = sm.qr[i], rl = sm.qrl[i];
-        const T mu = sm.qdl[i] / r;
+    int key = ((HIP_PM_NCMAX + 1) << 5) | lane;  // empty lanes sort last
+    if (lane < n) {
+        const T r = sq.qr[(head + lane) & (HIP_PM_QCAP - 1)];
+        const int c = min((int)(r * inv_dc), n_c - 1);
+        key = (c << 5) | lane;
+    }
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int other = __shfl_xor_sync(0xffffffffu, key, j);
+            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+            key = keep_min ? min(key, other) : max(key, other);
+        }
+    if (lane < n) {
+        const int c = key >> 5, q = (head + (key & 31)) & (HIP_PM_QCAP - 1);
+        const T r = sq.qr[q], rl = sq.qrl[q];
+        const T mu = sq.qdl[q] / r;
         T l2, l4;
         hip_legendre24<T>(mu, l2, l4);
-        const T om = sm.qw[i] * hip_W<T>(r * invR0);
-        int c = (int)(r / dc);
-        c = c < n_c - 1 ? c : n_c - 1;
+        const T om = sq.qw[q] * hip_W<T>(r * invR0);
         // t in [-1, 1]: r - c dc is exact in FP32 for c >= 1 (Sterbenz), the low part rl added after
         const T t = ((r - T(c) * dc) + rl) * inv_hdc - T(1);
-        const T o0 = om, o2 = om * l2, o4 = om * l4;
+        T *P = sg.P + lane * HIP_PM_PST;
         T p0 = T(1), p1 = t;
-        T *M0 = M + c, *M2 = M + (size_t)HIP_PM_M * n_c + c, *M4 = M + (size_t)2 * HIP_PM_M * n_c + c;
-        hip_pm_add(M0, o0);
-        if (MASK & 4) hip_pm_add(M2, o2);
-        if (MASK & 16) hip_pm_add(M4, o4);
-        hip_pm_add(M0 + n_c, o0 * p1);
-        if (MASK & 4) hip_pm_add(M2 + n_c, o2 * p1);
-        if (MASK & 16) hip_pm_add(M4 + n_c, o4 * p1);
+        P[0] = p0;
+        P[1] = p1;
 #pragma unroll
         for (int m = 1; m + 1 < HIP_PM_M; ++m) {
             // (m+1) P_{m+1} = (2m+1) t P_m - m P_{m-1}
             const T p2 = (T(2 * m + 1) * t * p1 - T(m) * p0) * T(1.0 / (m + 1));
             p0 = p1;
             p1 = p2;
-            hip_pm_add(M0 + (size_t)(m + 1) * n_c, o0 * p2);
-            if (MASK & 4) hip_pm_add(M2 + (size_t)(m + 1) * n_c, o2 * p2);
-            if (MASK & 16) hip_pm_add(M4 + (size_t)(m + 1) * n_c, o4 * p2);
+            P[m + 1] = p2;
         }
+        PmRow<T> rw;
+        rw.o0 = om;
+        rw.o2 = om * l2;
+        rw.o4 = om * l4;
+        rw.c = c;
+        sg.row[lane] = rw;
     }
+    __syncwarp();
+    const int m = lane & 15, g = lane >> 4;
+    T *Ma = M + (size_t)(g * HIP_PM_M + m) * n_cp;
+    T *Mb = M + (size_t)(2 * HIP_PM_M + m) * n_cp;
+    const bool use_a = (g == 0) || (MASK & 4);
+    const bool use_b = (g == 0) && (MASK & 16);
+    T sa = T(0), sb = T(0);
+    int cur = sg.row[0].c;
+#pragma unroll 4
+    for (int s = 0; s < n; ++s) {
+        const PmRow<T> rw = sg.row[s];
+        if (rw.c != cur) {  // warp-uniform
+            if (use_a) hip_pm_add(Ma + cur, sa);
+            if (use_b) hip_pm_add(Mb + cur, sb);
+            sa = T(0);
+            sb = T(0);
+            cur = rw.c;
+        }
+        const T p = sg.P[s * HIP_PM_PST + m];
+        sa += (g ? rw.o2 : rw.o0) * p;
+        sb += rw.o4 * p;
+    }
+    if (use_a) hip_pm_add(Ma + cur, sa);
+    if (use_b) hip_pm_add(Mb + cur, sb);
+    __syncwarp();
 }
 
-// Fold a moment array into the FP64 totals and clear it (lanes of one warp, or
-// the whole CTA when nthreads = blockDim.x).
+// Adds the CTA's moment array into the FP64 totals Mg ([3 M][n_c]) and clears it.
 template <typename T>
-__device__ __forceinline__ void hip_pm_fold(T *M, int len, double *Mg, int tid, int nthreads)
+__device__ __forceinline__ void hip_pm_fold(T *M, int n_cp, int n_c, double *Mg)
 {
-    for (int i = tid; i < len; i += nthreads) {
+    for (int i = threadIdx.x; i < 3 * HIP_PM_M * n_cp; i += blockDim.x) {
+        const int row = i / n_cp, c = i - row * n_cp;
         const T v = M[i];
-        if (v != T(0)) atomicAdd(&Mg[i], (double)v);
+        if (c < n_c && v != T(0)) atomicAdd(&Mg[(size_t)row * n_c + c], (double)v);
         M[i] = T(0);
     }
 }
 
-// The pair pass: warps take work items (home cell, half-shell shift) as in the
-// direct kernel, test candidates one per lane, queue accepted pairs (r as hi + lo
-// for FP32), and at 32 queued pairs add their moments.  FP32: moments per warp
-// (dynamic shared memory [warps][3][M][n_c]), folded every HIP_PM_FOLD pairs.
-// FP64: one moment array per CTA, folded at the end.
+// The pair pass: the CTA takes work items (home cell, half-shell shift) from the
+// counter; its warps share the two cells' tiles and split the home particles,
+// test candidates one per lane, queue accepted pairs (r as hi + lo for FP32),
+// and drain 32 queued pairs at a time into the CTA's moment array in shared
+// memory ([3][M][n_cp], T, n_cp = n_c rounded up to odd so the 16 moments of one
+// interval fall in distinct banks).  The FP32 array is folded into the FP64
+// totals Mg whenever the CTA has added HIP_PM_FOLD pairs since the last fold (at
+// item boundaries, under a barrier) and at the end.
 template <typename T, int MASK>
 __global__ void __launch_bounds__(HIP_PM_WARPS * 32)
     k_power_moments(CellList<T> cl, PowerKernelArgs a, T R0, int n_c, T dc, double *Mg)
 {
-    __shared__ PmWarp<T> smem[HIP_PM_WARPS];
+    __shared__ PmTiles<T> tl;
+    __shared__ PmQueue<T> queues[HIP_PM_WARPS];
+    __shared__ PmStage<T> stages[HIP_PM_WARPS];
+    __shared__ int s_item;
     extern __shared__ __align__(16) unsigned char pm_raw[];
-    constexpr bool PERWARP = sizeof(T) == 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    PmWarp<T> &sm = smem[warp];
-    const int len = 3 * HIP_PM_M * n_c;
-    T *M = reinterpret_cast<T *>(pm_raw) + (PERWARP ? (size_t)warp * len : 0);
-    for (int i = (PERWARP ? lane : threadIdx.x); i < len; i += (PERWARP ? 32 : blockDim.x)) M[i] = T(0);
-    __syncthreads();
-    const T R0sq = R0 * R0, invR0 = T(1) / R0, inv_hdc = T(2) / dc;
+    PmQueue<T> &sq = queues[warp];
+    PmStage<T> &sg = stages[warp];
+    const int n_cp = n_c | 1;
+    T *M = reinterpret_cast<T *>(pm_raw);
+    for (int i = threadIdx.x; i < 3 * HIP_PM_M * n_cp; i += blockDim.x) M[i] = T(0);
+    const T R0sq = R0 * R0, invR0 = T(1) / R0, inv_hdc = T(2) / dc, inv_dc = T(1) / dc;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int n_c3 = cl.n_c;
     unsigned long long cnt = 0;
-    int qn = 0;
-    long long since_fold = 0;
+    int qh = 0, qn = 0;     // ring head and length of this warp's queue
+    int since_fold = 0;     // pairs the CTA drained since the last fold (warp 0's count of all warps)
+    int drained = 0;        // pairs this warp drained in the current item
+    __shared__ int s_drained[HIP_PM_WARPS];
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(a.work_counter, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(a.work_counter, 1);
+        __syncthreads();
+        const int item = s_item;
         if (item >= a.n_items) break;
         const int c = item / HIP_NSHIFT, q = item - c * HIP_NSHIFT;
         const int cx = c / (n_c3 * n_c3), cy = (c / n_c3) % n_c3, cz = c % n_c3;
@@ -186,91 +258,95 @@ __global__ void __launch_bounds__(HIP_PM_WARPS * 32)
         const int a0 = cl.cell_start[c], a1 = cl.cell_start[c + 1];
         const int b0 = cl.cell_start[nb], b1 = cl.cell_start[nb + 1];
         const bool self = (q == 0);
-        for (int hb = a0; hb < a1; hb += HIP_WTILE) {
-            const int hn = min(HIP_WTILE, a1 - hb);
-            __syncwarp();
-            for (int i = lane; i < hn; i += 32) {
-                sm.hx[i] = cl.x[hb + i];
-                sm.hy[i] = cl.y[hb + i];
-                sm.hz[i] = cl.z[hb + i];
-                sm.hw[i] = cl.w[hb + i];
+        for (int hb = a0; hb < a1; hb += HIP_PM_TILE) {
+            const int hn = min(HIP_PM_TILE, a1 - hb);
+            __syncthreads();
+            for (int i = threadIdx.x; i < hn; i += blockDim.x) {
+                tl.hx[i] = cl.x[hb + i];
+                tl.hy[i] = cl.y[hb + i];
+                tl.hz[i] = cl.z[hb + i];
+                tl.hw[i] = cl.w[hb + i];
                 const long long oi = cl.idx[hb + i];
-                sm.hin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
+                tl.hin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
             }
-            for (int nbs = self ? hb : b0; nbs < b1; nbs += HIP_WTILE) {
-                const int nn = min(HIP_WTILE, b1 - nbs);
-                __syncwarp();
-                for (int i = lane; i < nn; i += 32) {
-                    sm.nx[i] = cl.x[nbs + i];
-                    sm.ny[i] = cl.y[nbs + i];
-                    sm.nz[i] = cl.z[nbs + i];
-                    sm.nw[i] = cl.w[nbs + i];
+            for (int nbs = self ? hb : b0; nbs < b1; nbs += HIP_PM_TILE) {
+                const int nn = min(HIP_PM_TILE, b1 - nbs);
+                __syncthreads();
+                for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+                    tl.nx[i] = cl.x[nbs + i];
+                    tl.ny[i] = cl.y[nbs + i];
+                    tl.nz[i] = cl.z[nbs + i];
+                    tl.nw[i] = cl.w[nbs + i];
                     const long long oi = cl.idx[nbs + i];
-                    sm.nin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
+                    tl.nin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
                 }
-                __syncwarp();
+                __syncthreads();
                 const bool same = self && (nbs == hb);
-                for (int il = 0; il < hn; ++il) {
-                    const T hx = sm.hx[il], hy = sm.hy[il], hz = sm.hz[il];
+                for (int il = warp; il < hn; il += HIP_PM_WARPS) {
+                    const T hx = tl.hx[il], hy = tl.hy[il], hz = tl.hz[il];
                     const T xi = hx - sx, yi = hy - sy, zi = hz - sz;
                     const T xil = hip_low(hx, -sx, xi) - sxl, yil = hip_low(hy, -sy, yi) - syl,
                             zil = hip_low(hz, -sz, zi) - szl;
-                    const float wi = sm.hw[il];
-                    const int ini = sm.hin[il];
+                    const float wi = tl.hw[il];
+                    const int ini = tl.hin[il];
                     for (int jb = same ? il + 1 : 0; jb < nn; jb += 32) {
                         const int jl = jb + lane;
                         bool ok = false;
                         T ddx = T(0), ddy = T(0), ddz = T(0);
                         int mult = 0;
                         if (jl < nn) {
-                            ddx = xi - sm.nx[jl];
-                            ddy = yi - sm.ny[jl];
-                            ddz = zi - sm.nz[jl];
+                            ddx = xi - tl.nx[jl];
+                            ddy = yi - tl.ny[jl];
+                            ddz = zi - tl.nz[jl];
                             const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            mult = ini + sm.nin[jl];
+                            mult = ini + tl.nin[jl];
                             ok = (r2 < R0sq) && (r2 > T(0)) && (mult > 0);
                         }
-                        const unsigned m = __ballot_sync(0xffffffffu, ok);
+                        const unsigned bal = __ballot_sync(0xffffffffu, ok);
                         if (ok) {
                             T r, rl;
-                            hip_pair_sep(xi, xil, yi, yil, zi, zil, sm.nx[jl], sm.ny[jl], sm.nz[jl], ddx, ddy, ddz,
+                            hip_pair_sep(xi, xil, yi, yil, zi, zil, tl.nx[jl], tl.ny[jl], tl.nz[jl], ddx, ddy, ddz,
                                          &r, &rl);
-                            const int slot = qn + __popc(m & lt_mask);
-                            sm.qr[slot] = r;
-                            sm.qrl[slot] = rl;
-                            sm.qdl[slot] = a.los == 0 ? ddx : (a.los == 1 ? ddy : ddz);
-                            sm.qw[slot] = T(wi) * T(sm.nw[jl]) * T(mult);
+                            const int slot = (qh + qn + __popc(bal & lt_mask)) & (HIP_PM_QCAP - 1);
+                            sq.qr[slot] = r;
+                            sq.qrl[slot] = rl;
+                            sq.qdl[slot] = a.los == 0 ? ddx : (a.los == 1 ? ddy : ddz);
+                            sq.qw[slot] = T(wi) * T(tl.nw[jl]) * T(mult);
                             cnt += (unsigned long long)mult;
                         }
-                        qn += __popc(m);
+                        qn += __popc(bal);
                         if (qn >= 32) {
                             __syncwarp();
-                            hip_pm_drain<T, MASK>(sm, qn, lane, M, n_c, dc, inv_hdc, invR0);
-                            since_fold += qn;
-                            qn = 0;
-                            __syncwarp();
-                            if (PERWARP && since_fold >= HIP_PM_FOLD) {
-                                hip_pm_fold(M, len, Mg, lane, 32);
-                                since_fold = 0;
-                                __syncwarp();
-                            }
+                            hip_pm_drain<T, MASK>(sq, sg, qh, 32, lane, M, n_cp, n_c, dc, inv_dc, inv_hdc, invR0);
+                            qh = (qh + 32) & (HIP_PM_QCAP - 1);
+                            qn -= 32;
+                            drained += 32;
                         }
                     }
                 }
             }
         }
+        // item boundary: fold the FP32 moments when the CTA has added enough pairs
+        if (sizeof(T) == 4) {
+            if (lane == 0) s_drained[warp] = drained;
+            __syncthreads();
+            int tot = 0;
+#pragma unroll
+            for (int w = 0; w < HIP_PM_WARPS; ++w) tot += s_drained[w];
+            drained = 0;
+            since_fold += tot;
+            if (since_fold >= HIP_PM_FOLD) {  // CTA-uniform
+                hip_pm_fold(M, n_cp, n_c, Mg);
+                since_fold = 0;
+            }
+        }
     }
     if (qn > 0) {
         __syncwarp();
-        hip_pm_drain<T, MASK>(sm, qn, lane, M, n_c, dc, inv_hdc, invR0);
-        __syncwarp();
+        hip_pm_drain<T, MASK>(sq, sg, qh, qn, lane, M, n_cp, n_c, dc, inv_dc, inv_hdc, invR0);
     }
-    if (PERWARP) {
-        hip_pm_fold(M, len, Mg, lane, 32);
-    } else {
-        __syncthreads();
-        hip_pm_fold(M, len, Mg, threadIdx.x, blockDim.x);
-    }
+    __syncthreads();
+    hip_pm_fold(M, n_cp, n_c, Mg);
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if (lane == 0 && cnt) atomicAdd(a.npairs, cnt);
 }
@@ -301,7 +377,7 @@ __global__ void __launch_bounds__(256) k_pm_contract(const double *__restrict__ 
 // ------------------------------------------------------------------ host ----
 int hip_pm_intervals(double R0, double k_max)
 {
-    const int n = (int)std::ceil(R0 * k_max / 2.0);
+    const int n = (int)std::ceil(R0 * k_max / 4.0);
     return n < 8 ? 8 : n;
 }
 
@@ -313,7 +389,7 @@ size_t hip_pm_scratch_bytes(int n_e, int n_c)
 template <typename T>
 static size_t pm_dyn_smem(int n_c)
 {
-    return sizeof(T) * 3 * HIP_PM_M * (size_t)n_c * (sizeof(T) == 4 ? HIP_PM_WARPS : 1);
+    return sizeof(T) * 3 * HIP_PM_M * (size_t)(n_c | 1);
 }
 
 bool hip_pm_applicable(double R0, double k_max, bool fp32)
@@ -321,7 +397,8 @@ bool hip_pm_applicable(double R0, double k_max, bool fp32)
     const int n_c = hip_pm_intervals(R0, k_max);
     if (n_c > HIP_PM_NCMAX) return false;
     const size_t dyn = fp32 ? pm_dyn_smem<float>(n_c) : pm_dyn_smem<double>(n_c);
-    return dyn + sizeof(PmWarp<double>) * HIP_PM_WARPS <= 220 * 1024;
+    const size_t stat = sizeof(PmTiles<double>) + (sizeof(PmQueue<double>) + sizeof(PmStage<double>)) * HIP_PM_WARPS;
+    return dyn + stat <= 220 * 1024;
 }
 
 template <typename T, int MASK>

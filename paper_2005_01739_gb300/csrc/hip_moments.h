@@ -4,7 +4,7 @@
 #include "hip_internal.h"
 
 #define HIP_PM_M 16       // Legendre moments per separation interval
-#define HIP_PM_NCMAX 256  // most intervals on [0, R0) (n_c = max(8, ceil(R0 k_max / 2)))
+#define HIP_PM_NCMAX 256  // most intervals on [0, R0) (n_c = max(8, ceil(R0 k_max / 4)))
 
 // Intervals for a given R0 and largest edge, and whether the moment pass applies
 // (n_c <= HIP_PM_NCMAX and its shared memory fits); otherwise the direct pass is used.

@@ -114,3 +114,16 @@ def test_kernel_D_fp32_branches(lib, variant, lo, hi, l):
         uf = float(np.float32(u))
         env = uf ** 3 * (1.0 / 3.0 if uf < 1 else 1.0 / uf ** 2)
         assert abs(binding.debug_D(variant, l, uf) - oracle.dhat(l, uf)) < bound * env, (variant, l, uf)
+
+
+def test_power_pair_pass_choice():
+    # moment pass while n_c = max(8, ceil(R0 k_max / 4)) <= 256, the direct pass beyond
+    assert binding.power_pair_pass(50.0, 5.0) == 1
+    assert binding.power_pair_pass(50.0, 5.0, "fp64") == 1
+    assert binding.power_pair_pass(20.0, 51.2) == 1  # R0 k_max = 1024: n_c = 256
+    assert binding.power_pair_pass(20.0, 51.3) == 0
+    assert binding.power_pair_pass(17.3, 14.0) == 1
+    with pytest.raises(ValueError):
+        binding.power_pair_pass(-1.0, 5.0)
+    with pytest.raises(ValueError):
+        binding.power_pair_pass(10.0, 0.0)

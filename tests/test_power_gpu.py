@@ -100,6 +100,20 @@ def test_bin_chunks_parity(prec, nk, kmax):
     assert _err(P, Pref) < TOL[prec]
 
 
+def test_direct_pass_beyond_moment_range():
+    # R0 k_max = 1080 > 1024: more than 256 moment intervals, so hip_power takes
+    # the direct pair pass (every edge evaluated per pair; FP64 here, the FP32
+    # direct pass is covered by the batched and allocation-free tests)
+    pos, w = catalogs.thomas(1500, 60.0, 40, 1.5, seed=35, background_frac=0.3, los_sigma=2.0)
+    L, R0 = 60.0, 12.0
+    edges = catalogs.linear_edges(0.5, 90.0, 255)
+    assert binding.power_pair_pass(R0, edges[-1], "fp64") == 0
+    Pref, _, nref, _ = _oracle_P("direct_pass", pos, w, L, R0, edges)
+    P, _, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, "fp64")
+    _same_count("fp64", npairs, nref)
+    assert _err(P, Pref) < TOL["fp64"]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_inexact_cell_side_large_arguments(prec):
     # L / n_c = 19.46 is no float, and r k reaches 17.3 * 14 = 242: the cell
