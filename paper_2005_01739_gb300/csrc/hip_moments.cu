@@ -86,23 +86,19 @@ __global__ void k_pm_coeffs(const double *__restrict__ kedge, int n_e, int n_c, 
             a[(((size_t)il * n_e + e) * n_c + c) * HIP_PM_M + m] = 0.5 * (2.0 * m + 1.0) * acc[il][m];
 }
 
-// Staging of the pair pass: tiles of the two cells (shared by the CTA), a ring
-// queue of accepted pairs per warp (separation hi + lo, line-of-sight
-// component, weight) and, per warp, the stage of one drain: the pairs in
-// interval order with omega L_l, their interval, and the table P_m(t).
+// Staging of the pair pass: tiles of the two cells (shared by the CTA: offsets
+// and primary flag packed for one 16-byte load, weights apart) and, per warp, a
+// ring queue of accepted pairs (tile indices only) and the stage of one drain:
+// the pairs in interval order with omega L_l, their interval, and P_m(t).
 template <typename T>
-struct PmTiles {
-    T hx[HIP_PM_TILE], hy[HIP_PM_TILE], hz[HIP_PM_TILE];
-    float hw[HIP_PM_TILE];
-    int hin[HIP_PM_TILE];
-    T nx[HIP_PM_TILE], ny[HIP_PM_TILE], nz[HIP_PM_TILE];
-    float nw[HIP_PM_TILE];
-    int nin[HIP_PM_TILE];
+struct __align__(16) PmPt {
+    T x, y, z;
+    T in;  // 1 if the particle is in the primary range, else 0
 };
 template <typename T>
-struct PmQueue {
-    T qr[HIP_PM_QCAP], qrl[HIP_PM_QCAP], qdl[HIP_PM_QCAP];
-    T qw[HIP_PM_QCAP];  // w_i w_j times the ordered pairs counted (formed in T: FP64 keeps the product exact)
+struct PmTiles {
+    PmPt<T> h[HIP_PM_TILE], n[HIP_PM_TILE];
+    float hw[HIP_PM_TILE], nw[HIP_PM_TILE];
 };
 template <typename T>
 struct __align__(16) PmRow {
@@ -113,27 +109,55 @@ template <typename T>
 struct PmStage {
     PmRow<T> row[32];
     T P[32 * HIP_PM_PST];  // P_m(t) of row s at s HIP_PM_PST + m
+    int q[HIP_PM_QCAP];    // queued pairs: home index << 9 | neighbour index << 2 | ordered pairs counted
 };
 
 __device__ __forceinline__ void hip_pm_add(float *M, float v) { atomicAdd(M, v); }
 __device__ __forceinline__ void hip_pm_add(double *M, double v) { atomicAdd(M, v); }
 
+// Frame of one work item: the neighbour cell's offset from the home cell (hi + lo).
+template <typename T>
+struct PmShift {
+    T x, y, z, xl, yl, zl;
+};
+
 // Moments of the n (1..32) queued pairs at ring positions head, head + 1, ...:
-// M[(il M + m) n_cp + c] += omega L_l P_m(t).  The pairs are sorted by interval
-// across the warp (bitonic network on (interval, lane) keys); lane s then
-// evaluates the s-th pair (omega, L_l, t and P_m(t) into the stage); finally the
-// lanes run over the moments (lane = 16 g + m: g = 0 sums l = 0 and l = 4,
-// g = 1 sums l = 2), walk the sorted pairs with register sums, and add a sum to
-// the shared array once per interval run, at 48 distinct addresses.
+// M[(il M + m) n_cp + c] += omega L_l P_m(t).  Lane p first evaluates queued
+// pair p from the tiles (exact separation, mu, W, interval, t); the pairs are
+// then sorted by interval across the warp (bitonic network on (interval, lane)
+// keys), lane s tabulates P_m(t) of the s-th pair, and finally the lanes run
+// over the moments (lane = 16 g + m: g = 0 sums l = 0 and l = 4, g = 1 sums
+// l = 2), walk the sorted pairs with register sums, and add a sum to the shared
+// array once per interval run, at 48 distinct addresses.
 template <typename T, int MASK>
-__device__ __forceinline__ void hip_pm_drain(const PmQueue<T> &sq, PmStage<T> &sg, int head, int n, int lane, T *M,
-                                             int n_cp, int n_c, T dc, T inv_dc, T inv_hdc, T invR0)
+__device__ __forceinline__ void hip_pm_drain(PmStage<T> &sg, const PmTiles<T> &tl, const PmShift<T> &sh, int los,
+                                             int head, int n, int lane, T *M, int n_cp, int n_c, T dc, T inv_dc,
+                                             T inv_hdc, T invR0, unsigned long long &cnt)
 {
     int key = ((HIP_PM_NCMAX + 1) << 5) | lane;  // empty lanes sort last
+    T t = T(0), o0 = T(0), o2 = T(0), o4 = T(0);
     if (lane < n) {
-        const T r = sq.qr[(head + lane) & (HIP_PM_QCAP - 1)];
+        const int e = sg.q[(head + lane) & (HIP_PM_QCAP - 1)];
+        const int il = e >> 9, jl = (e >> 2) & 127, mult = e & 3;
+        const PmPt<T> h = tl.h[il], nb = tl.n[jl];
+        const T xi = h.x - sh.x, yi = h.y - sh.y, zi = h.z - sh.z;
+        const T xil = hip_low(h.x, -sh.x, xi) - sh.xl, yil = hip_low(h.y, -sh.y, yi) - sh.yl,
+                zil = hip_low(h.z, -sh.z, zi) - sh.zl;
+        const T ddx = xi - nb.x, ddy = yi - nb.y, ddz = zi - nb.z;
+        T r, rl;
+        hip_pair_sep(xi, xil, yi, yil, zi, zil, nb.x, nb.y, nb.z, ddx, ddy, ddz, &r, &rl);
+        const T mu = (los == 0 ? ddx : (los == 1 ? ddy : ddz)) / r;
+        T l2, l4;
+        hip_legendre24<T>(mu, l2, l4);
+        // w_i w_j times the ordered pairs counted, formed in T (exact in FP64), then W
+        o0 = (T(tl.hw[il]) * T(tl.nw[jl]) * T(mult)) * hip_W<T>(r * invR0);
+        o2 = o0 * l2;
+        o4 = o0 * l4;
         const int c = min((int)(r * inv_dc), n_c - 1);
+        // t in [-1, 1]: r - c dc is exact in FP32 for c >= 1 (Sterbenz), the low part rl added after
+        t = ((r - T(c) * dc) + rl) * inv_hdc - T(1);
         key = (c << 5) | lane;
+        cnt += (unsigned long long)mult;
     }
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1)
@@ -143,32 +167,26 @@ __device__ __forceinline__ void hip_pm_drain(const PmQueue<T> &sq, PmStage<T> &s
             const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
             key = keep_min ? min(key, other) : max(key, other);
         }
+    const int src = key & 31;
+    const T ts = __shfl_sync(0xffffffffu, t, src);
+    PmRow<T> rw;
+    rw.o0 = __shfl_sync(0xffffffffu, o0, src);
+    rw.o2 = __shfl_sync(0xffffffffu, o2, src);
+    rw.o4 = __shfl_sync(0xffffffffu, o4, src);
+    rw.c = key >> 5;
     if (lane < n) {
-        const int c = key >> 5, q = (head + (key & 31)) & (HIP_PM_QCAP - 1);
-        const T r = sq.qr[q], rl = sq.qrl[q];
-        const T mu = sq.qdl[q] / r;
-        T l2, l4;
-        hip_legendre24<T>(mu, l2, l4);
-        const T om = sq.qw[q] * hip_W<T>(r * invR0);
-        // t in [-1, 1]: r - c dc is exact in FP32 for c >= 1 (Sterbenz), the low part rl added after
-        const T t = ((r - T(c) * dc) + rl) * inv_hdc - T(1);
         T *P = sg.P + lane * HIP_PM_PST;
-        T p0 = T(1), p1 = t;
+        T p0 = T(1), p1 = ts;
         P[0] = p0;
         P[1] = p1;
 #pragma unroll
         for (int m = 1; m + 1 < HIP_PM_M; ++m) {
             // (m+1) P_{m+1} = (2m+1) t P_m - m P_{m-1}
-            const T p2 = (T(2 * m + 1) * t * p1 - T(m) * p0) * T(1.0 / (m + 1));
+            const T p2 = (T(2 * m + 1) * ts * p1 - T(m) * p0) * T(1.0 / (m + 1));
             p0 = p1;
             p1 = p2;
             P[m + 1] = p2;
         }
-        PmRow<T> rw;
-        rw.o0 = om;
-        rw.o2 = om * l2;
-        rw.o4 = om * l4;
-        rw.c = c;
         sg.row[lane] = rw;
     }
     __syncwarp();
@@ -181,17 +199,17 @@ __device__ __forceinline__ void hip_pm_drain(const PmQueue<T> &sq, PmStage<T> &s
     int cur = sg.row[0].c;
 #pragma unroll 4
     for (int s = 0; s < n; ++s) {
-        const PmRow<T> rw = sg.row[s];
-        if (rw.c != cur) {  // warp-uniform
+        const PmRow<T> r = sg.row[s];
+        if (r.c != cur) {  // warp-uniform
             if (use_a) hip_pm_add(Ma + cur, sa);
             if (use_b) hip_pm_add(Mb + cur, sb);
             sa = T(0);
             sb = T(0);
-            cur = rw.c;
+            cur = r.c;
         }
         const T p = sg.P[s * HIP_PM_PST + m];
-        sa += (g ? rw.o2 : rw.o0) * p;
-        sb += rw.o4 * p;
+        sa += (g ? r.o2 : r.o0) * p;
+        sb += r.o4 * p;
     }
     if (use_a) hip_pm_add(Ma + cur, sa);
     if (use_b) hip_pm_add(Mb + cur, sb);
@@ -212,23 +230,22 @@ __device__ __forceinline__ void hip_pm_fold(T *M, int n_cp, int n_c, double *Mg)
 
 // The pair pass: the CTA takes work items (home cell, half-shell shift) from the
 // counter; its warps share the two cells' tiles and split the home particles,
-// test candidates one per lane, queue accepted pairs (r as hi + lo for FP32),
-// and drain 32 queued pairs at a time into the CTA's moment array in shared
-// memory ([3][M][n_cp], T, n_cp = n_c rounded up to odd so the 16 moments of one
-// interval fall in distinct banks).  The FP32 array is folded into the FP64
-// totals Mg whenever the CTA has added HIP_PM_FOLD pairs since the last fold (at
-// item boundaries, under a barrier) and at the end.
+// test candidates one per lane and queue the accepted ones as tile indices; 32
+// queued pairs (and whatever is queued when a tile pair is done) are drained
+// into the CTA's moment array in shared memory ([3][M][n_cp], T, n_cp = n_c
+// rounded up to odd so the 16 moments of one interval fall in distinct banks).
+// The FP32 array is folded into the FP64 totals Mg whenever the CTA has added
+// HIP_PM_FOLD pairs since the last fold (at item boundaries, under a barrier)
+// and at the end.
 template <typename T, int MASK>
 __global__ void __launch_bounds__(HIP_PM_WARPS * 32)
     k_power_moments(CellList<T> cl, PowerKernelArgs a, T R0, int n_c, T dc, double *Mg)
 {
     __shared__ PmTiles<T> tl;
-    __shared__ PmQueue<T> queues[HIP_PM_WARPS];
     __shared__ PmStage<T> stages[HIP_PM_WARPS];
-    __shared__ int s_item;
+    __shared__ int s_item, s_drained[HIP_PM_WARPS];
     extern __shared__ __align__(16) unsigned char pm_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    PmQueue<T> &sq = queues[warp];
     PmStage<T> &sg = stages[warp];
     const int n_cp = n_c | 1;
     T *M = reinterpret_cast<T *>(pm_raw);
@@ -237,10 +254,8 @@ __global__ void __launch_bounds__(HIP_PM_WARPS * 32)
     const unsigned lt_mask = (1u << lane) - 1u;
     const int n_c3 = cl.n_c;
     unsigned long long cnt = 0;
-    int qh = 0, qn = 0;     // ring head and length of this warp's queue
-    int since_fold = 0;     // pairs the CTA drained since the last fold (warp 0's count of all warps)
-    int drained = 0;        // pairs this warp drained in the current item
-    __shared__ int s_drained[HIP_PM_WARPS];
+    int since_fold = 0;  // pairs the CTA drained since the last fold
+    int drained = 0;     // pairs this warp drained in the current item
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = atomicAdd(a.work_counter, 1);
@@ -251,10 +266,10 @@ __global__ void __launch_bounds__(HIP_PM_WARPS * 32)
         const int cx = c / (n_c3 * n_c3), cy = (c / n_c3) % n_c3, cz = c % n_c3;
         const int dx = c_shift[q][0], dy = c_shift[q][1], dz = c_shift[q][2];
         const int nb = (((cx + dx + n_c3) % n_c3) * n_c3 + (cy + dy + n_c3) % n_c3) * n_c3 + (cz + dz + n_c3) % n_c3;
-        T sx, sy, sz, sxl, syl, szl;
-        hip_cell_shift(cl, cx, dx, sx, sxl);
-        hip_cell_shift(cl, cy, dy, sy, syl);
-        hip_cell_shift(cl, cz, dz, sz, szl);
+        PmShift<T> sh;
+        hip_cell_shift(cl, cx, dx, sh.x, sh.xl);
+        hip_cell_shift(cl, cy, dy, sh.y, sh.yl);
+        hip_cell_shift(cl, cz, dz, sh.z, sh.zl);
         const int a0 = cl.cell_start[c], a1 = cl.cell_start[c + 1];
         const int b0 = cl.cell_start[nb], b1 = cl.cell_start[nb + 1];
         const bool self = (q == 0);
@@ -262,67 +277,65 @@ __global__ void __launch_bounds__(HIP_PM_WARPS * 32)
             const int hn = min(HIP_PM_TILE, a1 - hb);
             __syncthreads();
             for (int i = threadIdx.x; i < hn; i += blockDim.x) {
-                tl.hx[i] = cl.x[hb + i];
-                tl.hy[i] = cl.y[hb + i];
-                tl.hz[i] = cl.z[hb + i];
-                tl.hw[i] = cl.w[hb + i];
                 const long long oi = cl.idx[hb + i];
-                tl.hin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
+                PmPt<T> p;
+                p.x = cl.x[hb + i];
+                p.y = cl.y[hb + i];
+                p.z = cl.z[hb + i];
+                p.in = (oi >= a.p0 && oi < a.p1) ? T(1) : T(0);
+                tl.h[i] = p;
+                tl.hw[i] = cl.w[hb + i];
             }
             for (int nbs = self ? hb : b0; nbs < b1; nbs += HIP_PM_TILE) {
                 const int nn = min(HIP_PM_TILE, b1 - nbs);
                 __syncthreads();
                 for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-                    tl.nx[i] = cl.x[nbs + i];
-                    tl.ny[i] = cl.y[nbs + i];
-                    tl.nz[i] = cl.z[nbs + i];
-                    tl.nw[i] = cl.w[nbs + i];
                     const long long oi = cl.idx[nbs + i];
-                    tl.nin[i] = (oi >= a.p0 && oi < a.p1) ? 1 : 0;
+                    PmPt<T> p;
+                    p.x = cl.x[nbs + i];
+                    p.y = cl.y[nbs + i];
+                    p.z = cl.z[nbs + i];
+                    p.in = (oi >= a.p0 && oi < a.p1) ? T(1) : T(0);
+                    tl.n[i] = p;
+                    tl.nw[i] = cl.w[nbs + i];
                 }
                 __syncthreads();
                 const bool same = self && (nbs == hb);
+                int qn = 0;  // queued pairs of this warp (ring head 0 after each partial drain)
+                int qh = 0;
                 for (int il = warp; il < hn; il += HIP_PM_WARPS) {
-                    const T hx = tl.hx[il], hy = tl.hy[il], hz = tl.hz[il];
-                    const T xi = hx - sx, yi = hy - sy, zi = hz - sz;
-                    const T xil = hip_low(hx, -sx, xi) - sxl, yil = hip_low(hy, -sy, yi) - syl,
-                            zil = hip_low(hz, -sz, zi) - szl;
-                    const float wi = tl.hw[il];
-                    const int ini = tl.hin[il];
+                    const PmPt<T> h = tl.h[il];
+                    const T xi = h.x - sh.x, yi = h.y - sh.y, zi = h.z - sh.z;
+                    const int ini = (int)h.in;
                     for (int jb = same ? il + 1 : 0; jb < nn; jb += 32) {
                         const int jl = jb + lane;
                         bool ok = false;
-                        T ddx = T(0), ddy = T(0), ddz = T(0);
                         int mult = 0;
                         if (jl < nn) {
-                            ddx = xi - tl.nx[jl];
-                            ddy = yi - tl.ny[jl];
-                            ddz = zi - tl.nz[jl];
+                            const PmPt<T> p = tl.n[jl];
+                            const T ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
                             const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            mult = ini + tl.nin[jl];
+                            mult = ini + (int)p.in;
                             ok = (r2 < R0sq) && (r2 > T(0)) && (mult > 0);
                         }
                         const unsigned bal = __ballot_sync(0xffffffffu, ok);
-                        if (ok) {
-                            T r, rl;
-                            hip_pair_sep(xi, xil, yi, yil, zi, zil, tl.nx[jl], tl.ny[jl], tl.nz[jl], ddx, ddy, ddz,
-                                         &r, &rl);
-                            const int slot = (qh + qn + __popc(bal & lt_mask)) & (HIP_PM_QCAP - 1);
-                            sq.qr[slot] = r;
-                            sq.qrl[slot] = rl;
-                            sq.qdl[slot] = a.los == 0 ? ddx : (a.los == 1 ? ddy : ddz);
-                            sq.qw[slot] = T(wi) * T(tl.nw[jl]) * T(mult);
-                            cnt += (unsigned long long)mult;
-                        }
+                        if (ok) sg.q[(qh + qn + __popc(bal & lt_mask)) & (HIP_PM_QCAP - 1)] = (il << 9) | (jl << 2) | mult;
                         qn += __popc(bal);
                         if (qn >= 32) {
                             __syncwarp();
-                            hip_pm_drain<T, MASK>(sq, sg, qh, 32, lane, M, n_cp, n_c, dc, inv_dc, inv_hdc, invR0);
+                            hip_pm_drain<T, MASK>(sg, tl, sh, a.los, qh, 32, lane, M, n_cp, n_c, dc, inv_dc, inv_hdc,
+                                                  invR0, cnt);
                             qh = (qh + 32) & (HIP_PM_QCAP - 1);
                             qn -= 32;
                             drained += 32;
                         }
                     }
+                }
+                if (qn > 0) {  // the tiles change after this tile pair
+                    __syncwarp();
+                    hip_pm_drain<T, MASK>(sg, tl, sh, a.los, qh, qn, lane, M, n_cp, n_c, dc, inv_dc, inv_hdc, invR0,
+                                          cnt);
+                    drained += qn;
                 }
             }
         }
@@ -340,10 +353,6 @@ __global__ void __launch_bounds__(HIP_PM_WARPS * 32)
                 since_fold = 0;
             }
         }
-    }
-    if (qn > 0) {
-        __syncwarp();
-        hip_pm_drain<T, MASK>(sq, sg, qh, qn, lane, M, n_cp, n_c, dc, inv_dc, inv_hdc, invR0);
     }
     __syncthreads();
     hip_pm_fold(M, n_cp, n_c, Mg);
@@ -397,7 +406,7 @@ bool hip_pm_applicable(double R0, double k_max, bool fp32)
     const int n_c = hip_pm_intervals(R0, k_max);
     if (n_c > HIP_PM_NCMAX) return false;
     const size_t dyn = fp32 ? pm_dyn_smem<float>(n_c) : pm_dyn_smem<double>(n_c);
-    const size_t stat = sizeof(PmTiles<double>) + (sizeof(PmQueue<double>) + sizeof(PmStage<double>)) * HIP_PM_WARPS;
+    const size_t stat = sizeof(PmTiles<double>) + sizeof(PmStage<double>) * HIP_PM_WARPS;
     return dyn + stat <= 220 * 1024;
 }
 
