@@ -1,6 +1,9 @@
 // Batched power spectra: many catalogs (each with its own N, L, R0, bins) in one
 // persistent pair-kernel launch, with the cell builds, the pair pass and the
-// FP64 finalize recorded once into a CUDA graph and replayed per run.
+// FP64 finalize recorded once into a CUDA graph and replayed per run.  The pair
+// pass is the Legendre-moment pass (hip_moments.cu) when every catalog has
+// R0 k_max <= 1024, with the edge functions' coefficients computed once when
+// the plan is built; otherwise the direct pass.
 //
 // A plan owns its device memory (sized for its catalogs at creation); the graph
 // refers to fixed addresses in it.  Host-resident inputs are copied into the
@@ -15,6 +18,7 @@
 #include <vector>
 
 #include "hip_internal.h"
+#include "hip_moments.h"
 #include "hip_workspace.h"
 
 std::mutex &hip_api_mutex();
@@ -28,6 +32,8 @@ struct CatLayout {
     int n_c = 1, n_cells = 1, n_e = 2, n_ell = 1, items = 0;
     size_t o_pos = 0, o_w = 0, o_x = 0, o_y = 0, o_z = 0, o_ws = 0, o_idx = 0, o_cid = 0, o_start = 0, o_fill = 0;
     size_t o_acc = 0, o_s1 = 0, o_np = 0, o_wt = 0, o_dd = 0, o_p = 0;
+    int pm_nc = 0;  // moment intervals (moment pass)
+    size_t o_ke = 0, o_coef = 0, o_mg = 0;
 };
 
 // Cells per side for a batched catalog: at least R0 wide, and no more cells
@@ -80,14 +86,19 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
     pl->lay.assign(nc, CatLayout());
     Carve cv;
     int nch = 1, nk_max = 1, items = 0;
-    // process the most expensive catalogs first (their items come first in the work list)
+    bool pm = true;  // every catalog within the moment pass's range
+    for (int i = 0; i < nc; ++i)
+        pm = pm && hip_pm_applicable(pl->cats[i].R0, pl->cats[i].k_edges[pl->cats[i].n_k], sizeof(T) == 4);
+    // process the most expensive catalogs first (their items come first in the work list); the
+    // direct pass costs per pair and edge, the moment pass per pair
     std::vector<int> order(nc);
     std::iota(order.begin(), order.end(), 0);
     std::vector<double> cost(nc);
     for (int i = 0; i < nc; ++i) {
         const hip_catalog &c = pl->cats[i];
-        cost[i] = (double)c.N * (double)c.N / (c.L * c.L * c.L) * c.R0 * c.R0 * c.R0 * (c.n_k + 1);
+        cost[i] = (double)c.N * (double)c.N / (c.L * c.L * c.L) * c.R0 * c.R0 * c.R0 * (pm ? 1.0 : c.n_k + 1.0);
     }
+    int nc_max = 1, ne_max = 1;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     for (int i = 0; i < nc; ++i) {
         const hip_catalog &c = pl->cats[i];
@@ -118,8 +129,17 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
         L.o_wt = cv.take(sizeof(double) * c.n_k);
         L.o_dd = cv.take(sizeof(double) * 3 * c.n_k);
         L.o_p = cv.take(sizeof(double) * 3 * c.n_k);
+        if (pm) {
+            L.pm_nc = hip_pm_intervals(c.R0, c.k_edges[c.n_k]);
+            nc_max = std::max(nc_max, L.pm_nc);
+            ne_max = std::max(ne_max, L.n_e);
+            L.o_ke = cv.take(sizeof(double) * L.n_e);
+            L.o_coef = cv.take(sizeof(double) * hip_pm_coef_doubles(L.n_e, L.pm_nc));
+            L.o_mg = cv.take(sizeof(double) * 3 * HIP_PM_M * L.pm_nc);
+        }
     }
     const size_t o_bc = cv.take(sizeof(BatchCat<T>) * nc), o_fc = cv.take(sizeof(FinalCat) * nc);
+    const size_t o_pc = cv.take(sizeof(PmCat<T>) * nc), o_cc = cv.take(sizeof(PmContractCat) * nc);
     const size_t o_misc = cv.take(sizeof(int) * 4);
     cudaError_t e = cudaMalloc(&pl->buf, cv.total);
     if (e != cudaSuccess) {
@@ -132,6 +152,8 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
     // descriptors
     std::vector<BatchCat<T>> bc(nc);
     std::vector<FinalCat> fc(nc);
+    std::vector<PmCat<T>> pc(nc);
+    std::vector<PmContractCat> cc(nc);
     for (int oi = 0; oi < nc; ++oi) {
         const int i = order[oi];
         const hip_catalog &c = pl->cats[i];
@@ -177,11 +199,48 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
         f.Wt = (double *)(b + L.o_wt);
         f.DD = (double *)(b + L.o_dd);
         f.P = (double *)(b + L.o_p);
+        if (pm) {
+            PmCat<T> &m = pc[oi];
+            std::memset(&m, 0, sizeof(m));
+            m.cl = d.cl;
+            m.p0 = d.p0;
+            m.p1 = d.p1;
+            m.los = d.los;
+            m.n_c = L.pm_nc;
+            m.item_begin = d.item_begin;
+            m.item_end = d.item_end;
+            m.R0 = (T)c.R0;
+            m.dc = (T)(c.R0 / L.pm_nc);
+            m.Mg = (double *)(b + L.o_mg);
+            m.npairs = d.npairs;
+            PmContractCat &k = cc[oi];
+            k.coef = (const double *)(b + L.o_coef);
+            k.Mg = (const double *)(b + L.o_mg);
+            k.n_e = L.n_e;
+            k.n_c = L.pm_nc;
+            k.n_ell = L.n_ell;
+            k.row = d.acc;
+        }
     }
     if ((e = cudaMemcpy(b + o_bc, bc.data(), sizeof(BatchCat<T>) * nc, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b + o_fc, fc.data(), sizeof(FinalCat) * nc, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (e = cudaMemcpy(b + o_fc, fc.data(), sizeof(FinalCat) * nc, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (pm && (e = cudaMemcpy(b + o_pc, pc.data(), sizeof(PmCat<T>) * nc, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (pm && (e = cudaMemcpy(b + o_cc, cc.data(), sizeof(PmContractCat) * nc, cudaMemcpyHostToDevice)) !=
+                   cudaSuccess)) {
         std::snprintf(g_batch_msg, sizeof(g_batch_msg), "descriptor upload: %s", cudaGetErrorString(e));
         return HIP_ERR_CUDA;
+    }
+    // the moment pass's edge-function coefficients depend only on the bins and R0: once per plan
+    for (int i = 0; pm && i < nc; ++i) {
+        const hip_catalog &c = pl->cats[i];
+        const CatLayout &L = pl->lay[i];
+        if ((e = cudaMemcpy(b + L.o_ke, c.k_edges, sizeof(double) * L.n_e, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = hip_pm_coeffs((const double *)(b + L.o_ke), L.n_e, L.n_ell, c.R0, c.k_edges[c.n_k],
+                               (double *)(b + L.o_coef), nullptr)) != cudaSuccess ||
+            (e = cudaDeviceSynchronize()) != cudaSuccess) {
+            std::snprintf(g_batch_msg, sizeof(g_batch_msg), "moment coefficients: %s", cudaGetErrorString(e));
+            return HIP_ERR_CUDA;
+        }
     }
     // pinned host mirror of the outputs
     pl->out_off.assign(nc, 0);
@@ -221,6 +280,8 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
         const float *w = c.w ? (L.dev_w ? c.w : (const float *)(b + L.o_w)) : nullptr;
         if ((ce = cudaMemsetAsync(b + L.o_acc, 0, sizeof(double) * 3 * L.n_e, st)) != cudaSuccess) break;
         if ((ce = cudaMemsetAsync(b + L.o_np, 0, sizeof(unsigned long long), st)) != cudaSuccess) break;
+        if (pm && (ce = cudaMemsetAsync(b + L.o_mg, 0, sizeof(double) * 3 * HIP_PM_M * L.pm_nc, st)) != cudaSuccess)
+            break;
         // each catalog has its own S1 and error word (the cell build clears both)
         ce = hip_build_cells<T>(pos, w, c.N, c.L, L.n_c, (T *)(b + L.o_x), (T *)(b + L.o_y), (T *)(b + L.o_z),
                                 (float *)(b + L.o_ws), (int *)(b + L.o_idx), (int *)(b + L.o_cid),
@@ -228,9 +289,16 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
                                 (int *)(b + L.o_s1 + sizeof(double)), st);
         launches += 3;
     }
-    if (ce == cudaSuccess) ce = hip_power_pairs_batched<T>((const BatchCat<T> *)(b + o_bc), nc, items, nch, counter,
-                                                           grid, st);
-    launches += 1;
+    if (pm) {
+        if (ce == cudaSuccess)
+            ce = hip_power_moments_batched<T>((const PmCat<T> *)(b + o_pc), nc, items, nc_max, counter,
+                                              (const PmContractCat *)(b + o_cc), ne_max, st);
+        launches += 2;
+    } else {
+        if (ce == cudaSuccess)
+            ce = hip_power_pairs_batched<T>((const BatchCat<T> *)(b + o_bc), nc, items, nch, counter, grid, st);
+        launches += 1;
+    }
     if (ce == cudaSuccess) ce = hip_power_finalize_batched((const FinalCat *)(b + o_fc), nc, nk_max, st);
     launches += 2;
     // copy the outputs and error words into the pinned host mirror

@@ -228,15 +228,126 @@ __device__ __forceinline__ void hip_pm_fold(T *M, int n_cp, int n_c, double *Mg)
     }
 }
 
-// The pair pass: the CTA takes work items (home cell, half-shell shift) from the
-// counter; its warps share the two cells' tiles and split the home particles,
-// test candidates one per lane and queue the accepted ones as tile indices; 32
+// One work item (home cell, half-shell shift; item counts within the catalog):
+// the CTA stages the two cells' tiles, its warps split the home particles, test
+// candidates one per lane and queue the accepted ones as tile indices; 32
 // queued pairs (and whatever is queued when a tile pair is done) are drained
-// into the CTA's moment array in shared memory ([3][M][n_cp], T, n_cp = n_c
-// rounded up to odd so the 16 moments of one interval fall in distinct banks).
-// The FP32 array is folded into the FP64 totals Mg whenever the CTA has added
-// HIP_PM_FOLD pairs since the last fold (at item boundaries, under a barrier)
-// and at the end.
+// into the CTA's moment array M.  Called by all threads of the CTA.
+template <typename T, int MASK>
+__device__ __forceinline__ void hip_pm_item(const CellList<T> &cl, long long p0, long long p1, int los, int item,
+                                            PmTiles<T> &tl, PmStage<T> &sg, T *M, int n_cp, int n_c, T R0, T dc,
+                                            unsigned long long &cnt, int &drained)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const T R0sq = R0 * R0, invR0 = T(1) / R0, inv_hdc = T(2) / dc, inv_dc = T(1) / dc;
+    const int n_c3 = cl.n_c;
+    const int c = item / HIP_NSHIFT, q = item - c * HIP_NSHIFT;
+    const int cx = c / (n_c3 * n_c3), cy = (c / n_c3) % n_c3, cz = c % n_c3;
+    const int dx = c_shift[q][0], dy = c_shift[q][1], dz = c_shift[q][2];
+    const int nb = (((cx + dx + n_c3) % n_c3) * n_c3 + (cy + dy + n_c3) % n_c3) * n_c3 + (cz + dz + n_c3) % n_c3;
+    PmShift<T> sh;
+    hip_cell_shift(cl, cx, dx, sh.x, sh.xl);
+    hip_cell_shift(cl, cy, dy, sh.y, sh.yl);
+    hip_cell_shift(cl, cz, dz, sh.z, sh.zl);
+    const int a0 = cl.cell_start[c], a1 = cl.cell_start[c + 1];
+    const int b0 = cl.cell_start[nb], b1 = cl.cell_start[nb + 1];
+    const bool self = (q == 0);
+    for (int hb = a0; hb < a1; hb += HIP_PM_TILE) {
+        const int hn = min(HIP_PM_TILE, a1 - hb);
+        __syncthreads();
+        for (int i = threadIdx.x; i < hn; i += blockDim.x) {
+            const long long oi = cl.idx[hb + i];
+            PmPt<T> p;
+            p.x = cl.x[hb + i];
+            p.y = cl.y[hb + i];
+            p.z = cl.z[hb + i];
+            p.in = (oi >= p0 && oi < p1) ? T(1) : T(0);
+            tl.h[i] = p;
+            tl.hw[i] = cl.w[hb + i];
+        }
+        for (int nbs = self ? hb : b0; nbs < b1; nbs += HIP_PM_TILE) {
+            const int nn = min(HIP_PM_TILE, b1 - nbs);
+            __syncthreads();
+            for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+                const long long oi = cl.idx[nbs + i];
+                PmPt<T> p;
+                p.x = cl.x[nbs + i];
+                p.y = cl.y[nbs + i];
+                p.z = cl.z[nbs + i];
+                p.in = (oi >= p0 && oi < p1) ? T(1) : T(0);
+                tl.n[i] = p;
+                tl.nw[i] = cl.w[nbs + i];
+            }
+            __syncthreads();
+            const bool same = self && (nbs == hb);
+            int qn = 0;  // queued pairs of this warp (ring head 0 after each partial drain)
+            int qh = 0;
+            for (int il = warp; il < hn; il += HIP_PM_WARPS) {
+                const PmPt<T> h = tl.h[il];
+                const T xi = h.x - sh.x, yi = h.y - sh.y, zi = h.z - sh.z;
+                const int ini = (int)h.in;
+                for (int jb = same ? il + 1 : 0; jb < nn; jb += 32) {
+                    const int jl = jb + lane;
+                    bool ok = false;
+                    int mult = 0;
+                    if (jl < nn) {
+                        const PmPt<T> p = tl.n[jl];
+                        const T ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
+                        const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        mult = ini + (int)p.in;
+                        ok = (r2 < R0sq) && (r2 > T(0)) && (mult > 0);
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                    if (ok) sg.q[(qh + qn + __popc(bal & lt_mask)) & (HIP_PM_QCAP - 1)] = (il << 9) | (jl << 2) | mult;
+                    qn += __popc(bal);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        hip_pm_drain<T, MASK>(sg, tl, sh, los, qh, 32, lane, M, n_cp, n_c, dc, inv_dc, inv_hdc,
+                                              invR0, cnt);
+                        qh = (qh + 32) & (HIP_PM_QCAP - 1);
+                        qn -= 32;
+                        drained += 32;
+                    }
+                }
+            }
+            if (qn > 0) {  // the tiles change after this tile pair
+                __syncwarp();
+                hip_pm_drain<T, MASK>(sg, tl, sh, los, qh, qn, lane, M, n_cp, n_c, dc, inv_dc, inv_hdc, invR0,
+                                      cnt);
+                drained += qn;
+            }
+        }
+    }
+}
+
+// Adds the CTA's per-warp item counts into since_fold and folds the FP32 moments
+// into Mg when HIP_PM_FOLD pairs have been added since the last fold (FP32 only;
+// the FP64 array is folded once per catalog).  Called by all threads.
+template <typename T>
+__device__ __forceinline__ void hip_pm_maybe_fold(T *M, int n_cp, int n_c, double *Mg, int *s_drained, int &drained,
+                                                  int &since_fold)
+{
+    if (sizeof(T) != 4) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_drained[warp] = drained;
+    __syncthreads();
+    int tot = 0;
+#pragma unroll
+    for (int w = 0; w < HIP_PM_WARPS; ++w) tot += s_drained[w];
+    drained = 0;
+    since_fold += tot;
+    if (since_fold >= HIP_PM_FOLD) {  // CTA-uniform
+        hip_pm_fold(M, n_cp, n_c, Mg);
+        since_fold = 0;
+    }
+}
+
+// The pair pass of one catalog: persistent CTAs take work items from the
+// counter (hip_pm_item).  The moment array lives in dynamic shared memory
+// ([3][M][n_cp], T, n_cp = n_c rounded up to odd so the 16 moments of one
+// interval fall in distinct banks) and is folded into the FP64 totals Mg every
+// HIP_PM_FOLD pairs (FP32, at item boundaries) and at the end.
 template <typename T, int MASK>
 __global__ void __launch_bounds__(HIP_PM_WARPS * 32)
     k_power_moments(CellList<T> cl, PowerKernelArgs a, T R0, int n_c, T dc, double *Mg)
@@ -246,113 +357,19 @@ __global__ void __launch_bounds__(HIP_PM_WARPS * 32)
     __shared__ int s_item, s_drained[HIP_PM_WARPS];
     extern __shared__ __align__(16) unsigned char pm_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    PmStage<T> &sg = stages[warp];
     const int n_cp = n_c | 1;
     T *M = reinterpret_cast<T *>(pm_raw);
     for (int i = threadIdx.x; i < 3 * HIP_PM_M * n_cp; i += blockDim.x) M[i] = T(0);
-    const T R0sq = R0 * R0, invR0 = T(1) / R0, inv_hdc = T(2) / dc, inv_dc = T(1) / dc;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const int n_c3 = cl.n_c;
     unsigned long long cnt = 0;
-    int since_fold = 0;  // pairs the CTA drained since the last fold
-    int drained = 0;     // pairs this warp drained in the current item
+    int since_fold = 0, drained = 0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = atomicAdd(a.work_counter, 1);
         __syncthreads();
         const int item = s_item;
         if (item >= a.n_items) break;
-        const int c = item / HIP_NSHIFT, q = item - c * HIP_NSHIFT;
-        const int cx = c / (n_c3 * n_c3), cy = (c / n_c3) % n_c3, cz = c % n_c3;
-        const int dx = c_shift[q][0], dy = c_shift[q][1], dz = c_shift[q][2];
-        const int nb = (((cx + dx + n_c3) % n_c3) * n_c3 + (cy + dy + n_c3) % n_c3) * n_c3 + (cz + dz + n_c3) % n_c3;
-        PmShift<T> sh;
-        hip_cell_shift(cl, cx, dx, sh.x, sh.xl);
-        hip_cell_shift(cl, cy, dy, sh.y, sh.yl);
-        hip_cell_shift(cl, cz, dz, sh.z, sh.zl);
-        const int a0 = cl.cell_start[c], a1 = cl.cell_start[c + 1];
-        const int b0 = cl.cell_start[nb], b1 = cl.cell_start[nb + 1];
-        const bool self = (q == 0);
-        for (int hb = a0; hb < a1; hb += HIP_PM_TILE) {
-            const int hn = min(HIP_PM_TILE, a1 - hb);
-            __syncthreads();
-            for (int i = threadIdx.x; i < hn; i += blockDim.x) {
-                const long long oi = cl.idx[hb + i];
-                PmPt<T> p;
-                p.x = cl.x[hb + i];
-                p.y = cl.y[hb + i];
-                p.z = cl.z[hb + i];
-                p.in = (oi >= a.p0 && oi < a.p1) ? T(1) : T(0);
-                tl.h[i] = p;
-                tl.hw[i] = cl.w[hb + i];
-            }
-            for (int nbs = self ? hb : b0; nbs < b1; nbs += HIP_PM_TILE) {
-                const int nn = min(HIP_PM_TILE, b1 - nbs);
-                __syncthreads();
-                for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-                    const long long oi = cl.idx[nbs + i];
-                    PmPt<T> p;
-                    p.x = cl.x[nbs + i];
-                    p.y = cl.y[nbs + i];
-                    p.z = cl.z[nbs + i];
-                    p.in = (oi >= a.p0 && oi < a.p1) ? T(1) : T(0);
-                    tl.n[i] = p;
-                    tl.nw[i] = cl.w[nbs + i];
-                }
-                __syncthreads();
-                const bool same = self && (nbs == hb);
-                int qn = 0;  // queued pairs of this warp (ring head 0 after each partial drain)
-                int qh = 0;
-                for (int il = warp; il < hn; il += HIP_PM_WARPS) {
-                    const PmPt<T> h = tl.h[il];
-                    const T xi = h.x - sh.x, yi = h.y - sh.y, zi = h.z - sh.z;
-                    const int ini = (int)h.in;
-                    for (int jb = same ? il + 1 : 0; jb < nn; jb += 32) {
-                        const int jl = jb + lane;
-                        bool ok = false;
-                        int mult = 0;
-                        if (jl < nn) {
-                            const PmPt<T> p = tl.n[jl];
-                            const T ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
-                            const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            mult = ini + (int)p.in;
-                            ok = (r2 < R0sq) && (r2 > T(0)) && (mult > 0);
-                        }
-                        const unsigned bal = __ballot_sync(0xffffffffu, ok);
-                        if (ok) sg.q[(qh + qn + __popc(bal & lt_mask)) & (HIP_PM_QCAP - 1)] = (il << 9) | (jl << 2) | mult;
-                        qn += __popc(bal);
-                        if (qn >= 32) {
-                            __syncwarp();
-                            hip_pm_drain<T, MASK>(sg, tl, sh, a.los, qh, 32, lane, M, n_cp, n_c, dc, inv_dc, inv_hdc,
-                                                  invR0, cnt);
-                            qh = (qh + 32) & (HIP_PM_QCAP - 1);
-                            qn -= 32;
-                            drained += 32;
-                        }
-                    }
-                }
-                if (qn > 0) {  // the tiles change after this tile pair
-                    __syncwarp();
-                    hip_pm_drain<T, MASK>(sg, tl, sh, a.los, qh, qn, lane, M, n_cp, n_c, dc, inv_dc, inv_hdc, invR0,
-                                          cnt);
-                    drained += qn;
-                }
-            }
-        }
-        // item boundary: fold the FP32 moments when the CTA has added enough pairs
-        if (sizeof(T) == 4) {
-            if (lane == 0) s_drained[warp] = drained;
-            __syncthreads();
-            int tot = 0;
-#pragma unroll
-            for (int w = 0; w < HIP_PM_WARPS; ++w) tot += s_drained[w];
-            drained = 0;
-            since_fold += tot;
-            if (since_fold >= HIP_PM_FOLD) {  // CTA-uniform
-                hip_pm_fold(M, n_cp, n_c, Mg);
-                since_fold = 0;
-            }
-        }
+        hip_pm_item<T, MASK>(cl, a.p0, a.p1, a.los, item, tl, stages[warp], M, n_cp, n_c, R0, dc, cnt, drained);
+        hip_pm_maybe_fold(M, n_cp, n_c, Mg, s_drained, drained, since_fold);
     }
     __syncthreads();
     hip_pm_fold(M, n_cp, n_c, Mg);
@@ -360,13 +377,60 @@ __global__ void __launch_bounds__(HIP_PM_WARPS * 32)
     if (lane == 0 && cnt) atomicAdd(a.npairs, cnt);
 }
 
-// S[il][e] = sum_c sum_m a[il][e][c][m] Mg[il][m][c]: one block per (il, e),
-// written as one partial row [3][n_e] of the power finalize.
-__global__ void __launch_bounds__(256) k_pm_contract(const double *__restrict__ a, const double *__restrict__ Mg,
-                                                     int n_e, int n_c, double *row)
+// The batched pair pass: all catalogs' work items end to end in one persistent
+// launch (l = 0, 2, 4 always).  A CTA's items increase, so it moves through the
+// catalogs in order; when it moves on it folds its moments and pair count into
+// the catalog it leaves.  The dynamic array is sized for the largest n_c.
+template <typename T>
+__global__ void __launch_bounds__(HIP_PM_WARPS * 32)
+    k_power_moments_batched(const PmCat<T> *__restrict__ cats, int n_cats, int n_items, int n_c_max, int *counter)
+{
+    __shared__ PmTiles<T> tl;
+    __shared__ PmStage<T> stages[HIP_PM_WARPS];
+    __shared__ int s_item, s_drained[HIP_PM_WARPS];
+    extern __shared__ __align__(16) unsigned char pm_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *M = reinterpret_cast<T *>(pm_raw);
+    for (int i = threadIdx.x; i < 3 * HIP_PM_M * (n_c_max | 1); i += blockDim.x) M[i] = T(0);
+    unsigned long long cnt = 0;
+    int since_fold = 0, drained = 0;
+    int ci = -1;
+    PmCat<T> cat;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        const bool done = item >= n_items;
+        int nci = ci < 0 ? 0 : ci;
+        if (!done)
+            while (nci < n_cats - 1 && item >= cats[nci].item_end) ++nci;
+        if (done || nci != ci) {  // CTA-uniform
+            if (ci >= 0) {
+                __syncthreads();
+                hip_pm_fold(M, cat.n_c | 1, cat.n_c, cat.Mg);  // leaves M zero
+                unsigned long long c2 = cnt;
+                for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+                if (lane == 0 && c2) atomicAdd(cat.npairs, c2);
+                cnt = 0;
+                since_fold = 0;
+            }
+            if (done) break;
+            ci = nci;
+            cat = cats[ci];
+        }
+        hip_pm_item<T, 21>(cat.cl, cat.p0, cat.p1, cat.los, item - cat.item_begin, tl, stages[warp], M, cat.n_c | 1,
+                           cat.n_c, cat.R0, cat.dc, cnt, drained);
+        hip_pm_maybe_fold(M, cat.n_c | 1, cat.n_c, cat.Mg, s_drained, drained, since_fold);
+    }
+}
+
+// S[il][e] = sum_c sum_m a[il][e][c][m] Mg[il][m][c] by one 256-thread block,
+// written as row[il n_e + e] (one partial row [3][n_e] of the power finalize).
+__device__ __forceinline__ void hip_pm_contract_block(const double *__restrict__ a, const double *__restrict__ Mg,
+                                                      int n_e, int n_c, int il, int e, double *row)
 {
     __shared__ double red[256];
-    const int il = blockIdx.x / n_e, e = blockIdx.x - il * n_e;
     const double *ae = a + ((size_t)il * n_e + e) * n_c * HIP_PM_M;
     const double *mg = Mg + (size_t)il * HIP_PM_M * n_c;
     double acc = 0.0;
@@ -383,11 +447,38 @@ __global__ void __launch_bounds__(256) k_pm_contract(const double *__restrict__ 
     if (threadIdx.x == 0) row[il * n_e + e] = red[0];
 }
 
+// one block per (il, e)
+__global__ void __launch_bounds__(256) k_pm_contract(const double *__restrict__ a, const double *__restrict__ Mg,
+                                                     int n_e, int n_c, double *row)
+{
+    const int il = blockIdx.x / n_e, e = blockIdx.x - il * n_e;
+    hip_pm_contract_block(a, Mg, n_e, n_c, il, e, row);
+}
+
+// blockIdx.y = catalog, blockIdx.x = il n_e_max + e
+__global__ void __launch_bounds__(256) k_pm_contract_batched(const PmContractCat *__restrict__ cc, int n_e_max)
+{
+    const PmContractCat c = cc[blockIdx.y];
+    const int il = blockIdx.x / n_e_max, e = blockIdx.x - il * n_e_max;
+    if (il >= c.n_ell || e >= c.n_e) return;
+    hip_pm_contract_block(c.coef, c.Mg, c.n_e, c.n_c, il, e, c.row);
+}
+
 // ------------------------------------------------------------------ host ----
 int hip_pm_intervals(double R0, double k_max)
 {
     const int n = (int)std::ceil(R0 * k_max / 4.0);
     return n < 8 ? 8 : n;
+}
+
+size_t hip_pm_coef_doubles(int n_e, int n_c) { return (size_t)3 * n_e * n_c * HIP_PM_M; }
+
+cudaError_t hip_pm_coeffs(const double *d_kedges, int n_e, int n_ell, double R0, double k_max, double *coef,
+                          cudaStream_t st)
+{
+    const int n_c = hip_pm_intervals(R0, k_max);
+    k_pm_coeffs<<<(n_e * n_c + 127) / 128, 128, 0, st>>>(d_kedges, n_e, n_c, R0 / n_c, n_ell, coef);
+    return cudaGetLastError();
 }
 
 size_t hip_pm_scratch_bytes(int n_e, int n_c)
@@ -456,3 +547,26 @@ template cudaError_t hip_power_moments<float>(const CellList<float> &, const Pow
                                               double, void *, double *, cudaStream_t);
 template cudaError_t hip_power_moments<double>(const CellList<double> &, const PowerKernelArgs &, const double *,
                                                int, double, void *, double *, cudaStream_t);
+
+template <typename T>
+cudaError_t hip_power_moments_batched(const PmCat<T> *cats, int n_cats, int n_items, int n_c_max, int *counter,
+                                      const PmContractCat *cc, int n_e_max, cudaStream_t st)
+{
+    const size_t dyn = pm_dyn_smem<T>(n_c_max);
+    cudaError_t e = cudaFuncSetAttribute(k_power_moments_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dyn);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_power_moments_batched<T>, HIP_PM_WARPS * 32, dyn);
+    const int grid = sms * (nb < 1 ? 1 : nb);
+    k_power_moments_batched<T><<<grid, HIP_PM_WARPS * 32, dyn, st>>>(cats, n_cats, n_items, n_c_max, counter);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_pm_contract_batched<<<dim3(3 * n_e_max, n_cats), 256, 0, st>>>(cc, n_e_max);
+    return cudaGetLastError();
+}
+template cudaError_t hip_power_moments_batched<float>(const PmCat<float> *, int, int, int, int *,
+                                                      const PmContractCat *, int, cudaStream_t);
+template cudaError_t hip_power_moments_batched<double>(const PmCat<double> *, int, int, int, int *,
+                                                       const PmContractCat *, int, cudaStream_t);

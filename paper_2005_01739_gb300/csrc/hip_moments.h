@@ -18,5 +18,32 @@ template <typename T>
 cudaError_t hip_power_moments(const CellList<T> &cl, const PowerKernelArgs &a, const double *kedges, int n_ell,
                               double R0, void *scratch, double *row, cudaStream_t st);
 
+// Batched moment pass: catalogs' work items laid end to end, one persistent
+// launch; the CTA folds its moments into a catalog's totals when it moves on.
+template <typename T>
+struct PmCat {
+    CellList<T> cl;
+    long long p0, p1;            // primary range in input order
+    int los, n_c;                // line-of-sight axis, intervals
+    int item_begin, item_end;    // global work items [begin, end)
+    T R0, dc;
+    double *Mg;                  // [3][M][n_c] FP64 moment totals (zeroed before the launch)
+    unsigned long long *npairs;  // ordered pairs counted
+};
+struct PmContractCat {
+    const double *coef, *Mg;     // hip_pm_coeffs output, moment totals
+    int n_e, n_c, n_ell;
+    double *row;                 // [3][n_e] edge sums written for l < n_ell
+};
+
+// Legendre coefficients of the edge functions (n_c intervals for R0, k_max);
+// d_kedges and coef are device arrays, coef holds hip_pm_coef_doubles(n_e, n_c).
+size_t hip_pm_coef_doubles(int n_e, int n_c);
+cudaError_t hip_pm_coeffs(const double *d_kedges, int n_e, int n_ell, double R0, double k_max, double *coef,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t hip_power_moments_batched(const PmCat<T> *cats, int n_cats, int n_items, int n_c_max, int *counter,
+                                      const PmContractCat *cc, int n_e_max, cudaStream_t st);
+
 cudaError_t hip_upload_coeffs_moments();
 cudaError_t hip_upload_pm_tables();

@@ -52,7 +52,10 @@ def _batch(device):
 def test_batched_matches_oracle_and_single_calls():
     cats = _batch(device=True)
     plan = binding.BatchPlan([c for c, _, _ in cats], "mixed")
-    assert plan.launches == 3 * len(cats) + 3
+    # cell builds (3 per catalog), the pair pass (moment pass and contraction, or the direct pass), finalize (2)
+    pm = all(binding.power_pair_pass(c["R0"], c["edges"][-1]) == 1 for c, _, _ in cats)
+    assert pm
+    assert plan.launches == 3 * len(cats) + (4 if pm else 3)
     res1 = plan.run()
     res2 = plan.run()  # replay of the same graph
     for (c, pos, w), (P, DD, n), (P2, _, n2) in zip(cats, res1, res2):
@@ -84,6 +87,24 @@ def test_batched_fp64_host_inputs_and_nonfinite():
     with pytest.raises(binding.HipError) as ei:
         binding.hip_power_batched(bad, "mixed")
     assert ei.value.status == binding.HIP_ERR_NONFINITE
+
+
+def test_batched_direct_pass_beyond_moment_range():
+    # one catalog with R0 k_max = 1080 (> 1024) sends the whole plan to the direct
+    # pass; both catalogs must equal their single FP64 calls
+    cats = []
+    for i, (N, L, R0, kmax, nk) in enumerate([(1200, 60.0, 12.0, 90.0, 255), (900, 50.0, 10.0, 3.0, 20)]):
+        pos, w = catalogs.thomas(N, L, 40, 1.5, seed=610 + i, background_frac=0.3, weights="u05_15")
+        cats.append((dict(pos=pos, w=w, L=L, R0=R0, edges=catalogs.linear_edges(0.5, kmax, nk), ell_max=4,
+                          los_axis=2), pos, w))
+    assert binding.power_pair_pass(12.0, 90.0, "fp64") == 0
+    plan = binding.BatchPlan([c for c, _, _ in cats], "fp64")
+    assert plan.launches == 3 * len(cats) + 3
+    for (c, pos, w), (P, DD, n) in zip(cats, plan.run()):
+        Ps, _, ns = binding.hip_power(pos, w, c["L"], c["R0"], c["edges"], 4, 2, "fp64")
+        assert n == ns
+        assert _err(P, Ps) < 1e-10
+    plan.close()
 
 
 def test_bispectrum_batched_matches_single_calls_and_oracle():
