@@ -209,11 +209,12 @@ hip_status hip_batch_plan_run(hip_batch_plan *plan, void *cuda_stream);
  * picks cells by hand): a batched catalog uses cells at least R0 wide and, when
  * it is sparse, fewer of them, about one per `occ` particles (more particles per
  * work item, fewer empty items).  hip_batch_plan_tune rebuilds the plan for occ
- * in {4, 8, 16, 32, 64} and for cells exactly R0 wide (reported as 0), replays
- * each once after a warm-up (the catalogs' inputs must be valid; their outputs
- * are overwritten), and keeps the fastest.  chosen_out (or NULL) receives the
- * chosen occ; ms_out (or NULL) receives the six replay times in that order, in ms.
- * A new plan starts at occ = 16.  Errors as in hip_batch_plan_run. */
+ * in {4, 8, 16, 32, 64, 128, 256} and for cells exactly R0 wide (reported as
+ * 0), replays each once after a warm-up (the catalogs' inputs must be valid;
+ * their outputs are overwritten), and keeps the fastest.  chosen_out (or NULL)
+ * receives the chosen occ; ms_out (or NULL) receives the eight replay times in
+ * that order, in ms.  A new plan starts at occ = 64.  Errors as in
+ * hip_batch_plan_run. */
 hip_status hip_batch_plan_tune(hip_batch_plan *plan, void *cuda_stream, int *chosen_out, float *ms_out);
 void hip_batch_plan_destroy(hip_batch_plan *plan);
 int hip_batch_plan_launches(const hip_batch_plan *plan);

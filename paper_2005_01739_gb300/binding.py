@@ -242,12 +242,12 @@ class BatchPlan:
         """Autotune the plan's cell shape (hip_batch_plan_tune): returns (chosen
         target particles per cell, 0 = cells R0 wide; {candidate: replay ms})."""
         chosen = ctypes.c_int(0)
-        ms = (ctypes.c_float * 6)()
+        ms = (ctypes.c_float * 8)()
         rc = self._lib.hip_batch_plan_tune(self._plan, _stream_handle(stream), ctypes.byref(chosen), ms)
         if rc != 0:
             raise HipError(rc, f"hip_batch_plan_tune: {self._lib.hip_status_string(rc).decode()} "
                                f"({self._lib.hip_batch_message().decode()})")
-        return int(chosen.value), dict(zip((4, 8, 16, 32, 64, 0), (float(x) for x in ms)))
+        return int(chosen.value), dict(zip((4, 8, 16, 32, 64, 128, 256, 0), (float(x) for x in ms)))
 
     def close(self):
         if self._plan:

@@ -74,7 +74,7 @@ struct hip_batch_plan {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;
     int launches = 0;
-    int occ = 16;  // target particles per cell (see batch_cells_per_side)
+    int occ = 64;  // target particles per cell (see batch_cells_per_side)
 };
 
 extern "C" const char *hip_batch_message(void) { return g_batch_msg; }
@@ -460,7 +460,7 @@ extern "C" hip_status hip_batch_plan_run(hip_batch_plan *pl, void *cuda_stream)
 
 // Candidate target occupancies of the autotuner (particles per cell; 0 = cells
 // exactly R0 wide).
-static const int k_tune_occ[] = {4, 8, 16, 32, 64, 0};
+static const int k_tune_occ[] = {4, 8, 16, 32, 64, 128, 256, 0};
 
 extern "C" hip_status hip_batch_plan_tune(hip_batch_plan *pl, void *cuda_stream, int *chosen_out, float *ms_out)
 {

@@ -147,7 +147,7 @@ def test_plan_autotune_keeps_results():
     try:
         before = [(P, n) for P, _, n in plan.run()]
         chosen, ms = plan.tune()
-        assert chosen in (4, 8, 16, 32, 64, 0) and all(v > 0 for v in ms.values())
+        assert chosen in (4, 8, 16, 32, 64, 128, 256, 0) and len(ms) == 8 and all(v > 0 for v in ms.values())
         after = plan.run()
         for (P0, n0), (P1, _, n1) in zip(before, after):
             assert _err(P1, P0) < 1e-5
