@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "hip_internal.h"
+#include "hip_moments.h"
 #include "hip_workspace.h"
 
 #define HIP_NOALLOC_BYTES ((size_t)64 << 20)  // 64 MiB
@@ -83,6 +84,9 @@ extern "C" hip_status hip_power_noalloc(const float *pos, const float *w, int64_
     const size_t o_small = cv.take(sizeof(double) * 8);
     const size_t o_wt = cv.take(sizeof(double) * n_k);
     const size_t o_dd = cv.take(sizeof(double) * 3 * n_k), o_p = cv.take(sizeof(double) * 3 * n_k);
+    // the Legendre-moment pass where it applies (as hip_power), else the direct pass
+    const bool moments = hip_pm_applicable(R0, k_edges[n_k], true);
+    const size_t o_pm = moments ? cv.take(hip_pm_scratch_bytes(n_e, hip_pm_intervals(R0, k_edges[n_k]))) : 0;
     if (cv.total > HIP_NOALLOC_BYTES) {
         std::snprintf(g_noalloc_msg, sizeof(g_noalloc_msg),
                       "hip_power_noalloc: this call needs %zu bytes of scratch, the static array holds %zu "
@@ -138,8 +142,12 @@ extern "C" hip_status hip_power_noalloc(const float *pos, const float *w, int64_
     ka.work_counter = counter;
     ka.partials = partials;  // every CTA overwrites its own row
     ka.npairs = npairs;
-    HIP_NA_CK(hip_power_pairs<float>(cl, ka, k_edges, n_ell, R0, grid, st), "pair kernel");
-    HIP_NA_CK(hip_power_finalize(partials, grid, n_e, n_ell, k_edges, R0, L, S1, Wt, DD, P, st), "finalize");
+    if (moments)
+        HIP_NA_CK(hip_power_moments<float>(cl, ka, k_edges, n_ell, R0, b + o_pm, partials, st), "moment pass");
+    else
+        HIP_NA_CK(hip_power_pairs<float>(cl, ka, k_edges, n_ell, R0, grid, st), "pair kernel");
+    HIP_NA_CK(hip_power_finalize(partials, moments ? 1 : grid, n_e, n_ell, k_edges, R0, L, S1, Wt, DD, P, st),
+              "finalize");
     unsigned long long hn = 0;
     HIP_NA_CK(cudaMemcpyAsync(P_out, P, sizeof(double) * n_ell * n_k, cudaMemcpyDeviceToHost, st), "D2H P");
     if (DD_out)
