@@ -100,6 +100,19 @@ def test_bin_chunks_parity(prec, nk, kmax):
     assert _err(P, Pref) < TOL[prec]
 
 
+@pytest.mark.parametrize("ell_max", [0, 2])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ell_max_subsets(prec, ell_max):
+    # l_max = 0 and 2 run their own kernel variants; their rows equal the
+    # leading rows of the l_max = 4 oracle (the multipoles are independent sums)
+    pos, w, L, R0, edges = _dense_case()
+    Pref, _, nref, _ = _oracle_P("dense", pos, w, L, R0, edges)
+    P, _, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, ell_max, 2, prec)
+    assert P.shape[0] == ell_max // 2 + 1
+    _same_count(prec, npairs, nref)
+    assert _err(P, Pref[: ell_max // 2 + 1]) < TOL[prec]
+
+
 def test_direct_pass_beyond_moment_range():
     # R0 k_max = 1080 > 1024: more than 256 moment intervals, so hip_power takes
     # the direct pair pass (every edge evaluated per pair; FP64 here, the FP32
