@@ -318,6 +318,26 @@ extern "C" hip_status hip_power(const float *pos, const float *w, int64_t N, dou
 }
 
 // --------------------------------------------------------- hip_bispectrum ----
+// S^a of the bispectrum estimator (Sec. 4.5): the l = 0 pair sum of the power
+// pass over all data, finalized into DD; the Legendre-moment pass where it
+// applies (pm_scratch then holds s_pass_scratch bytes), else the direct pass.
+static size_t s_pass_scratch(double R0, const double *k_edges, int n_k, bool fp32)
+{
+    if (!hip_pm_applicable(R0, k_edges[n_k], fp32)) return 256;
+    return hip_pm_scratch_bytes(n_k + 1, hip_pm_intervals(R0, k_edges[n_k]));
+}
+template <typename T>
+static cudaError_t s_pass(const CellList<T> &cl, const PowerKernelArgs &ka, const double *k_edges, int n_k, double R0,
+                          double L, const double *S1, double *Wt, double *DD, double *P, void *pm_scratch, int pgrid,
+                          cudaStream_t st)
+{
+    const bool pm = hip_pm_applicable(R0, k_edges[n_k], sizeof(T) == 4);
+    const cudaError_t e = pm ? hip_power_moments<T>(cl, ka, k_edges, 1, R0, pm_scratch, ka.partials, st)
+                             : hip_power_pairs<T>(cl, ka, k_edges, 1, R0, pgrid, st);
+    if (e != cudaSuccess) return e;
+    return hip_power_finalize(ka.partials, pm ? 1 : pgrid, n_k + 1, 1, k_edges, R0, L, S1, Wt, DD, P, st);
+}
+
 template <typename T>
 static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const float *rpos, int64_t N_r, double L,
                               double R0, const double *k_edges, int n_k, int lmax, double *B_out,
@@ -349,6 +369,7 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     const size_t o_small = cv.take(sizeof(double) * 16);
     const size_t o_wt = cv.take(sizeof(double) * n_k), o_dd = cv.take(sizeof(double) * 3 * n_k);
     const size_t o_p = cv.take(sizeof(double) * 3 * n_k), o_b = cv.take(sizeof(double) * tsz);
+    const size_t o_pm = cv.take(s_pass_scratch(R0, k_edges, n_k, sizeof(T) == 4));
     hip_status hs = ws.reserve(cv.total, st);
     if (hs != HIP_OK) return hs;
     char *b = (char *)ws.base;
@@ -410,9 +431,8 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     ka.work_counter = counter;
     ka.partials = (double *)(b + o_pp);
     ka.npairs = npairs;
-    HIP_CK(hip_power_pairs<T>(dcl, ka, k_edges, 1, R0, pgrid, st), "pair kernel (S)");
     double *Wt = (double *)(b + o_wt), *DD = (double *)(b + o_dd), *P = (double *)(b + o_p);
-    HIP_CK(hip_power_finalize(ka.partials, pgrid, n_e, 1, k_edges, R0, L, S1, Wt, DD, P, st), "finalize (S)");
+    HIP_CK(s_pass<T>(dcl, ka, k_edges, n_k, R0, L, S1, Wt, DD, P, b + o_pm, pgrid, st), "pair pass (S)");
 
     BispecArgs<T> ba;
     ba.data = dcl;
@@ -535,6 +555,10 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
         y.o_acc = cv.take(sizeof(double) * tsz);
     }
     const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * ne_max);
+    size_t pm_bytes = 256;  // the S passes run one after another in stream order and share this scratch
+    for (int i = 0; i < nc; ++i)
+        pm_bytes = std::max(pm_bytes, s_pass_scratch(cats[i].R0, cats[i].k_edges, cats[i].n_k, sizeof(T) == 4));
+    const size_t o_pm = cv.take(pm_bytes);
     const size_t o_desc = cv.take(sizeof(BispecCat<T>) * nc);
     const size_t o_cnt = cv.take(sizeof(int) * 4);
     hip_status hs = ws.reserve(cv.total, st);
@@ -620,10 +644,9 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
         ka.work_counter = counter;
         ka.partials = (double *)(b + o_pp);
         ka.npairs = npairs;
-        HIP_CK(hip_power_pairs<T>(dcl[i], ka, c.k_edges, 1, c.R0, pgrid, st), "pair kernel (S)");
-        HIP_CK(hip_power_finalize(ka.partials, pgrid, y.n_e, 1, c.k_edges, c.R0, c.L, small,
-                                  (double *)(b + y.o_wt), (double *)(b + y.o_dd), (double *)(b + y.o_p), st),
-               "finalize (S)");
+        HIP_CK(s_pass<T>(dcl[i], ka, c.k_edges, c.n_k, c.R0, c.L, small, (double *)(b + y.o_wt),
+                         (double *)(b + y.o_dd), (double *)(b + y.o_p), b + o_pm, pgrid, st),
+               "pair pass (S)");
         BispecCat<T> &d = desc[i];
         std::memset(&d, 0, sizeof(d));
         BispecArgs<T> &ba = d.a;
@@ -752,6 +775,7 @@ static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t
     const size_t o_wt = cv.take(sizeof(double) * n_k), o_dd = cv.take(sizeof(double) * 3 * n_k);
     const size_t o_p = cv.take(sizeof(double) * 3 * n_k), o_b = cv.take(sizeof(double) * tsz);
     const size_t o_e2 = cv.take(hip_e2_scratch_bytes(nodes, n_k));
+    const size_t o_pm = cv.take(s_pass_scratch(R0, k_edges, n_k, sizeof(T) == 4));
     hip_status hs = ws.reserve(cv.total, st);
     if (hs != HIP_OK) return hs;
     char *b = (char *)ws.base;
@@ -804,9 +828,8 @@ static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t
     ka.work_counter = counter;
     ka.partials = (double *)(b + o_pp);
     ka.npairs = npairs;
-    HIP_CK(hip_power_pairs<T>(dcl, ka, k_edges, 1, R0, pgrid, st), "pair kernel (S)");
     double *Wt = (double *)(b + o_wt), *DD = (double *)(b + o_dd), *P = (double *)(b + o_p);
-    HIP_CK(hip_power_finalize(ka.partials, pgrid, n_e, 1, k_edges, R0, L, S1, Wt, DD, P, st), "finalize (S)");
+    HIP_CK(s_pass<T>(dcl, ka, k_edges, n_k, R0, L, S1, Wt, DD, P, b + o_pm, pgrid, st), "pair pass (S)");
 
     BispecArgs<T> ba;
     std::memset(&ba, 0, sizeof(ba));
