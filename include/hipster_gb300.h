@@ -248,6 +248,28 @@ hip_status hip_power_noalloc(const float *pos, const float *w, int64_t N, double
 size_t hip_noalloc_capacity(void);
 const char *hip_noalloc_message(void);
 
+/* Random subsample of a catalog (Sec. 9: at fixed R0 the estimators cost N^2,
+ * so large catalogs, matter particles in the paper, are counted on a random
+ * fraction 1/f_sub of their tracers; the estimators then apply unchanged, with
+ * the subsample's own n_w).  Particle i is kept iff (z_i >> 11) <
+ * floor(fraction 2^53), z_i the i-th output of SplitMix64 seeded with `seed`
+ * (z = seed + (i+1) 0x9E3779B97F4A7C15, z ^= z >> 30, z *= 0xBF58476D1CE4E5B9,
+ * z ^= z >> 27, z *= 0x94D049BB133111EB, z ^= z >> 31); kept particles keep
+ * their input order.  Exact: the same selection on every machine.
+ *
+ *   pos, w      inputs as in hip_power (w NULL: no weights are written)
+ *   N           number of particles, 0 .. 2e9
+ *   fraction    kept fraction, 0 <= fraction <= 1 (1 keeps all)
+ *   seed        generator seed
+ *   pos_out     [N][3] float32, host or device, caller-owned (room for N)
+ *   w_out       [N] float32 or NULL (ignored when w is NULL)
+ *   n_out       number of particles kept (host)
+ *   cuda_stream stream to run on; the call returns after the outputs are written
+ * Errors: HIP_ERR_ARG (NULL pos, pos_out or n_out, N out of range),
+ * HIP_ERR_RANGE (fraction outside [0, 1] or not finite), HIP_ERR_CUDA. */
+hip_status hip_subsample(const float *pos, const float *w, int64_t N, double fraction, uint64_t seed, float *pos_out,
+                         float *w_out, int64_t *n_out, void *cuda_stream);
+
 /* Stage timing of the most recent hip_power call on this process, for
  * measurement.  When enabled (on != 0), each call records CUDA events on its
  * stream around its stages; hip_stage_times then writes, in milliseconds,

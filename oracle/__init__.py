@@ -20,7 +20,9 @@ What is computed, and where each piece comes from:
   quadrature, P^a_l (binned estimator of Sec. 3) and B^ab_l (summary, Sec. 4.5);
   and the random-free DDR^II term of App. A: omega^a_l (Eq. omega-ell-a-def),
   the kernel E^{II,ab}_l(r) = int p^2 dp/(2 pi^2) j_0(p r) omega^a_l omega^b_l and
-  the pair sum over it, with the bipolar form of App. B for cross-checks.
+  the pair sum over it, with the bipolar form of App. B for cross-checks;
+  the random subsample of Sec. 9 (a fraction 1/f_sub of the tracers), drawn
+  with SplitMix64 written here from its published definition.
 """
 from __future__ import annotations
 
@@ -389,3 +391,24 @@ def bispectrum_analytic(pos, w, L, R0, edges, lmax=4):
     # bispectrum_from_sums subtracts (S1/N_r) Trand; pass Trand = E2 N_r / V with N_r = 1
     B = bispectrum_from_sums(Td, E2 / V, DD[0], S1, 1.0, L, Wt)
     return B, dict(Tdata=Td, E2=E2, S=DD[0], Wt=Wt, npairs_data=npd)
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """Outputs 1..n of SplitMix64 seeded with `seed` (Steele, Lea & Flood 2014):
+    z = seed + i * 0x9E3779B97F4A7C15, z = (z ^ z>>30) * 0xBF58476D1CE4E5B9,
+    z = (z ^ z>>27) * 0x94D049BB133111EB, output z ^ z>>31 (all mod 2^64)."""
+    i = np.arange(1, n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def subsample_mask(n: int, fraction: float, seed: int) -> np.ndarray:
+    """The random subsample of Sec. 9: particle i (0-based) is kept iff its
+    uniform variate u_i = (z_{i+1} >> 11) 2^-53 is below `fraction`, compared
+    exactly in integers as (z >> 11) < floor(fraction 2^53)."""
+    import math
+    thr = np.uint64(math.floor(math.ldexp(float(fraction), 53)))
+    return (splitmix64(seed, n) >> np.uint64(11)) < thr

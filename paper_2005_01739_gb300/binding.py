@@ -68,6 +68,8 @@ def load(path: str | None = None):
         L.hip_bispectrum.argtypes = [P, P, i64, P, i64, d, d, i, P, i, i, i, P, P, P]
         L.hip_power_noalloc.restype = i
         L.hip_power_noalloc.argtypes = [P, P, i64, d, d, i, P, i, i, i, i64, i64, P, P, P, P]
+        L.hip_subsample.restype = i
+        L.hip_subsample.argtypes = [P, P, i64, d, ctypes.c_uint64, P, P, P, P]
         L.hip_noalloc_capacity.restype = ctypes.c_size_t
         L.hip_noalloc_capacity.argtypes = []
         L.hip_noalloc_message.restype = ctypes.c_char_p
@@ -162,6 +164,33 @@ def hip_power(pos, w, L, R0, k_edges, ell_max=4, los_axis=2, prec="mixed", prim_
     _check(lib, rc, "hip_power")
     del keep_p, keep_w
     return P, DD, int(npairs.value)
+
+
+def hip_subsample(pos, w, fraction, seed, stream=None):
+    """Random subsample of a catalog (hip_subsample): keeps particle i iff its
+    SplitMix64 variate is below `fraction`, in input order.  Outputs are of the
+    inputs' kind (torch tensors on the same device, else numpy): (pos [n, 3],
+    w [n] or None)."""
+    lib = load()
+    n = int(pos.shape[0])
+    pp, keep_p = _ptr(pos)
+    wp, keep_w = _ptr(w)
+    if hasattr(pos, "data_ptr"):
+        import torch
+        pos_out = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        w_out = None if w is None else torch.empty((n,), dtype=torch.float32, device=pos.device)
+    else:
+        pos_out = np.empty((n, 3), dtype=np.float32)
+        w_out = None if w is None else np.empty((n,), dtype=np.float32)
+    po, _ = _ptr(pos_out)
+    wo = None if w_out is None else _ptr(w_out)[0]
+    n_out = ctypes.c_int64(0)
+    rc = lib.hip_subsample(pp, wp, n, float(fraction), int(seed) & 0xFFFFFFFFFFFFFFFF, po, wo, ctypes.byref(n_out),
+                           _stream_handle(stream))
+    _check(lib, rc, "hip_subsample")
+    del keep_p, keep_w
+    m = int(n_out.value)
+    return pos_out[:m], (None if w_out is None else w_out[:m])
 
 
 def hip_power_noalloc(pos, w, L, R0, k_edges, ell_max=4, los_axis=2, prim_range=None, stream=None):

@@ -127,3 +127,18 @@ def test_power_pair_pass_choice():
         binding.power_pair_pass(-1.0, 5.0)
     with pytest.raises(ValueError):
         binding.power_pair_pass(10.0, 0.0)
+
+
+def test_subsample_argument_checks(lib):
+    # rejected before any device work
+    vp = ctypes.c_void_p
+    pos = np.zeros((4, 3), np.float32)
+    out = np.zeros((4, 3), np.float32)
+    n = ctypes.c_int64(0)
+    args = lambda f: (pos.ctypes.data_as(vp), None, 4, f, 1, out.ctypes.data_as(vp), None, ctypes.byref(n), None)
+    assert lib.hip_subsample(*args(1.5)) == binding.HIP_ERR_RANGE
+    assert lib.hip_subsample(*args(float("nan"))) == binding.HIP_ERR_RANGE
+    assert lib.hip_subsample(None, None, 4, 0.5, 1, out.ctypes.data_as(vp), None, ctypes.byref(n), None) == \
+        binding.HIP_ERR_ARG
+    assert lib.hip_subsample(pos.ctypes.data_as(vp), None, -1, 0.5, 1, out.ctypes.data_as(vp), None,
+                             ctypes.byref(n), None) == binding.HIP_ERR_ARG

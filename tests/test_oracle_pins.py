@@ -463,3 +463,24 @@ def test_ddr2_is_the_expectation_of_the_random_catalog_term():
     z = np.abs(mean - E2) / np.maximum(err, 1e-12 * np.max(np.abs(E2)))
     assert np.max(z) < 5.0, float(np.max(z))
     assert np.max(np.abs(mean - E2)) < 0.05 * np.max(np.abs(E2))
+
+
+# --------------------------------------------------------------- subsample ----
+def test_splitmix64_published_outputs():
+    # the first outputs of SplitMix64 seeded with 0, as printed by its reference implementation
+    z = oracle.splitmix64(0, 3)
+    assert [int(x) for x in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_subsample_fraction_and_limits():
+    n = 400_000
+    for f in (0.01, 0.3, 0.77):
+        k = int(oracle.subsample_mask(n, f, seed=12345).sum())
+        assert abs(k - f * n) < 6.0 * np.sqrt(n * f * (1 - f)), (f, k)
+    assert not oracle.subsample_mask(n, 0.0, 7).any()
+    assert oracle.subsample_mask(n, 1.0, 7).all()
+    # different seeds give (nearly) independent selections; nested fractions nest
+    a, b = oracle.subsample_mask(n, 0.5, 1), oracle.subsample_mask(n, 0.5, 2)
+    assert abs((a & b).sum() - 0.25 * n) < 6.0 * np.sqrt(n * 0.25 * 0.75)
+    small, big = oracle.subsample_mask(n, 0.2, 9), oracle.subsample_mask(n, 0.6, 9)
+    assert not (small & ~big).any()
