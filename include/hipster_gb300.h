@@ -248,6 +248,26 @@ hip_status hip_power_noalloc(const float *pos, const float *w, int64_t N, double
 size_t hip_noalloc_capacity(void);
 const char *hip_noalloc_message(void);
 
+/* The binned window kernel of the pair-separation window (Eq. omega-ell-a-def):
+ *
+ *   omega^a_l(p) = 4 pi int_0^R0 r^2 j_l(p r) jbar^a_l(r) W(r/R0) dr,
+ *
+ * which carries the window convolution and the Poisson/Gaussian covariance of
+ * the estimators (Sec. 6) and the random-free DDR^II term (App. A), in FP64:
+ * composite 16-point Gauss-Legendre in r on the three polynomial pieces of W,
+ * panels no wider than pi / max(p_max, k_hi).
+ *
+ *   k_edges, n_k   bins as in hip_power (host)
+ *   R0             truncation radius, > 0
+ *   lmax           0..4: l = 0 .. lmax are returned
+ *   p, n_p         [n_p] wavenumbers >= 0 (host), 1 <= n_p <= 2^20
+ *   omega_out      [(lmax+1)][n_k][n_p] float64 host, row-major (l, a, q)
+ *   cuda_stream    stream to run on; the call returns after omega_out is written
+ * Errors: HIP_ERR_ARG (NULL arrays, n_p or lmax out of range), HIP_ERR_RANGE
+ * (R0, edges or p invalid), HIP_ERR_NOMEM, HIP_ERR_CUDA. */
+hip_status hip_window_omega(const double *k_edges, int n_k, double R0, int lmax, const double *p, int n_p,
+                            double *omega_out, void *cuda_stream);
+
 /* Random subsample of a catalog (Sec. 9: at fixed R0 the estimators cost N^2,
  * so large catalogs, matter particles in the paper, are counted on a random
  * fraction 1/f_sub of their tracers; the estimators then apply unchanged, with

@@ -68,6 +68,8 @@ def load(path: str | None = None):
         L.hip_bispectrum.argtypes = [P, P, i64, P, i64, d, d, i, P, i, i, i, P, P, P]
         L.hip_power_noalloc.restype = i
         L.hip_power_noalloc.argtypes = [P, P, i64, d, d, i, P, i, i, i, i64, i64, P, P, P, P]
+        L.hip_window_omega.restype = i
+        L.hip_window_omega.argtypes = [P, i, d, i, P, i, P, P]
         L.hip_subsample.restype = i
         L.hip_subsample.argtypes = [P, P, i64, d, ctypes.c_uint64, P, P, P, P]
         L.hip_noalloc_capacity.restype = ctypes.c_size_t
@@ -164,6 +166,20 @@ def hip_power(pos, w, L, R0, k_edges, ell_max=4, los_axis=2, prec="mixed", prim_
     _check(lib, rc, "hip_power")
     del keep_p, keep_w
     return P, DD, int(npairs.value)
+
+
+def hip_window_omega(k_edges, R0, lmax, p, stream=None):
+    """omega^a_l(p) (Eq. omega-ell-a-def) for l = 0..lmax: [lmax+1, n_k, len(p)] float64."""
+    lib = load()
+    edges = np.ascontiguousarray(np.asarray(k_edges, dtype=np.float64))
+    pp = np.ascontiguousarray(np.atleast_1d(np.asarray(p, dtype=np.float64)))
+    n_k = len(edges) - 1
+    out = np.zeros((int(lmax) + 1, n_k, len(pp)))
+    rc = lib.hip_window_omega(edges.ctypes.data_as(ctypes.c_void_p), n_k, float(R0), int(lmax),
+                              pp.ctypes.data_as(ctypes.c_void_p), len(pp), out.ctypes.data_as(ctypes.c_void_p),
+                              _stream_handle(stream))
+    _check(lib, rc, "hip_window_omega")
+    return out
 
 
 def hip_subsample(pos, w, fraction, seed, stream=None):

@@ -936,6 +936,31 @@ extern "C" hip_status hip_bispectrum_partial(const float *pos, const float *w, i
 // ------------------------------------------------------ host self-checks -----
 // Evaluate the pair kernels' F_l(u) = D_l(u)/u^3 on the host with the same source
 // and coefficient tables (FP32 path when prec == HIP_PREC_MIXED).  For tests.
+extern "C" hip_status hip_window_omega(const double *k_edges, int n_k, double R0, int lmax, const double *p, int n_p,
+                                       double *omega_out, void *cuda_stream)
+{
+    g_errbuf[0] = 0;
+    if (!k_edges || !p || !omega_out || n_p < 1 || n_p > (1 << 20) || lmax < 0 || lmax > HIP_LMAX) return HIP_ERR_ARG;
+    if (!(R0 > 0.0) || !std::isfinite(R0)) return HIP_ERR_RANGE;
+    hip_status hs = hip_check_edges(k_edges, n_k);
+    if (hs != HIP_OK) return hs;
+    for (int q = 0; q < n_p; ++q)
+        if (!(p[q] >= 0.0) || !std::isfinite(p[q])) return HIP_ERR_RANGE;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    int dev = 0;
+    if ((hs = hip_device_setup(&dev)) != HIP_OK) return hs;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    Workspace &ws = g_ws[dev];
+    if ((hs = ws.reserve(hip_omega_scratch_bytes(k_edges, n_k, R0, p, n_p), st)) != HIP_OK) return hs;
+    cudaError_t e = hip_omega_eval(k_edges, n_k, R0, lmax, p, n_p, ws.base, omega_out, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_err("window omega", e);
+        return HIP_ERR_CUDA;
+    }
+    return HIP_OK;
+}
+
 extern "C" double hip_debug_F(int prec, int l, double u)
 {
     if (l < 0 || l > HIP_LMAX) return NAN;

@@ -17,6 +17,7 @@
 //   k_e2_S         S(p) at the p nodes from the histogram;
 //   k_e2_contract  the p integral, written as one extra FP64 partial row of the
 //                  bispectrum primary sum: -(S1/V) sum_{j != k} w_j w_k E^{II}.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -290,4 +291,55 @@ cudaError_t hip_e2_term(const CellList<float> &cl2, int n_items2, int *counter, 
     const int nout = (HIP_LMAX + 1) * n_k * n_k;
     k_e2_contract<<<(nout + 127) / 128, 128, 0, st>>>(om, S, pn, pw, nq, n_k, lmax, S1, L * L * L, row);
     return cudaGetLastError();
+}
+
+// r nodes of omega^a_l(p) at caller-given p: composite 16-point Gauss-Legendre on
+// the three pieces of W, panels no wider than pi / max(p_max, k_hi), as for the
+// DDR^II term.
+static void omega_r_nodes(const double *k_edges, int n_k, double R0, const double *p, int n_p, std::vector<double> &rn,
+                          std::vector<double> &rw)
+{
+    std::vector<double> gx, gw;
+    hip_gauss_legendre(16, gx, gw);
+    double pmax = k_edges[n_k];
+    for (int q = 0; q < n_p; ++q) pmax = std::max(pmax, std::fabs(p[q]));
+    const double hr = M_PI / pmax;
+    rn.clear();
+    rw.clear();
+    gl_panels(0.0, 0.5 * R0, hr, gx, gw, rn, rw);
+    gl_panels(0.5 * R0, 0.75 * R0, hr, gx, gw, rn, rw);
+    gl_panels(0.75 * R0, R0, hr, gx, gw, rn, rw);
+}
+
+size_t hip_omega_scratch_bytes(const double *k_edges, int n_k, double R0, const double *p, int n_p)
+{
+    std::vector<double> rn, rw;
+    omega_r_nodes(k_edges, n_k, R0, p, n_p, rn, rw);
+    const size_t nr = rn.size();
+    return sizeof(double) * (2 * nr + (size_t)(n_k + 1) + (size_t)n_p + (size_t)(HIP_LMAX + 1) * n_k * nr +
+                             (size_t)(HIP_LMAX + 1) * n_k * n_p) +
+           64 * 8;
+}
+
+// omega^a_l(p) of Eq. omega-ell-a-def at caller-given p, with the two kernels of
+// the DDR^II term.
+cudaError_t hip_omega_eval(const double *k_edges, int n_k, double R0, int lmax, const double *p, int n_p,
+                           void *scratch, double *out, cudaStream_t st)
+{
+    std::vector<double> rn, rw;
+    omega_r_nodes(k_edges, n_k, R0, p, n_p, rn, rw);
+    const int nr = (int)rn.size(), n_e = n_k + 1;
+    double *d = (double *)scratch;
+    double *drn = d, *drw = drn + nr, *ke = drw + nr, *pn = ke + n_e, *G = pn + n_p;
+    double *om = G + (size_t)(HIP_LMAX + 1) * n_k * nr;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(drn, rn.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(drw, rw.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(ke, k_edges, sizeof(double) * n_e, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(pn, p, sizeof(double) * n_p, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    k_e2_jbar<<<(nr + 127) / 128, 128, 0, st>>>(drn, drw, nr, ke, n_e, R0, G);
+    const long long nth = (long long)(lmax + 1) * n_p * ((n_k + HIP_E2_ACH - 1) / HIP_E2_ACH);
+    k_e2_omega<<<(unsigned)((nth + 127) / 128), 128, 0, st>>>(G, drn, nr, pn, n_p, n_k, lmax, om);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaMemcpyAsync(out, om, sizeof(double) * (lmax + 1) * n_k * n_p, cudaMemcpyDeviceToHost, st);
 }

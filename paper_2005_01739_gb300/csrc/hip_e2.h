@@ -23,4 +23,11 @@ cudaError_t hip_e2_term(const CellList<float> &cl2, int n_items2, int *counter, 
                         const double *k_edges, int n_k, int lmax, const double *S1, const E2Nodes &nd, void *scratch,
                         double *row, unsigned long long *npairs2, cudaStream_t st);
 
+// omega^a_l(p) (Eq. omega-ell-a-def) for l <= lmax at n_p caller-given p (host):
+// out[(l n_k + a) n_p + q] (host, written when the stream reaches it); scratch
+// holds hip_omega_scratch_bytes(...) bytes.
+size_t hip_omega_scratch_bytes(const double *k_edges, int n_k, double R0, const double *p, int n_p);
+cudaError_t hip_omega_eval(const double *k_edges, int n_k, double R0, int lmax, const double *p, int n_p,
+                           void *scratch, double *out, cudaStream_t st);
+
 cudaError_t hip_upload_coeffs_e2();

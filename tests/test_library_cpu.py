@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2005_01739_gb300 import binding, build
+from paper_2005_01739_gb300 import binding, build, catalogs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -142,3 +142,16 @@ def test_subsample_argument_checks(lib):
         binding.HIP_ERR_ARG
     assert lib.hip_subsample(pos.ctypes.data_as(vp), None, -1, 0.5, 1, out.ctypes.data_as(vp), None,
                              ctypes.byref(n), None) == binding.HIP_ERR_ARG
+
+
+def test_window_omega_argument_checks(lib):
+    # rejected on the host, before any device work
+    edges = catalogs.linear_edges(0.3, 3.0, 5)
+    for args, code in [((edges, -1.0, 4, [0.1]), binding.HIP_ERR_RANGE),
+                       ((edges, 10.0, 5, [0.1]), binding.HIP_ERR_ARG),
+                       ((edges, 10.0, 4, [-0.1]), binding.HIP_ERR_RANGE),
+                       ((edges, 10.0, 4, [float("nan")]), binding.HIP_ERR_RANGE),
+                       ((edges[::-1], 10.0, 4, [0.1]), binding.HIP_ERR_RANGE)]:
+        with pytest.raises(binding.HipError) as ei:
+            binding.hip_window_omega(*args)
+        assert ei.value.status == code
