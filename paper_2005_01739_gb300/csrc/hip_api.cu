@@ -21,6 +21,8 @@ static void set_err(const char *what, cudaError_t e)
 }
 
 extern "C" const char *hip_last_error(void) { return g_errbuf; }
+void hip_clear_error() { g_errbuf[0] = 0; }
+void hip_set_error(const char *what, cudaError_t e) { set_err(what, e); }
 
 extern "C" const char *hip_status_string(hip_status s)
 {

@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(HIP_SUB_THREADS) k_sub_scatter(const float *__
 extern "C" hip_status hip_subsample(const float *pos, const float *w, int64_t N, double fraction, uint64_t seed,
                                     float *pos_out, float *w_out, int64_t *n_out, void *cuda_stream)
 {
+    hip_clear_error();
     if (!pos || !pos_out || !n_out || N < 0 || N > 2000000000LL) return HIP_ERR_ARG;
     if (!(fraction >= 0.0 && fraction <= 1.0)) return HIP_ERR_RANGE;
     std::lock_guard<std::mutex> lk(hip_api_mutex());
@@ -176,6 +177,7 @@ extern "C" hip_status hip_subsample(const float *pos, const float *w, int64_t N,
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     if (e != cudaSuccess) {
+        hip_set_error("subsample", e);
         cudaGetLastError();
         return HIP_ERR_CUDA;
     }

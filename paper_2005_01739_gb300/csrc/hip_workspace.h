@@ -24,6 +24,10 @@ struct Carve {
 };
 
 Workspace &hip_workspace(int dev);
+// The message hip_last_error() returns: cleared at the start of a public call,
+// set with the failing step and the CUDA error when one fails.
+void hip_clear_error();
+void hip_set_error(const char *what, cudaError_t e);
 hip_status hip_device_setup(int *dev_out);
 bool hip_is_device_ptr(const void *p);
 int hip_cells_per_side(double L, double R0);
