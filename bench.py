@@ -1,9 +1,14 @@
 """Benchmark of the GB300 small-scale power-spectrum path (arXiv:2005.01739, Sec. 3).
 
 One step = one complete hip_power call on a device-resident catalog: cell-list
-build, FP32 pair kernel, FP64 finalize (W~^a, reduction, normalisation) and the
-download of P and DD.  Metric: unordered pairs with 0 < r < R0, times the number
-of k bins, per second (pairs x k-bins / s).
+build, the FP32 pair pass (Legendre moments of the separation, with the FP64
+projection of the bin-edge functions and the FP64 contraction), FP64 finalize
+(W~^a, reduction, normalisation) and the download of P and DD.  Metric:
+unordered pairs with 0 < r < R0, times the number of k bins, per second
+(pairs x k-bins / s).  The same line also reports the plain FP64 path, the
+bispectrum (with and without randoms), the parity of both precisions against
+the oracle on a primary sample, the subsample selection, the clocks seen and
+the oracle's own rate on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
