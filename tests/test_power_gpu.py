@@ -113,6 +113,19 @@ def test_ell_max_subsets(prec, ell_max):
     assert _err(P, Pref[: ell_max // 2 + 1]) < TOL[prec]
 
 
+def test_moment_pass_at_its_largest_range():
+    # R0 k_max = 1020 with 255 bins: 255 moment intervals, the most the moment pass takes
+    pos, w = catalogs.thomas(1500, 60.0, 40, 1.5, seed=35, background_frac=0.3, los_sigma=2.0)
+    L, R0 = 60.0, 12.0
+    edges = catalogs.linear_edges(0.5, 85.0, 255)
+    assert binding.power_pair_pass(R0, edges[-1], "mixed") == 1
+    Pref, _, nref, _ = _oracle_P("moment_edge", pos, w, L, R0, edges)
+    for prec in ("fp64", "mixed"):
+        P, _, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, prec)
+        _same_count(prec, npairs, nref)
+        assert _err(P, Pref) < TOL[prec], prec
+
+
 def test_direct_pass_beyond_moment_range():
     # R0 k_max = 1080 > 1024: more than 256 moment intervals, so hip_power takes
     # the direct pair pass (every edge evaluated per pair; FP64 here, the FP32
