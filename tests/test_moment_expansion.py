@@ -55,3 +55,44 @@ def test_wider_intervals_fail_the_bound():
     h2 = 16.0 / kmax
     err = _max_trunc_err(0, kmax, 5 * h2, h2)
     assert err > 1e-9 * kmax ** 3 / 3.0
+
+
+def test_moment_decomposition_reproduces_the_pair_sum():
+    # the whole decomposition in FP64 numpy: moments of omega L_l P_m(t) per interval, contracted with the
+    # edge functions' Legendre coefficients, differenced over the bin edges -> DD, against the oracle's
+    # brute-force pair sum (Sec. 3).  No CUDA code is involved.
+    rng = np.random.default_rng(5)
+    N, L, R0 = 300, 40.0, 10.0
+    pos = rng.uniform(0, L, (N, 3))
+    w = rng.uniform(0.5, 1.5, N)
+    edges = np.linspace(0.2, 3.0, 15)
+    DDref, _ = oracle.power_pair_sum(pos, w, L, R0, edges, 4, 2)
+    d = pos[:, None, :] - pos[None, :, :]
+    d -= L * np.round(d / L)
+    r = np.sqrt((d * d).sum(-1))
+    iu = np.triu_indices(N, 1)
+    rr, dz = r[iu], d[..., 2][iu]
+    ww = (w[:, None] * w[None, :])[iu]
+    keep = (rr > 0) & (rr < R0)
+    rr, mu, ww = rr[keep], dz[keep] / rr[keep], ww[keep]
+    om = 2.0 * ww * np.array([oracle.window(x) for x in rr / R0])  # both orders of each pair
+    Lw = [np.ones_like(mu), 0.5 * (3 * mu ** 2 - 1), (35 * mu ** 4 - 30 * mu ** 2 + 3) / 8]
+    n_c = max(8, int(np.ceil(R0 * edges[-1] / 4.0)))
+    h2 = R0 / n_c
+    c = np.minimum((rr / h2).astype(int), n_c - 1)
+    t = (rr - c * h2) / (0.5 * h2) - 1.0
+    P = Lg.legvander(t, M - 1)
+    gx, gw = Lg.leggauss(24)
+    V = Lg.legvander(gx, M - 1)
+    S = np.zeros((3, len(edges)))
+    for il, l in enumerate((0, 2, 4)):
+        mom = np.zeros((n_c, M))
+        np.add.at(mom, c, (om * Lw[il])[:, None] * P)
+        for e, k in enumerate(edges):
+            for cc in range(n_c):
+                f = _f(l, k, cc * h2 + 0.5 * h2 * (1 + gx))
+                a = (V * gw[:, None]).T @ f * (2 * np.arange(M) + 1) / 2
+                S[il, e] += a @ mom[cc]
+    k3 = edges ** 3
+    DD = 3 * (S[:, 1:] - S[:, :-1]) / (k3[1:] - k3[:-1])
+    assert np.max(np.abs(DD - DDref)) < 1e-11 * np.max(np.abs(DDref))
