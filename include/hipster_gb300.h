@@ -185,10 +185,12 @@ typedef struct {
 typedef struct hip_batch_plan hip_batch_plan;
 
 /* Batched power spectra (the estimator of hip_power, Sec. 3, for many catalogs):
- * the catalogs' cell builds, ONE persistent pair-kernel launch over all of their
- * work items, and the FP64 finalize are recorded into a CUDA graph at plan
- * creation and replayed by hip_batch_plan_run.  Catalogs may differ in N, L, R0,
- * bins, ell_max and line of sight.
+ * the catalogs' cell builds, ONE persistent pair-pass launch over all of their
+ * work items (the Legendre-moment pass, with one batched FP64 contraction, when
+ * every catalog has R0 k_max <= 1024; else the direct pass), and the FP64
+ * finalize are recorded into a CUDA graph at plan creation and replayed by
+ * hip_batch_plan_run.  Catalogs may differ in N, L, R0, bins, ell_max and line
+ * of sight.
  *
  * hip_batch_plan_create: validates every catalog (HIP_ERR_ARG/RANGE as in
  *   hip_power; hip_batch_message() names the catalog), allocates the plan's
