@@ -231,9 +231,12 @@ const char *hip_batch_message(void);
  * hip_noalloc_capacity() bytes (64 MiB) that every device loading the library
  * reserves until the process exits; no cudaMalloc/cudaFree or other allocating
  * routine is called.  It is for callers that cannot allocate device memory
- * while they run: work recorded into CUDA graphs, hosts whose own memory pool
- * owns the device, loops that cannot afford the device-wide synchronisation of
- * cudaMalloc/cudaFree.
+ * while they run: a host application whose own memory pool has already
+ * reserved the device's memory (a library cudaMalloc would fail or take memory
+ * the pool counts on), or a service that must know its peak device footprint
+ * before it starts.  The call is eager and synchronising, like hip_power: it
+ * reads an error word back to the host after the cell build and synchronises
+ * `cuda_stream` before returning.
  *
  * Limit: the call needs about 24 bytes per particle for device-resident inputs
  * (40 for host inputs), plus cell tables and per-CTA partial sums; a call that
@@ -241,9 +244,11 @@ const char *hip_batch_message(void);
  * bytes it needed.  The array's device address is looked up on the first call
  * made with each device current: make that first call before any stream
  * capture.  Every call shares the array (it keeps the previous call's
- * contents; each call clears what must start at zero); calls must not overlap
- * on the GPU, and this entry point serialises them and synchronises
- * `cuda_stream` before returning. */
+ * contents; each call clears what must start at zero); calls that overlapped
+ * on the GPU would race on it, so this entry point serialises its calls and
+ * synchronises `cuda_stream` before returning, on success and on failure.
+ * hip_noalloc_message() holds the reason for the last failing call (empty after
+ * a successful one). */
 hip_status hip_power_noalloc(const float *pos, const float *w, int64_t N, double L, double R0, hip_window window,
                              const double *k_edges, int n_k, int ell_max, int los_axis, int64_t prim_begin,
                              int64_t prim_end, double *P_out, double *DD_out, int64_t *npairs_out, void *cuda_stream);

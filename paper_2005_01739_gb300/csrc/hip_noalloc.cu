@@ -2,21 +2,26 @@
 // all of its scratch in one fixed, statically sized device array instead of the
 // library's growable workspace.
 //
-// Who needs this: code that must not allocate device memory while it runs --
-// work recorded into a CUDA graph (cudaMalloc is not capturable), hosts that
-// hand the whole device to their own memory pool so that a cudaMalloc from a
-// library fails or steals from it, and latency-sensitive loops where the
-// device-wide synchronisation implied by cudaMalloc/cudaFree is unacceptable.
+// Who needs this: callers that cannot allocate device memory while they run --
+// a host application whose own memory pool has already reserved the device's
+// memory (a cudaMalloc from a library would fail, or take memory the pool
+// counts on), and services that must know their peak device footprint before
+// they start, so that no call may grow it.
+//
+// The call is eager and synchronising: it reads the cell build's error word back
+// to the host in the middle of the call and synchronises `cuda_stream` before it
+// returns, like hip_power.
 //
 // The array below is reserved on every device that loads this library, for the
 // lifetime of the process.  Its device address is looked up once per device
 // (cudaGetSymbolAddress) on the first call made with that device current; make
-// that first call outside any stream capture.  Every call reuses the same array
+// that first call before any stream capture.  Every call reuses the same array
 // and it keeps the previous call's contents, so each call clears the counters
 // and accumulators it needs.  Calls must not overlap on the GPU: two calls whose
 // kernels ran at the same time would race on the array.  This entry point
 // serialises its calls on the host and synchronises the caller's stream before
-// returning, so calls made through it never overlap one another.
+// returning, also when a step fails, so calls made through it never overlap one
+// another.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -43,7 +48,6 @@ extern "C" hip_status hip_power_noalloc(const float *pos, const float *w, int64_
                                         int64_t prim_begin, int64_t prim_end, double *P_out, double *DD_out,
                                         int64_t *npairs_out, void *cuda_stream)
 {
-    g_noalloc_msg[0] = 0;
     if (!pos || !P_out) return HIP_ERR_ARG;
     if (N < 1 || N > 2000000000LL) return HIP_ERR_ARG;
     if (window != HIP_WINDOW_PHILCOX) return HIP_ERR_ARG;
@@ -55,8 +59,12 @@ extern "C" hip_status hip_power_noalloc(const float *pos, const float *w, int64_
     if (hs != HIP_OK) return hs;
 
     std::lock_guard<std::mutex> lk(hip_api_mutex());
+    g_noalloc_msg[0] = 0;
     int dev = 0;
-    if ((hs = hip_device_setup(&dev)) != HIP_OK) return hs;
+    if ((hs = hip_device_setup(&dev)) != HIP_OK) {
+        std::snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "device set-up: %s", hip_last_error());
+        return hs;
+    }
     cudaError_t e;
     if (!g_noalloc_ptr[dev]) {
         void *p = nullptr;
@@ -95,10 +103,14 @@ extern "C" hip_status hip_power_noalloc(const float *pos, const float *w, int64_
         return HIP_ERR_RANGE;
     }
     char *b = (char *)g_noalloc_ptr[dev];
+    // a failed step returns only after the work already queued on the array has
+    // finished, so that the next call cannot race with it
 #define HIP_NA_CK(call, what)                                                                                        \
     do {                                                                                                             \
         if ((e = (call)) != cudaSuccess) {                                                                           \
             std::snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "%s: %s", what, cudaGetErrorString(e));              \
+            cudaStreamSynchronize(st);                                                                               \
+            cudaGetLastError();                                                                                      \
             return HIP_ERR_CUDA;                                                                                     \
         }                                                                                                            \
     } while (0)

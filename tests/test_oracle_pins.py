@@ -484,3 +484,117 @@ def test_subsample_fraction_and_limits():
     assert abs((a & b).sum() - 0.25 * n) < 6.0 * np.sqrt(n * 0.25 * 0.75)
     small, big = oracle.subsample_mask(n, 0.2, 9), oracle.subsample_mask(n, 0.6, 9)
     assert not (small & ~big).any()
+
+
+# ------------------------------------------- estimator assembly (l > 0) -------
+# The pins above check the raw pair and primary sums; these run the oracle's
+# finalize functions (power_from_pairs, bispectrum_from_sums via bispectrum) and
+# compare whole estimates, every multipole, with the defining plane-wave forms
+# normalised as the paper does: P by n^2 V (Eq. general-Pk-ell with the
+# windowed counts of Eq. general-XY-counts, the RR term of Sec. 3), B by 6 n^3 V
+# with the six identical permutations of Eq. general-XYZ-counts, the DDR^I / DDR^II
+# split of Sec. 4.3 and the RRR term of Sec. 4.1.  A wrong phase ((-1)^l for
+# (-1)^(l/2) in P), a dropped (2l+1) or a wrong normaliser fails here.
+def _sphere_and_shell(n_ct, n_phi, n_k):
+    ct, wct = np.polynomial.legendre.leggauss(n_ct)
+    phi = np.arange(n_phi) * 2 * np.pi / n_phi
+    C, PH = np.meshgrid(ct, phi, indexing="ij")
+    S = np.sqrt(1 - C * C)
+    khat = np.stack([S * np.cos(PH), S * np.sin(PH), C], axis=-1).reshape(-1, 3)
+    wang = (np.outer(wct, np.full(n_phi, 2 * np.pi / n_phi)) / (4 * np.pi)).ravel()
+    xk, wk = np.polynomial.legendre.leggauss(n_k)
+    return khat, wang, xk, wk
+
+
+def _shell(edges, a, xk, wk):
+    # nodes and weights of (4 pi / v_a) int k^2 dk over bin a
+    klo, khi = edges[a], edges[a + 1]
+    ks = 0.5 * (khi - klo) * xk + 0.5 * (khi + klo)
+    return ks, 0.5 * (khi - klo) * wk * 3 * ks * ks / (khi ** 3 - klo ** 3)
+
+
+def test_power_estimate_equals_plane_wave_estimator():
+    L, R0 = 60.0, 20.0
+    pos = _tiny_catalog(9, L, 23, 6.0)
+    w = np.random.default_rng(24).uniform(0.5, 1.5, len(pos))
+    edges = np.array([0.05, 0.2, 0.35])
+    DD, _ = oracle.power_pair_sum(pos, w, L, R0, edges, ell_max=4)
+    Wt = oracle.window_transform_binned(edges, R0)
+    S1 = float(np.sum(w))
+    P = oracle.power_from_pairs(DD, S1, L, Wt)
+    V, n_w = L ** 3, S1 / L ** 3
+    d = _minimage(pos[:, None, :] - pos[None, :, :], L)
+    r = np.linalg.norm(d, axis=-1)
+    mask = (r > 0) & (r < R0)
+    ww = (w[:, None] * w[None, :])[mask] * np.array([oracle.window(x / R0) for x in r[mask]])
+    khat, wang, xk, wk = _sphere_and_shell(40, 80, 24)
+    for a in range(2):
+        ks, wks = _shell(edges, a, xk, wk)
+        for l in (0, 2, 4):
+            Ll = eval_legendre(l, khat[:, 2])  # line of sight z
+            dd = 0.0 + 0.0j
+            for k, wkk in zip(ks, wks):
+                dd += wkk * (2 * l + 1) * np.sum(wang * Ll * (np.exp(-1j * k * (khat @ d[mask].T)) @ ww))
+            expect = dd.real / (n_w * n_w * V) - (Wt[a] if l == 0 else 0.0)
+            assert abs(dd.imag) < 1e-9 * abs(dd)
+            assert P[l // 2, a] == pytest.approx(expect, rel=1e-8, abs=1e-9 * np.max(np.abs(P)))
+
+
+def _triple_plane_wave(prim_pos, prim_w, prim_is_data, pos, w, L, R0, edges, l, a, b, khat, wang, xk, wk):
+    """(2l+1) <L_l(k1hat.k2hat)> sum_p s_p sum_{j != k, both != p} w_j w_k
+    e^{-i k1.x_pj} e^{-i k2.x_pk} W(x_pj) W(x_pk), averaged over both k directions
+    and the shells a, b (one of the six identical permutations)."""
+    ka, wa = _shell(edges, a, xk, wk)
+    kb, wb = _shell(edges, b, xk, wk)
+    Lmat = eval_legendre(l, np.clip(khat @ khat.T, -1, 1)) * wang[:, None] * wang[None, :]
+    tot = 0.0 + 0.0j
+    for p in range(len(prim_pos)):
+        dv = _minimage(prim_pos[p] - pos, L)
+        r = np.linalg.norm(dv, axis=1)
+        sel = (r > 0) & (r < R0)
+        if prim_is_data:
+            sel[p] = False
+        dv, r = dv[sel], r[sel]
+        if len(r) == 0:
+            continue
+        f = w[sel] * np.array([oracle.window(x / R0) for x in r])
+        proj = khat @ dv.T
+        E1 = np.einsum("q,qdn->dn", wa, np.exp(-1j * ka[:, None, None] * proj[None]) * f)
+        E2 = np.einsum("q,qdn->dn", wb, np.exp(-1j * kb[:, None, None] * proj[None]) * f)
+        tot += prim_w[p] * (2 * l + 1) * (np.sum(E1.sum(1) * (Lmat @ E2.sum(1))) - np.sum(E1 * (Lmat @ E2)))
+    return tot
+
+
+def test_bispectrum_estimate_equals_plane_wave_estimator():
+    L, R0 = 60.0, 20.0
+    pos = _tiny_catalog(7, L, 29, 5.0)
+    w = np.random.default_rng(30).uniform(0.5, 1.5, len(pos))
+    rnd = np.mod(pos[:4] + np.random.default_rng(31).normal(0, 4.0, size=(4, 3)), L)
+    edges = np.array([0.05, 0.2, 0.35])
+    B, info = oracle.bispectrum(pos, w, rnd, L, R0, edges, lmax=4)
+    Wt = oracle.window_transform_binned(edges, R0)
+    S1 = float(np.sum(w))
+    V, n_w = L ** 3, S1 / L ** 3
+    khat, wang, xk, wk = _sphere_and_shell(16, 32, 8)
+    # S^a = sum_{i != j} w_i w_j jbar^a_0 W from its own plane waves (l = 0 of Eq. general-XY-counts)
+    d = _minimage(pos[:, None, :] - pos[None, :, :], L)
+    r = np.linalg.norm(d, axis=-1)
+    mask = (r > 0) & (r < R0)
+    ww = (w[:, None] * w[None, :])[mask] * np.array([oracle.window(x / R0) for x in r[mask]])
+    S = np.zeros(2)
+    for a in range(2):
+        ks, wks = _shell(edges, a, xk, wk)
+        S[a] = sum(wkk * np.sum(wang * (np.exp(-1j * k * (khat @ d[mask].T)) @ ww)).real for k, wkk in zip(ks, wks))
+    for l in range(5):
+        for a in range(2):
+            for b in range(2):
+                ddd = _triple_plane_wave(pos, w, True, pos, w, L, R0, edges, l, a, b, khat, wang, xk, wk)
+                ddr2 = _triple_plane_wave(rnd, np.ones(len(rnd)), False, pos, w, L, R0, edges, l, a, b,
+                                          khat, wang, xk, wk)
+                # 1/(6 n^3 V) [6 DDD - 3 (4 DDR^I + 2 DDR^II)] + 2 delta W~W~, DDR^II from the randoms
+                # with weight S1 / N_r each (1/f_rand for unit weights)
+                expect = (ddd - (S1 / len(rnd)) * ddr2).real / (V * n_w ** 3)
+                if l == 0:
+                    expect += -(Wt[a] * S[b] + Wt[b] * S[a]) / (V * n_w ** 2) + 2 * Wt[a] * Wt[b]
+                scale = max(np.max(np.abs(B[l])), np.max(np.abs(B[0])))
+                assert B[l, a, b] == pytest.approx(expect, rel=1e-7, abs=1e-8 * scale)

@@ -1,9 +1,10 @@
 """The allocation-free power-spectrum entry point (hip_power_noalloc).
 
-Some callers cannot allocate device memory while they run (graph capture,
-hosts whose own pool owns the device, loops that cannot pay for the
-synchronisation of cudaMalloc); this entry point serves them from a static
-device array.  Checked here through the C ABI against hip_power on two calls in
+Some callers cannot allocate device memory while they run (a host application
+whose own memory pool has already reserved the device's memory, or a service
+that must fix its peak device footprint up front); this entry point serves them
+from a static device array.  Like hip_power it is eager and synchronises the
+caller's stream before it returns.  Checked here through the C ABI against hip_power on two calls in
 a row (the array keeps the previous call's contents, so the second call also
 checks that everything that must start at zero is cleared), with the mixed-path
 tolerance of the other tests.  This file is collected last on purpose.
@@ -52,11 +53,32 @@ def test_noalloc_matches_hip_power_twice():
 
 
 def test_noalloc_rejects_oversized_call():
+    # host inputs are staged in the array too: about 40 bytes per particle
     cap = binding.load().hip_noalloc_capacity()
-    n = cap // 24 + 1000  # more particles than the static array can hold
+    n = cap // 40 + 1000
     pos = np.zeros((n, 3), np.float32)
     pos[:, 0] = np.linspace(0, 99, n)
     with pytest.raises(binding.HipError) as ei:
         binding.hip_power_noalloc(pos, None, 100.0, 10.0, catalogs.linear_edges(0.1, 1.0, 5))
     assert ei.value.status == binding.HIP_ERR_RANGE
     assert "bytes" in str(ei.value)
+
+
+def test_noalloc_device_input_limit():
+    # device-resident inputs need about 24 bytes per particle: just above the
+    # limit the call is refused, well below it the call runs
+    import torch
+    cap = binding.load().hip_noalloc_capacity()
+    edges = catalogs.linear_edges(0.1, 1.0, 5)
+    n_big = cap // 24 + 1000
+    big = torch.zeros((n_big, 3), dtype=torch.float32, device="cuda")
+    big[:, 0] = torch.linspace(0, 99, n_big, device="cuda")
+    with pytest.raises(binding.HipError) as ei:
+        binding.hip_power_noalloc(big, None, 100.0, 10.0, edges)
+    assert ei.value.status == binding.HIP_ERR_RANGE
+    assert "bytes" in str(ei.value)
+    del big
+    n_ok = cap // 24 - (1 << 18)
+    pos = torch.rand((n_ok, 3), dtype=torch.float32, device="cuda") * 100.0
+    P, _, n = binding.hip_power_noalloc(pos, None, 100.0, 2.0, edges, 0, 2)
+    assert np.all(np.isfinite(P)) and n > 0
