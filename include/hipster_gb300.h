@@ -239,7 +239,7 @@ const char *hip_batch_message(void);
  * `cuda_stream` before returning.
  *
  * Limit: the call needs about 24 bytes per particle for device-resident inputs
- * (40 for host inputs), plus cell tables and per-CTA partial sums; a call that
+ * (36 for host positions, 40 with host weights), plus cell tables and per-CTA partial sums; a call that
  * would not fit returns HIP_ERR_RANGE and hip_noalloc_message() says how many
  * bytes it needed.  The array's device address is looked up on the first call
  * made with each device current: make that first call before any stream

@@ -108,6 +108,10 @@ def load(path: str | None = None):
         L.hip_debug_D.argtypes = [i, i, d]
         L.hip_debug_F_array.restype = None
         L.hip_debug_F_array.argtypes = [i, i, P, P, i64]
+        L.hip_debug_bk_caps.restype = None
+        L.hip_debug_bk_caps.argtypes = [i, i]
+        L.hip_debug_bk_mode.restype = None
+        L.hip_debug_bk_mode.argtypes = [i, i]
         L.hip_set_profiling.restype = None
         L.hip_set_profiling.argtypes = [i]
         L.hip_stage_times.restype = i
@@ -421,6 +425,19 @@ def debug_D(variant: str, l: int, u: float) -> float:
     (closed form, asymptotic auxiliaries).  sin u and cos u are passed in correctly
     rounded, so the result isolates the D-form arithmetic."""
     return load().hip_debug_D({"series": 0, "fit": 1, "asym": 2}[variant], int(l), float(u))
+
+
+def debug_bk_caps(tc_grid_cap: int = 0, chunk_cap: int = 0) -> None:
+    """Test hook: cap the CTAs of the bispectrum's tensor-core contraction and the
+    primaries per chunk of the bispectrum pass (0 = the library's own choice)."""
+    load().hip_debug_bk_caps(int(tc_grid_cap), int(chunk_cap))
+
+
+def debug_bk_mode(contract_on_cores: bool = False, fold_prims: int = 0) -> None:
+    """Test hook: contract the mixed path's accumulators on the CUDA cores in FP64
+    instead of the tensor cores, and/or set the primaries between the tensor-core
+    contraction's FP64 folds (0 = the library's default)."""
+    load().hip_debug_bk_mode(int(bool(contract_on_cores)), int(fold_prims))
 
 
 def debug_F_array(prec: str, l: int, u) -> np.ndarray:

@@ -340,6 +340,218 @@ static cudaError_t s_pass(const CellList<T> &cl, const PowerKernelArgs &ka, cons
     return hip_power_finalize(ka.partials, pm ? 1 : pgrid, n_k + 1, 1, k_edges, R0, L, S1, Wt, DD, P, st);
 }
 
+// ------------------------------------------------ the bispectrum primary sum ----
+// Scratch plan of the B pass for catalogs whose largest n_k, n_cc are nk_max,
+// ncc_max and whose primaries (data then randoms, catalogs end to end) number
+// `total`.  Primaries go through the a_lm pass and the contraction in chunks of
+// at most `chunk` primaries, so X stays within HIP_BK_XBUDGET bytes.
+#define HIP_BK_XBUDGET ((size_t)2 << 30)
+static int g_bk_tc_grid_cap = 0;  // tests: caps the contraction's CTAs (0 = one per SM)
+static int g_bk_chunk_cap = 0;    // tests: caps the primaries per chunk (0 = by the X budget)
+static int g_bk_fold = 0;         // tests: primaries between the contraction's FP64 folds (0 = default)
+static int g_bk_cores = 0;        // tests: contract FP32 accumulators on the CUDA cores in FP64
+
+struct BkPlan {
+    int nc = 0, nk_max = 0, ncc_max = 0;
+    long long chunk = 0;
+    size_t o_cats = 0, o_spans = 0, o_segs = 0, o_X = 0, o_sp = 0, o_slots = 0, o_cc = 0, o_cnt = 0;
+    size_t slots_bytes = 0;
+    bool tc = false;  // contraction on the tensor cores
+};
+
+template <typename T>
+static BkPlan bk_plan(Carve &cv, int nc, int nk_max, int ncc_max, long long total, size_t cc_bytes)
+{
+    BkPlan pl;
+    pl.nc = nc;
+    pl.nk_max = nk_max;
+    pl.ncc_max = ncc_max;
+    const size_t per = sizeof(T) * HIP_NLM * (size_t)nk_max;
+    long long ch = (long long)(HIP_BK_XBUDGET / per);
+    if (g_bk_chunk_cap > 0 && ch > g_bk_chunk_cap) ch = g_bk_chunk_cap;
+    ch = (ch / 8) * 8;
+    if (ch < 8) ch = 8;
+    const long long tot8 = ((total + 7) / 8) * 8;
+    pl.chunk = ch < tot8 ? ch : tot8;
+    pl.o_cats = cv.take(sizeof(BkCat<T>) * nc);
+    pl.o_spans = cv.take(sizeof(BkSpan) * (nc + 1));
+    pl.o_segs = cv.take(sizeof(BkSeg) * (nc + 1));
+    pl.o_X = cv.take(per * (size_t)pl.chunk + sizeof(T) * 64 * (size_t)(nc + 1));
+    pl.o_sp = cv.take(sizeof(T) * ((size_t)pl.chunk + 8 * (size_t)(nc + 1)));
+    pl.slots_bytes = hip_bk_alm_slot_bytes<T>(ncc_max);
+    pl.o_slots = cv.take(pl.slots_bytes);
+    pl.tc = sizeof(T) == 4 && hip_bk_tc_supported(nk_max);
+    pl.o_cc = cv.take(cc_bytes);
+    pl.o_cnt = cv.take(sizeof(int) * 4);
+    return pl;
+}
+
+// Per catalog of the B pass (host side).
+struct BkHostCat {
+    long long n_prim;      // data + random primaries
+    int n_k, n_cc;
+    double R0;
+    const double *k_edges;  // host
+    double *cmom;           // device [n_cc][32]
+    double *acc;            // device [5][n_k][n_k], zeroed by bk_run
+};
+
+// The primary sum T of every catalog into its acc: the a_lm pass and the
+// contraction chunk by chunk, then the C term of each catalog.  `cats` holds the
+// device descriptors' host copies (complete but for cmom, which bk_run fills).
+template <typename T>
+static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCat> &hc, const BkPlan &pl, char *b,
+                         cudaStream_t st)
+{
+    cudaError_t e;
+#define HIP_CK(call, what)                                                                                           \
+    do {                                                                                                             \
+        if ((e = (call)) != cudaSuccess) {                                                                           \
+            set_err(what, e);                                                                                        \
+            return HIP_ERR_CUDA;                                                                                     \
+        }                                                                                                            \
+    } while (0)
+    const int nc = pl.nc;
+    BkCat<T> *dcats = (BkCat<T> *)(b + pl.o_cats);
+    BkSpan *dspans = (BkSpan *)(b + pl.o_spans);
+    BkSeg *dsegs = (BkSeg *)(b + pl.o_segs);
+    T *X = (T *)(b + pl.o_X);
+    T *sp = (T *)(b + pl.o_sp);
+    double *slots = (double *)(b + pl.o_slots);
+    int *cnt = (int *)(b + pl.o_cnt);  // [0] work counter, [1] status
+    for (int i = 0; i < nc; ++i) {
+        HIP_CK(cudaMemsetAsync(hc[i].cmom, 0, sizeof(double) * hc[i].n_cc * HIP_BK_NM, st), "memset");
+        HIP_CK(cudaMemsetAsync(hc[i].acc, 0, sizeof(double) * (HIP_LMAX + 1) * hc[i].n_k * hc[i].n_k, st), "memset");
+    }
+    HIP_CK(cudaMemsetAsync(slots, 0, pl.slots_bytes, st), "memset");
+    HIP_CK(cudaMemsetAsync(cnt, 0, sizeof(int) * 4, st), "memset");
+    HIP_CK(cudaMemcpyAsync(dcats, cats.data(), sizeof(BkCat<T>) * nc, cudaMemcpyHostToDevice, st), "H2D catalogs");
+    const int P = hip_bk_tc_stage_prims(pl.nk_max);
+    // walk the catalogs' primaries end to end, one chunk at a time
+    int ci = 0;
+    long long gi = 0;  // next primary of catalog ci
+    while (ci < nc) {
+        std::vector<BkSpan> spans;
+        std::vector<BkSeg> segs;
+        long long used = 0, x_off = 0, sp_off = 0;
+        int items = 0, stages = 0;
+        while (ci < nc && used < pl.chunk) {
+            const long long take = std::min(hc[ci].n_prim - gi, pl.chunk - used);
+            if (take > 0) {
+                BkSpan s;
+                s.cat = ci;
+                s.g0 = (int)gi;
+                s.g1 = (int)(gi + take);
+                s.item_begin = items;
+                items += (int)((take + HIP_BK_PRIM - 1) / HIP_BK_PRIM);
+                s.item_end = items;
+                s.x_off = x_off;
+                s.sp_off = sp_off;
+                spans.push_back(s);
+                BkSeg g;
+                g.X = X + x_off;
+                g.sp = sp + sp_off;
+                g.n_p = (int)take;
+                g.n_k = hc[ci].n_k;
+                g.stage_begin = stages;
+                stages += (int)((take + P - 1) / P);
+                g.stage_end = stages;
+                g.acc = hc[ci].acc;
+                segs.push_back(g);
+                x_off += ((take * HIP_NLM * hc[ci].n_k + 63) / 64) * 64;
+                sp_off += ((take + 7) / 8) * 8;
+                used += take;
+                gi += take;
+            }
+            if (gi >= hc[ci].n_prim) {
+                ++ci;
+                gi = 0;
+            }
+        }
+        if (spans.empty()) break;
+        HIP_CK(cudaMemcpyAsync(dspans, spans.data(), sizeof(BkSpan) * spans.size(), cudaMemcpyHostToDevice, st),
+               "H2D spans");
+        HIP_CK(cudaMemcpyAsync(dsegs, segs.data(), sizeof(BkSeg) * segs.size(), cudaMemcpyHostToDevice, st),
+               "H2D segments");
+        HIP_CK(cudaMemsetAsync(cnt, 0, sizeof(int), st), "memset");
+        HIP_CK(hip_bk_alm<T>(dcats, dspans, (int)spans.size(), items, pl.nk_max, pl.ncc_max, X, sp, slots, cnt, st),
+               "bispectrum a_lm pass");
+        if (pl.tc && !g_bk_cores)
+            HIP_CK(hip_bk_contract_tc(dsegs, (int)segs.size(), stages, pl.nk_max, cnt + 1, g_bk_tc_grid_cap, g_bk_fold,
+                                      st),
+                   "bispectrum contraction (tensor cores)");
+        else
+            HIP_CK(hip_bk_contract_f64<T>(dsegs, (int)segs.size(), used, pl.nk_max, st), "bispectrum contraction");
+    }
+    for (int i = 0; i < nc; ++i) {
+        BkCTerm c;
+        std::memset(&c, 0, sizeof(c));
+        for (int q = 0; q <= hc[i].n_k; ++q) c.k[q] = hc[i].k_edges[q];
+        c.R0 = hc[i].R0;
+        c.n_e = hc[i].n_k + 1;
+        c.n_cc = hc[i].n_cc;
+        c.cmom = hc[i].cmom;
+        c.acc = hc[i].acc;
+        HIP_CK(hip_bk_cterm(c, b + pl.o_cc, st), "bispectrum C term");
+    }
+    int status = 0;
+    HIP_CK(cudaMemcpyAsync(&status, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H status");
+    HIP_CK(cudaStreamSynchronize(st), "bispectrum sync");
+#undef HIP_CK
+    if (status) {
+        std::snprintf(g_errbuf, sizeof(g_errbuf), "bispectrum contraction: a bounded device wait gave up");
+        return HIP_ERR_TIMEOUT;
+    }
+    return HIP_OK;
+}
+
+// Host copy of one catalog's a_lm-pass descriptor.
+template <typename T>
+static BkCat<T> bk_cat(const CellList<T> &dcl, const CellList<T> &rcl, const int *dcell, const int *rcell,
+                       int64_t N, int64_t N_r, const int64_t *ranges, const double *k_edges, int n_k, double R0,
+                       double rand_weight, unsigned long long *npairs, double *cmom)
+{
+    BkCat<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.data = dcl;
+    a.rand = rcl;
+    a.dcell = dcell;
+    a.rcell = rcell;
+    a.n_data = (int)N;
+    a.n_rand = (int)N_r;
+    a.dp0 = ranges ? ranges[0] : 0;
+    a.dp1 = ranges ? ranges[1] : N;
+    a.rp0 = ranges ? ranges[2] : 0;
+    a.rp1 = ranges ? ranges[3] : N_r;
+    a.n_e = n_k + 1;
+    a.n_cc = hip_bk_intervals(R0, k_edges[n_k]);
+    a.R0 = (T)R0;
+    a.rand_weight = (T)rand_weight;
+    a.cc_scale = (T)(a.n_cc / R0);
+    a.cmom = cmom;
+    a.npairs = npairs;
+    for (int q = 0; q < HIP_BMAXE; ++q) {
+        const double k = q <= n_k ? k_edges[q] : 0.0;
+        a.k[q] = (T)k;
+        a.klo[q] = (T)(k - (double)a.k[q]);
+        a.k3[q] = (T)(k * k * k);
+        a.jfac[q] = q < n_k ? (T)(3.0 / (k_edges[q + 1] * k_edges[q + 1] * k_edges[q + 1] - k * k * k)) : T(0);
+    }
+    return a;
+}
+
+extern "C" void hip_debug_bk_caps(int tc_grid_cap, int chunk_cap)
+{
+    g_bk_tc_grid_cap = tc_grid_cap > 0 ? tc_grid_cap : 0;
+    g_bk_chunk_cap = chunk_cap > 0 ? chunk_cap : 0;
+}
+
+extern "C" void hip_debug_bk_mode(int contract_on_cores, int fold_prims)
+{
+    g_bk_cores = contract_on_cores != 0;
+    g_bk_fold = fold_prims > 0 ? fold_prims : 0;
+}
+
 template <typename T>
 static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const float *rpos, int64_t N_r, double L,
                               double R0, const double *k_edges, int n_k, int lmax, double *B_out,
@@ -351,8 +563,8 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     const int n_e = n_k + 1;
     const int pgrid = hip_power_grid<T>();
     const bool dpos = hip_is_device_ptr(pos), dw = w && hip_is_device_ptr(w), drp = hip_is_device_ptr(rpos);
-    const int bparts_max = 152 * 8;  // upper bound on the bispectrum grid
     const size_t tsz = (size_t)(HIP_LMAX + 1) * n_k * n_k;
+    const int n_cc = hip_bk_intervals(R0, k_edges[n_k]);
 
     Carve cv;
     const size_t o_pos = dpos ? 0 : cv.take(sizeof(float) * 3 * N);
@@ -367,11 +579,13 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     const size_t o_dsc = cv.take(sizeof(int) * N), o_rsc = cv.take(sizeof(int) * N_r);
     const size_t o_rs = cv.take(sizeof(int) * (n_cells + 1)), o_rf = cv.take(sizeof(int) * n_cells);
     const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * n_e);
-    const size_t o_bp = cv.take(sizeof(double) * bparts_max * tsz);
+    const size_t o_acc = cv.take(sizeof(double) * tsz);
+    const size_t o_cmom = cv.take(sizeof(double) * n_cc * HIP_BK_NM);
     const size_t o_small = cv.take(sizeof(double) * 16);
     const size_t o_wt = cv.take(sizeof(double) * n_k), o_dd = cv.take(sizeof(double) * 3 * n_k);
     const size_t o_p = cv.take(sizeof(double) * 3 * n_k), o_b = cv.take(sizeof(double) * tsz);
     const size_t o_pm = cv.take(s_pass_scratch(R0, k_edges, n_k, sizeof(T) == 4));
+    const BkPlan pl = bk_plan<T>(cv, 1, n_k, n_cc, N + N_r, hip_bk_cterm_scratch_bytes(n_cc, n_k));
     hip_status hs = ws.reserve(cv.total, st);
     if (hs != HIP_OK) return hs;
     char *b = (char *)ws.base;
@@ -400,7 +614,7 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     double *S1 = small, *S1r = small + 1;
     unsigned long long *npairs = (unsigned long long *)(small + 2);  // [2]: P pass; [3], [4]: B pass
     int *err = (int *)(small + 5), *errr = err + 1;
-    int *counter = (int *)(small + 6), *bcounter = counter + 1;
+    int *counter = (int *)(small + 6);
     T *dx = (T *)(b + o_dx), *dy = (T *)(b + o_dy), *dz = (T *)(b + o_dz);
     T *rx = (T *)(b + o_rx), *ry = (T *)(b + o_ry), *rz = (T *)(b + o_rz);
     int *dstart = (int *)(b + o_ds), *rstart = (int *)(b + o_rs);
@@ -424,50 +638,31 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     CellList<T> rcl{rx, ry, rz, (const float *)(b + o_rw), (const int *)(b + o_ridx), rstart, n_c, L, L / n_c};
     HIP_CK(cudaMemsetAsync(npairs, 0, 3 * sizeof(unsigned long long), st), "memset");
     HIP_CK(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st), "memset");
-    PowerKernelArgs ka;
-    ka.n_e = n_e;
-    ka.los = 2;
-    ka.p0 = 0;
-    ka.p1 = N;
-    ka.n_items = n_cells * HIP_NSHIFT;
-    ka.work_counter = counter;
-    ka.partials = (double *)(b + o_pp);
-    ka.npairs = npairs;
     double *Wt = (double *)(b + o_wt), *DD = (double *)(b + o_dd), *P = (double *)(b + o_p);
-    HIP_CK(s_pass<T>(dcl, ka, k_edges, n_k, R0, L, S1, Wt, DD, P, b + o_pm, pgrid, st), "pair pass (S)");
-
-    BispecArgs<T> ba;
-    ba.data = dcl;
-    ba.rand = rcl;
-    ba.n_cells = n_cells;
-    ba.dcell = (const int *)(b + o_dsc);
-    ba.rcell = (const int *)(b + o_rsc);
-    ba.n_data = (int)N;
-    ba.n_rand = (int)N_r;
-    ba.n_e = n_e;
-    ba.R0 = (T)R0;
-    ba.rand_weight = (T)(-hS1 / (double)N_r);
-    ba.work_counter = bcounter;
-    ba.partials = (double *)(b + o_bp);
-    ba.npairs = npairs + 1;
-    ba.dp0 = ranges ? ranges[0] : 0;
-    ba.dp1 = ranges ? ranges[1] : N;
-    ba.rp0 = ranges ? ranges[2] : 0;
-    ba.rp1 = ranges ? ranges[3] : N_r;
-    for (int q = 0; q < HIP_BMAXE; ++q) {
-        const double k = q < n_e ? k_edges[q] : 0.0;
-        ba.k[q] = (T)k;
-        ba.klo[q] = (T)(k - (double)ba.k[q]);
-        ba.k3[q] = (T)(k * k * k);
-        ba.jfac[q] = q + 1 < n_e ? (T)(3.0 / (k_edges[q + 1] * k_edges[q + 1] * k_edges[q + 1] - k * k * k)) : T(0);
+    if (!partial) {
+        PowerKernelArgs ka;
+        ka.n_e = n_e;
+        ka.los = 2;
+        ka.p0 = 0;
+        ka.p1 = N;
+        ka.n_items = n_cells * HIP_NSHIFT;
+        ka.work_counter = counter;
+        ka.partials = (double *)(b + o_pp);
+        ka.npairs = npairs;
+        HIP_CK(s_pass<T>(dcl, ka, k_edges, n_k, R0, L, S1, Wt, DD, P, b + o_pm, pgrid, st), "pair pass (S)");
     }
-    int bgrid = 0;
-    HIP_CK(hip_bispec_pairs<T>(ba, bparts_max, &bgrid, st), "bispectrum kernel");
+    std::vector<BkCat<T>> cats(1, bk_cat<T>(dcl, rcl, (const int *)(b + o_dsc), (const int *)(b + o_rsc), N, N_r,
+                                            ranges, k_edges, n_k, R0, -hS1 / (double)N_r, npairs + 1,
+                                            (double *)(b + o_cmom)));
+    std::vector<BkHostCat> hc(1);
+    hc[0] = BkHostCat{N + N_r, n_k, n_cc, R0, k_edges, (double *)(b + o_cmom), (double *)(b + o_acc)};
+    if ((hs = bk_run<T>(cats, hc, pl, b, st)) != HIP_OK) return hs;
+    double *acc = (double *)(b + o_acc);
     double *B = (double *)(b + o_b);
     if (partial)
-        HIP_CK(hip_bispec_sum(ba.partials, bgrid, n_k, lmax, B, st), "bispectrum sum");
+        HIP_CK(hip_bispec_sum(acc, 1, n_k, lmax, B, st), "bispectrum sum");
     else
-        HIP_CK(hip_bispec_finalize(ba.partials, bgrid, n_k, lmax, L, S1, DD, Wt, B, st), "bispectrum finalize");
+        HIP_CK(hip_bispec_finalize(acc, 1, n_k, lmax, L, S1, DD, Wt, B, st), "bispectrum finalize");
     const size_t nout = (size_t)(lmax + 1) * n_k * n_k;
     std::vector<double> hB(nout);
     unsigned long long hn[3] = {0, 0, 0};
@@ -521,7 +716,8 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
         int n_c, n_cells, n_k, n_e;
         bool dpos, dw, drp;
         size_t o_pos, o_w, o_rp, o_dx, o_dy, o_dz, o_dw, o_didx, o_dcid, o_rx, o_ry, o_rz, o_rw, o_ridx, o_rcid;
-        size_t o_ds, o_df, o_dsc, o_rsc, o_rs, o_rf, o_small, o_wt, o_dd, o_p, o_b, o_acc;
+        size_t o_ds, o_df, o_dsc, o_rsc, o_rs, o_rf, o_small, o_wt, o_dd, o_p, o_b, o_acc, o_cmom;
+        int n_cc;
     };
     std::vector<Lay> lay(nc);
     Carve cv;
@@ -555,14 +751,23 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
         y.o_wt = cv.take(sizeof(double) * c.n_k), y.o_dd = cv.take(sizeof(double) * 3 * c.n_k);
         y.o_p = cv.take(sizeof(double) * 3 * c.n_k), y.o_b = cv.take(sizeof(double) * tsz);
         y.o_acc = cv.take(sizeof(double) * tsz);
+        y.n_cc = hip_bk_intervals(c.R0, c.k_edges[c.n_k]);
+        y.o_cmom = cv.take(sizeof(double) * y.n_cc * HIP_BK_NM);
     }
     const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * ne_max);
     size_t pm_bytes = 256;  // the S passes run one after another in stream order and share this scratch
     for (int i = 0; i < nc; ++i)
         pm_bytes = std::max(pm_bytes, s_pass_scratch(cats[i].R0, cats[i].k_edges, cats[i].n_k, sizeof(T) == 4));
     const size_t o_pm = cv.take(pm_bytes);
-    const size_t o_desc = cv.take(sizeof(BispecCat<T>) * nc);
-    const size_t o_cnt = cv.take(sizeof(int) * 4);
+    int ncc_max = 1;
+    size_t cc_bytes = 256;
+    long long total = 0;
+    for (int i = 0; i < nc; ++i) {
+        ncc_max = std::max(ncc_max, lay[i].n_cc);
+        cc_bytes = std::max(cc_bytes, hip_bk_cterm_scratch_bytes(lay[i].n_cc, lay[i].n_k));
+        total += cats[i].N + cats[i].N_r;
+    }
+    const BkPlan pl = bk_plan<T>(cv, nc, nk_max, ncc_max, total, cc_bytes);
     hip_status hs = ws.reserve(cv.total, st);
     if (hs != HIP_OK) return hs;
     char *b = (char *)ws.base;
@@ -626,8 +831,8 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
     }
     // S^a of every catalog: the l = 0 power pair sum (one launch each; the
     // partial rows are reused in stream order)
-    std::vector<BispecCat<T>> desc(nc);
-    int items = 0;
+    std::vector<BkCat<T>> bcats(nc);
+    std::vector<BkHostCat> hcs(nc);
     for (int i = 0; i < nc; ++i) {
         const hip_bcatalog &c = cats[i];
         const Lay &y = lay[i];
@@ -636,7 +841,6 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
         int *counter = (int *)(small + 6);
         HIP_CK(cudaMemsetAsync(npairs, 0, 3 * sizeof(unsigned long long), st), "memset");
         HIP_CK(cudaMemsetAsync(counter, 0, sizeof(int), st), "memset");
-        HIP_CK(cudaMemsetAsync(b + y.o_acc, 0, sizeof(double) * (HIP_LMAX + 1) * c.n_k * c.n_k, st), "memset");
         PowerKernelArgs ka;
         ka.n_e = y.n_e;
         ka.los = 2;
@@ -649,46 +853,13 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
         HIP_CK(s_pass<T>(dcl[i], ka, c.k_edges, c.n_k, c.R0, c.L, small, (double *)(b + y.o_wt),
                          (double *)(b + y.o_dd), (double *)(b + y.o_p), b + o_pm, pgrid, st),
                "pair pass (S)");
-        BispecCat<T> &d = desc[i];
-        std::memset(&d, 0, sizeof(d));
-        BispecArgs<T> &ba = d.a;
-        ba.data = dcl[i];
-        ba.rand = rcl[i];
-        ba.n_cells = y.n_cells;
-        ba.dcell = (const int *)(b + y.o_dsc);
-        ba.rcell = (const int *)(b + y.o_rsc);
-        ba.n_data = (int)c.N;
-        ba.n_rand = (int)c.N_r;
-        ba.n_e = y.n_e;
-        ba.R0 = (T)c.R0;
-        ba.rand_weight = (T)(-hsm[(size_t)i * 6] / (double)c.N_r);
-        ba.npairs = npairs + 1;
-        ba.dp0 = 0;
-        ba.dp1 = c.N;
-        ba.rp0 = 0;
-        ba.rp1 = c.N_r;
-        for (int q = 0; q < HIP_BMAXE; ++q) {
-            const double k = q < y.n_e ? c.k_edges[q] : 0.0;
-            ba.k[q] = (T)k;
-            ba.klo[q] = (T)(k - (double)ba.k[q]);
-            ba.k3[q] = (T)(k * k * k);
-            ba.jfac[q] = q + 1 < y.n_e
-                             ? (T)(3.0 / (c.k_edges[q + 1] * c.k_edges[q + 1] * c.k_edges[q + 1] - k * k * k))
-                             : T(0);
-        }
-        const int64_t n_prim = c.N + c.N_r;
-        d.item_begin = items;
-        items += (int)((n_prim + HIP_BCTA_PRIM - 1) / HIP_BCTA_PRIM);
-        d.item_end = items;
-        d.acc = (double *)(b + y.o_acc);
+        bcats[i] = bk_cat<T>(dcl[i], rcl[i], (const int *)(b + y.o_dsc), (const int *)(b + y.o_rsc), c.N, c.N_r,
+                             nullptr, c.k_edges, c.n_k, c.R0, -hsm[(size_t)i * 6] / (double)c.N_r, npairs + 1,
+                             (double *)(b + y.o_cmom));
+        hcs[i] = BkHostCat{c.N + c.N_r, c.n_k, y.n_cc, c.R0, c.k_edges, (double *)(b + y.o_cmom),
+                           (double *)(b + y.o_acc)};
     }
-    BispecCat<T> *ddesc = (BispecCat<T> *)(b + o_desc);
-    int *bcounter = (int *)(b + o_cnt);
-    HIP_CK(cudaMemcpyAsync(ddesc, desc.data(), sizeof(BispecCat<T>) * nc, cudaMemcpyHostToDevice, st),
-           "H2D descriptors");
-    HIP_CK(cudaMemsetAsync(bcounter, 0, sizeof(int), st), "memset");
-    int bgrid = 0;
-    HIP_CK(hip_bispec_pairs_batched<T>(ddesc, nc, items, nk_max, bcounter, &bgrid, st), "batched bispectrum kernel");
+    if ((hs = bk_run<T>(bcats, hcs, pl, b, st)) != HIP_OK) return hs;
     std::vector<std::vector<double>> hB(nc);
     std::vector<unsigned long long> hn((size_t)nc * 3);
     for (int i = 0; i < nc; ++i) {
@@ -756,8 +927,8 @@ static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t
     const int n_e = n_k + 1;
     const int pgrid = hip_power_grid<T>();
     const bool dpos = hip_is_device_ptr(pos), dw = w && hip_is_device_ptr(w);
-    const int bparts_max = 152 * 8;
     const size_t tsz = (size_t)(HIP_LMAX + 1) * n_k * n_k;
+    const int n_cc = hip_bk_intervals(R0, k_edges[n_k]);
     E2Nodes nodes;
     hip_e2_nodes(k_edges, n_k, R0, nodes);
 
@@ -772,12 +943,14 @@ static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t
     const size_t o_w2 = cv.take(sizeof(float) * N), o_i2 = cv.take(sizeof(int) * N), o_c2 = cv.take(sizeof(int) * N);
     const size_t o_s2 = cv.take(sizeof(int) * (n_cells2 + 1)), o_f2 = cv.take(sizeof(int) * n_cells2);
     const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * n_e);
-    const size_t o_bp = cv.take(sizeof(double) * (bparts_max + 1) * tsz);
+    const size_t o_acc = cv.take(sizeof(double) * 2 * tsz);  // [0] primary sum, [1] the E^II row
+    const size_t o_cmom = cv.take(sizeof(double) * n_cc * HIP_BK_NM);
     const size_t o_small = cv.take(sizeof(double) * 16);
     const size_t o_wt = cv.take(sizeof(double) * n_k), o_dd = cv.take(sizeof(double) * 3 * n_k);
     const size_t o_p = cv.take(sizeof(double) * 3 * n_k), o_b = cv.take(sizeof(double) * tsz);
     const size_t o_e2 = cv.take(hip_e2_scratch_bytes(nodes, n_k));
     const size_t o_pm = cv.take(s_pass_scratch(R0, k_edges, n_k, sizeof(T) == 4));
+    const BkPlan pl = bk_plan<T>(cv, 1, n_k, n_cc, N, hip_bk_cterm_scratch_bytes(n_cc, n_k));
     hip_status hs = ws.reserve(cv.total, st);
     if (hs != HIP_OK) return hs;
     char *b = (char *)ws.base;
@@ -802,7 +975,7 @@ static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t
     double *S1 = small, *S1b = small + 1;
     unsigned long long *npairs = (unsigned long long *)(small + 2);  // [0]: P pass; [1], [2]: B pass
     int *err = (int *)(small + 5), *err2 = err + 1;
-    int *counter = (int *)(small + 6), *bcounter = counter + 1, *hcounter = counter + 2;
+    int *counter = (int *)(small + 6), *hcounter = counter + 2;
     T *dx = (T *)(b + o_dx), *dy = (T *)(b + o_dy), *dz = (T *)(b + o_dz);
     int *dstart = (int *)(b + o_ds);
     HIP_CK(hip_build_cells<T>(dposp, dwp, N, L, n_c, dx, dy, dz, (float *)(b + o_dw), (int *)(b + o_didx),
@@ -833,42 +1006,21 @@ static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t
     double *Wt = (double *)(b + o_wt), *DD = (double *)(b + o_dd), *P = (double *)(b + o_p);
     HIP_CK(s_pass<T>(dcl, ka, k_edges, n_k, R0, L, S1, Wt, DD, P, b + o_pm, pgrid, st), "pair pass (S)");
 
-    BispecArgs<T> ba;
-    std::memset(&ba, 0, sizeof(ba));
-    ba.data = dcl;
-    ba.rand = dcl;  // no random primaries
-    ba.n_cells = n_cells;
-    ba.dcell = (const int *)(b + o_dsc);
-    ba.rcell = (const int *)(b + o_dsc);
-    ba.n_data = (int)N;
-    ba.n_rand = 0;
-    ba.n_e = n_e;
-    ba.R0 = (T)R0;
-    ba.rand_weight = T(0);
-    ba.work_counter = bcounter;
-    ba.partials = (double *)(b + o_bp);
-    ba.npairs = npairs + 1;
-    ba.dp0 = 0;
-    ba.dp1 = N;
-    ba.rp0 = 0;
-    ba.rp1 = 0;
-    for (int q = 0; q < HIP_BMAXE; ++q) {
-        const double k = q < n_e ? k_edges[q] : 0.0;
-        ba.k[q] = (T)k;
-        ba.klo[q] = (T)(k - (double)ba.k[q]);
-        ba.k3[q] = (T)(k * k * k);
-        ba.jfac[q] = q + 1 < n_e ? (T)(3.0 / (k_edges[q + 1] * k_edges[q + 1] * k_edges[q + 1] - k * k * k)) : T(0);
-    }
-    int bgrid = 0;
-    HIP_CK(hip_bispec_pairs<T>(ba, bparts_max, &bgrid, st), "bispectrum kernel");
+    // the data primaries' sum (no random primaries)
+    std::vector<BkCat<T>> cats(1, bk_cat<T>(dcl, dcl, (const int *)(b + o_dsc), (const int *)(b + o_dsc), N, 0,
+                                            nullptr, k_edges, n_k, R0, 0.0, npairs + 1, (double *)(b + o_cmom)));
+    std::vector<BkHostCat> hc(1);
+    double *acc = (double *)(b + o_acc);
+    hc[0] = BkHostCat{N, n_k, n_cc, R0, k_edges, (double *)(b + o_cmom), acc};
+    if ((hs = bk_run<T>(cats, hc, pl, b, st)) != HIP_OK) return hs;
     CellList<float> cl2{(const float *)(b + o_x2), (const float *)(b + o_y2), (const float *)(b + o_z2),
                         (const float *)(b + o_w2), (const int *)(b + o_i2), (const int *)(b + o_s2), n_c2, L,
                         L / n_c2};
     HIP_CK(hip_e2_term(cl2, n_cells2 * HIP_NSHIFT, hcounter, R0, L, k_edges, n_k, lmax, S1, nodes, b + o_e2,
-                       ba.partials + (size_t)bgrid * tsz, nullptr, st),
+                       acc + tsz, nullptr, st),
            "DDR^II term");
     double *B = (double *)(b + o_b);
-    HIP_CK(hip_bispec_finalize(ba.partials, bgrid + 1, n_k, lmax, L, S1, DD, Wt, B, st), "bispectrum finalize");
+    HIP_CK(hip_bispec_finalize(acc, 2, n_k, lmax, L, S1, DD, Wt, B, st), "bispectrum finalize");
     const size_t nout = (size_t)(lmax + 1) * n_k * n_k;
     std::vector<double> hB(nout);
     unsigned long long hn[3] = {0, 0, 0};

@@ -1,22 +1,26 @@
-// Bispectrum kernels (Sec. 4 of arXiv:2005.01739).
+// Bispectrum kernels (Sec. 4 of arXiv:2005.01739): the a_lm pass, the FP64
+// contraction and the C term.  The tensor-core contraction is in hip_bk_tc.cu.
 //
-// For every primary p (data particles, then the random catalog) the kernel
+// For every primary p (data particles, then the random catalog) the a_lm pass
 // forms, over data neighbours j with 0 < |x_p - x_j| < R0,
 //     A^a_lm(p) = sum_j w_j W(r/R0) jbar^a_l(r) R_lm(rhat)        (Eq. AC-def, binned)
-//     C^ab_l(p) = sum_j w_j^2 W^2 jbar^a_l(r) jbar^b_l(r)
 // with real spherical harmonics R_lm scaled so that sum_m R_lm(u) R_lm(v) =
 // L_l(u.v) (the addition theorem with the 4 pi / (2l+1) absorbed; real and
-// complex harmonics give the same sum over m), and accumulates
-//     T^ab_l += s_p [ sum_m A^a_lm A^b_lm - C^ab_l ](p),
-// s_p = w_p for data primaries and -S1/N_r for random ones (the DDR^II term
-// of Sec. 4.3 estimated with a random catalog).
+// complex harmonics give the same sum over m), and writes it to X[p][lm][a].
+// The primary sum T^ab_l = sum_p s_p [sum_m A^a_lm A^b_lm - C^ab_l](p) (s_p = w_p
+// for data primaries, -S1/N_r for random ones: the DDR^II term of Sec. 4.3 with
+// a random catalog) is then the contraction sum_p s_p X_p X_p^T minus
+//     sum_p s_p C^ab_l(p) = sum_(p,j) s_p w_j^2 W(r)^2 jbar^a_l(r) jbar^b_l(r),
+// a pair sum of a function of r alone.  The a_lm pass accumulates it as 32
+// Legendre moments of s_p w_j^2 W^2 per separation interval; the FP64 C-term
+// kernels contract them with the products jbar^a_l jbar^b_l.
 //
-// One warp owns one primary at a time.  Accepted neighbours go to a per-warp
-// queue holding r, w_j W, w_j^2 W^2 and the 25 R_lm; the queue is drained with
-// one lane per bin edge e, each lane evaluating F_l(r k_e), l = 0..4 (see
-// hip_math.cuh) and accumulating w W F_l R_lm into its 25 registers.  The same
-// drain forms jbar^a_l from adjacent edges and stages it for the C term.  At
-// the end of a primary the edge sums are differenced into A^a_lm and contracted.
+// a_lm pass: one warp owns one primary at a time (8 consecutive sorted primaries
+// per work item).  Accepted neighbours are queued as separation vectors; 32 at a
+// time they get one lane each for r, W, the 25 R_lm and the C-term moments, and
+// are then drained with one lane per bin edge e: each lane evaluates
+// F_l(r k_e), l = 0..4 (see hip_math.cuh), and accumulates w W F_l R_lm into its
+// 25 registers.  At the end of the primary, adjacent edges give A^a_lm.
 #include <cmath>
 #include <cstdio>
 
@@ -27,6 +31,9 @@ static __constant__ HipCoeffs c_coeffs;
 // normalisation of the real harmonics: sqrt((l-m)!/(l+m)!) (times sqrt 2 for m > 0)
 static __constant__ float c_ylm_norm_f[HIP_LMAX + 1][HIP_LMAX + 1];
 static __constant__ double c_ylm_norm_d[HIP_LMAX + 1][HIP_LMAX + 1];
+// Legendre recurrence P_{m+1} = a_m t P_m - b_m P_{m-1}: a_m = (2m+1)/(m+1), b_m = m/(m+1)
+static __constant__ float c_leg_f[2][HIP_BK_NM];
+static __constant__ double c_leg_d[2][HIP_BK_NM];
 
 cudaError_t hip_upload_coeffs_bispec()
 {
@@ -46,7 +53,23 @@ cudaError_t hip_upload_coeffs_bispec()
             nf[l][m] = (float)v;
         }
     if ((e = cudaMemcpyToSymbol(c_ylm_norm_f, nf, sizeof(nf))) != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(c_ylm_norm_d, nd, sizeof(nd));
+    if ((e = cudaMemcpyToSymbol(c_ylm_norm_d, nd, sizeof(nd))) != cudaSuccess) return e;
+    float lf[2][HIP_BK_NM];
+    double ld[2][HIP_BK_NM];
+    for (int m = 0; m < HIP_BK_NM; ++m) {
+        ld[0][m] = (2.0 * m + 1.0) / (m + 1.0);
+        ld[1][m] = (double)m / (m + 1.0);
+        lf[0][m] = (float)ld[0][m];
+        lf[1][m] = (float)ld[1][m];
+    }
+    if ((e = cudaMemcpyToSymbol(c_leg_f, lf, sizeof(lf))) != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_leg_d, ld, sizeof(ld));
+}
+
+int hip_bk_intervals(double R0, double k_max)
+{
+    const double q = std::ceil(R0 * k_max / 8.0);
+    return q < 1.0 ? 1 : (int)q;
 }
 
 template <typename T>
@@ -55,6 +78,19 @@ template <>
 __device__ __forceinline__ float ylm_norm<float>(int l, int m) { return c_ylm_norm_f[l][m]; }
 template <>
 __device__ __forceinline__ double ylm_norm<double>(int l, int m) { return c_ylm_norm_d[l][m]; }
+
+template <typename T>
+__device__ __forceinline__ T leg_a(int m);
+template <>
+__device__ __forceinline__ float leg_a<float>(int m) { return c_leg_f[0][m]; }
+template <>
+__device__ __forceinline__ double leg_a<double>(int m) { return c_leg_d[0][m]; }
+template <typename T>
+__device__ __forceinline__ T leg_b(int m);
+template <>
+__device__ __forceinline__ float leg_b<float>(int m) { return c_leg_f[1][m]; }
+template <>
+__device__ __forceinline__ double leg_b<double>(int m) { return c_leg_d[1][m]; }
 
 // Real harmonics R_lm(u) for l <= 4 at unit vector (x, y, z), index l*l + l + m:
 // R_l0 = P_l(z); R_l,+m = n_lm Ptilde_l^m(z) Re (x + i y)^m; R_l,-m = same with Im,
@@ -94,26 +130,16 @@ __device__ __forceinline__ void hip_real_ylm(T x, T y, T z, T *R)
     }
 }
 
-#define HIP_BQ 8                        // neighbours per drain (one K = 8 MMA step)
-#define HIP_BPRIM 8                     // primaries per work item
-#define HIP_BQCAP (HIP_BQ + 32)         // queue capacity (a ballot adds up to 32)
-#define HIP_BWARPS 4
-#define HIP_BTHREADS (HIP_BWARPS * 32)
-#define HIP_NLM 25
-#define HIP_NLMP 28                     // 25 harmonics padded to a multiple of 4
+#define HIP_BK_WARPS 4
+#define HIP_BK_THREADS (HIP_BK_WARPS * 32)
+#define HIP_NLMP 28  // a drained pair's record: the 25 R_lm, r, w_j W, padding
 
-template <typename T, int NKMAX>
-struct BWarpSmem {
-    T qr[HIP_BQCAP], qw[HIP_BQCAP], qpsi[HIP_BQCAP];
-    alignas(16) T qy[HIP_BQCAP][HIP_NLMP];  // R_lm of each queued neighbour (row padded to 16 bytes)
-    union {
-        // jbar^a_l of each drained neighbour (C term); a fragment load reads
-        // J[q = 8 ks + t (+4)][col + g] for t = lane % 4, g = lane / 4, so the bank
-        // is (stride t + g) mod 32: a row stride = 8 (mod 32) makes the 32 lanes hit
-        // 32 different banks
-        T J[HIP_LMAX + 1][HIP_BQ][NKMAX + 8];
-        T X[NKMAX + 1][HIP_NLM];           // at the end of a primary: k_e^3 E_e, then A^a_lm
-    };
+template <typename T>
+struct BkWarpSmem {
+    alignas(16) T qa[64][4];            // accepted neighbours: primary minus neighbour, w_j
+    alignas(16) T qd[32][HIP_NLMP];     // drained pairs: R_lm (0..24), r (25), w_j W (26)
+    T pt[32][HIP_BK_NM + 1];            // C-term weight s_p w_j^2 W^2 times P_m(t), m < 32
+    int qc[32];                         // C-term interval of each drained pair
 };
 
 __global__ void k_sorted_cells(const int *__restrict__ start, int n_cells, int *__restrict__ scell)
@@ -147,190 +173,143 @@ __device__ __forceinline__ void hip_F_all(double u, double *F) { hip_F_f64<31>(u
 __device__ __forceinline__ float hip_arg(float r, float khi, float klo) { return fmaf(r, khi, r * klo); }
 __device__ __forceinline__ double hip_arg(double r, double khi, double) { return r * khi; }
 
-// Drain n queued neighbours of one primary: lanes over edges.  Accumulates the
-// edge sums E[t][lm] += w W F_l(r k_e) R_lm and stages jbar^a_l for the C term.
-template <typename T, int NCH, int NKMAX>
-__device__ __forceinline__ void hip_bdrain(BWarpSmem<T, NKMAX> &sm, int n, const T *kk, const T *kl, const T *k3,
-                                           const T *k3n, const T *jfac, int lane, int n_e, T (&E)[NCH][HIP_NLM])
+// The 28 entries of a drained pair's record into registers (vector loads).
+__device__ __forceinline__ void bk_load_rec(const float *src, float *dst)
 {
+#pragma unroll
+    for (int i = 0; i < HIP_NLMP / 4; ++i) {
+        const float4 v = reinterpret_cast<const float4 *>(src)[i];
+        dst[4 * i] = v.x;
+        dst[4 * i + 1] = v.y;
+        dst[4 * i + 2] = v.z;
+        dst[4 * i + 3] = v.w;
+    }
+}
+__device__ __forceinline__ void bk_load_rec(const double *src, double *dst)
+{
+#pragma unroll
+    for (int i = 0; i < HIP_NLMP / 2; ++i) {
+        const double2 v = reinterpret_cast<const double2 *>(src)[i];
+        dst[2 * i] = v.x;
+        dst[2 * i + 1] = v.y;
+    }
+}
+
+// Edge quantities of lane `lane` for chunk t (edge e = lane + 32 t).
+template <typename T, int NCH>
+struct BkEdges {
+    T kk[NCH], kl[NCH], k3[NCH], k3n[NCH], jfac[NCH];
+};
+
+template <typename T, int NCH>
+__device__ __forceinline__ void bk_load_edges(const BkCat<T> &a, int lane, BkEdges<T, NCH> &ed)
+{
+    const int n_e = a.n_e;
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+        const int e = lane + 32 * t;
+        ed.kk[t] = e < n_e ? a.k[e] : T(0);
+        ed.kl[t] = e < n_e ? a.klo[e] : T(0);
+        ed.k3[t] = e < n_e ? a.k3[e] : T(0);
+        ed.k3n[t] = e + 1 < n_e ? a.k3[e + 1] : T(0);
+        ed.jfac[t] = e + 1 < n_e ? a.jfac[e] : T(0);
+    }
+}
+
+// Process the first n (<= 32) queued neighbours of the current primary: their
+// geometry and harmonics (one per lane), their C-term moments (one lane per
+// moment) and their contributions to the edge sums (one lane per bin edge).
+template <typename T, int NCH>
+__device__ __forceinline__ void bk_flush(BkWarpSmem<T> &sm, T *cm, int n, T s_p, T invR0, T cc_scale, int n_cc,
+                                         int n_e, const BkEdges<T, NCH> &ed, int lane, T (&E)[NCH][HIP_NLM])
+{
+    if (lane < n) {
+        const T dx = sm.qa[lane][0], dy = sm.qa[lane][1], dz = sm.qa[lane][2], wj = sm.qa[lane][3];
+        const T r = hip_sqrt_b(dx * dx + dy * dy + dz * dz);
+        const T ir = T(1) / r;
+        const T W = hip_W<T>(r * invR0);
+        T R[HIP_NLM];
+        hip_real_ylm<T>(dx * ir, dy * ir, dz * ir, R);
+#pragma unroll
+        for (int i = 0; i < HIP_NLM; ++i) sm.qd[lane][i] = R[i];
+        sm.qd[lane][25] = r;
+        sm.qd[lane][26] = wj * W;
+        sm.qd[lane][27] = T(0);
+        // C term: interval c of width R0 / n_cc, coordinate t in [-1, 1]
+        const T x = r * cc_scale;
+        int c = (int)x;
+        if (c > n_cc - 1) c = n_cc - 1;
+        T t = T(2) * (x - T(c)) - T(1);
+        t = t < T(-1) ? T(-1) : (t > T(1) ? T(1) : t);
+        const T wc = s_p * wj * wj * W * W;
+        T p0 = wc, p1 = wc * t;
+        sm.pt[lane][0] = p0;
+        sm.pt[lane][1] = p1;
+#pragma unroll
+        for (int m = 1; m < HIP_BK_NM - 1; ++m) {
+            const T p2 = leg_a<T>(m) * t * p1 - leg_b<T>(m) * p0;
+            sm.pt[lane][m + 1] = p2;
+            p0 = p1;
+            p1 = p2;
+        }
+        sm.qc[lane] = c;
+    }
+    __syncwarp();
+    for (int q = 0; q < n; ++q) cm[sm.qc[q] * HIP_BK_NM + lane] += sm.pt[q][lane];
     for (int q = 0; q < n; ++q) {
-        const T r = sm.qr[q], ww = sm.qw[q];
-        T F[NCH][HIP_LMAX + 1];
+        T rec[HIP_NLMP];
+        bk_load_rec(sm.qd[q], rec);
+        const T r = rec[25], ww = rec[26];
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
-            hip_F_all(hip_arg(r, kk[t], kl[t]), F[t]);
+            T F[HIP_LMAX + 1];
+            hip_F_all(hip_arg(r, ed.kk[t], ed.kl[t]), F);
             if (lane + 32 * t < n_e) {
-                T y[HIP_NLMP];
-#pragma unroll
-                for (int i = 0; i < HIP_NLMP; ++i) y[i] = sm.qy[q][i];
 #pragma unroll
                 for (int l = 0; l <= HIP_LMAX; ++l) {
-                    const T f = ww * F[t][l];
+                    const T f = ww * F[l];
 #pragma unroll
-                    for (int m = -l; m <= l; ++m) E[t][l * l + l + m] += f * y[l * l + l + m];
+                    for (int m = -l; m <= l; ++m) E[t][l * l + l + m] += f * rec[l * l + l + m];
                 }
             }
         }
-        // jbar^a_l = jfac_a (k_{a+1}^3 F_l(u_{a+1}) - k_a^3 F_l(u_a)), a = lane + 32 t
-#pragma unroll
-        for (int t = 0; t < NCH; ++t) {
-#pragma unroll
-            for (int l = 0; l <= HIP_LMAX; ++l) {
-                T nxt = __shfl_down_sync(0xffffffffu, F[t][l], 1);
-                const T wrap = __shfl_sync(0xffffffffu, F[(t + 1 < NCH) ? t + 1 : t][l], 0);
-                if (lane == 31 && t + 1 < NCH) nxt = wrap;
-                const int a = lane + 32 * t;
-                if (a < n_e - 1) sm.J[l][q][a] = jfac[t] * (k3n[t] * nxt - k3[t] * F[t][l]);
-            }
-        }
     }
+    __syncwarp();
 }
 
-// The CTA accumulator Tc holds, per l, the upper triangle a <= b of the
-// symmetric n_k x n_k matrix (both the C term and the contraction are symmetric
-// in a, b), row a starting at a nk - a (a - 1) / 2.
-__device__ __forceinline__ int hip_tri(int a, int b, int nk) { return a * nk - (a * (a - 1)) / 2 + (b - a); }
-
-// Tc[l][a<=b] -= s_p sum_q psi_q J[l][q][a] J[l][q][b]  (the C term).
-template <typename T, int NKMAX>
-__device__ __forceinline__ void hip_cterm(const BWarpSmem<T, NKMAX> &sm, int n, int nk, T sp, int lane, T *Tc)
-{
-    const int per_l = nk * nk, ntri = nk * (nk + 1) / 2;
-    for (int i = lane; i < (HIP_LMAX + 1) * per_l; i += 32) {
-        const int l = i / per_l, ab = i - l * per_l, a = ab / nk, b = ab - a * nk;
-        if (a > b) continue;
-        T acc = T(0);
-        for (int q = 0; q < n; ++q) acc += sm.qpsi[q] * sm.J[l][q][a] * sm.J[l][q][b];
-        atomicAdd(&Tc[l * ntri + hip_tri(a, b, nk)], -sp * acc);
-    }
-}
-
-// The C term on the tensor cores (FP32 path): for each l, the batch's
-// contribution C_l[a][b] = sum_q (psi_q J[l][q][a]) J[l][q][b] is a
-// [n_k x 16] x [16 x n_k] product, done with mma.sync m16n8k8 TF32 in three
-// products of the split x = hi + lo (hi*hi + hi*lo + lo*hi, FP32 accumulate),
-// which keeps ~FP32 accuracy; the 16 x 8 result tiles are added to the CTA
-// accumulator.  Fragment layouts of m16n8k8 (g = lane/4, t = lane%4):
-// A a0..a3 = (g, t), (g+8, t), (g, t+4), (g+8, t+4); B b0, b1 = (t, g), (t+4, g);
-// C c0..c3 = (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1).
-__device__ __forceinline__ unsigned hip_tf32(float x)
-{
-    unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void hip_mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-template <int NKMAX>
-__device__ __forceinline__ void hip_cterm_mma(const BWarpSmem<float, NKMAX> &sm, int n, int nk, float sp, int lane,
-                                              float *Tc)
-{
-    constexpr int MT = NKMAX / 16, NT = NKMAX / 8;  // row tiles of 16, column tiles of 8
-    const int g = lane >> 2, t = lane & 3;
-    float psi[HIP_BQ / 8][2];  // psi of the K columns this lane feeds into A: q = 8 ks + t (+4)
-#pragma unroll
-    for (int ks = 0; ks < HIP_BQ / 8; ++ks) {
-        const int q0 = 8 * ks + t, q1 = q0 + 4;
-        psi[ks][0] = q0 < n ? -sp * sm.qpsi[q0] : 0.f;
-        psi[ks][1] = q1 < n ? -sp * sm.qpsi[q1] : 0.f;
-    }
-#pragma unroll 1
-    for (int l = 0; l <= HIP_LMAX; ++l) {
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-            if (16 * mt >= nk) break;
-            float acc[NT][4];
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-            for (int ks = 0; ks < HIP_BQ / 8; ++ks) {
-                const int q0 = 8 * ks + t, q1 = q0 + 4;
-                const float x0 = q0 < n ? psi[ks][0] * sm.J[l][q0][16 * mt + g] : 0.f;
-                const float x1 = q0 < n ? psi[ks][0] * sm.J[l][q0][16 * mt + g + 8] : 0.f;
-                const float x2 = q1 < n ? psi[ks][1] * sm.J[l][q1][16 * mt + g] : 0.f;
-                const float x3 = q1 < n ? psi[ks][1] * sm.J[l][q1][16 * mt + g + 8] : 0.f;
-                unsigned ah[4] = {hip_tf32(x0), hip_tf32(x1), hip_tf32(x2), hip_tf32(x3)};
-                unsigned al[4] = {hip_tf32(x0 - __uint_as_float(ah[0])), hip_tf32(x1 - __uint_as_float(ah[1])),
-                                  hip_tf32(x2 - __uint_as_float(ah[2])), hip_tf32(x3 - __uint_as_float(ah[3]))};
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    if (8 * nt >= nk) break;
-                    if (8 * nt + 7 < 16 * mt) continue;  // below the diagonal: not needed
-                    const float y0 = q0 < n ? sm.J[l][q0][8 * nt + g] : 0.f;
-                    const float y1 = q1 < n ? sm.J[l][q1][8 * nt + g] : 0.f;
-                    unsigned bh[2] = {hip_tf32(y0), hip_tf32(y1)};
-                    unsigned bl[2] = {hip_tf32(y0 - __uint_as_float(bh[0])), hip_tf32(y1 - __uint_as_float(bh[1]))};
-                    hip_mma_tf32(acc[nt], ah, bh);
-                    hip_mma_tf32(acc[nt], ah, bl);
-                    hip_mma_tf32(acc[nt], al, bh);
-                }
-            }
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                if (8 * nt >= nk) break;
-                if (8 * nt + 7 < 16 * mt) continue;  // tile entirely below the diagonal
-                const int r0 = 16 * mt + g, r1 = r0 + 8, c0 = 8 * nt + 2 * t, c1 = c0 + 1;
-                float *T = Tc + (size_t)l * (nk * (nk + 1) / 2);
-                if (c0 < nk && r0 <= c0) atomicAdd(&T[hip_tri(r0, c0, nk)], acc[nt][0]);
-                if (c1 < nk && r0 <= c1) atomicAdd(&T[hip_tri(r0, c1, nk)], acc[nt][1]);
-                if (c0 < nk && r1 <= c0) atomicAdd(&T[hip_tri(r1, c0, nk)], acc[nt][2]);
-                if (c1 < nk && r1 <= c1) atomicAdd(&T[hip_tri(r1, c1, nk)], acc[nt][3]);
-            }
-        }
-    }
-}
-
-template <typename T, int NKMAX>
-__device__ __forceinline__ void hip_cterm_any(const BWarpSmem<T, NKMAX> &sm, int n, int nk, T sp, int lane, T *Tc)
-{
-    if constexpr (sizeof(T) == 4)
-        hip_cterm_mma<NKMAX>(sm, n, nk, sp, lane, Tc);
-    else
-        hip_cterm<T, NKMAX>(sm, n, nk, sp, lane, Tc);
-}
-
-// One primary g (data first, then randoms) of the catalog described by a: the
-// 27-cell neighbour scan, the queued drains (edge sums, C term) and, at the end,
-// the contraction of its A^a_lm into the CTA accumulator Tc (upper triangle).
-template <typename T, int NCH, int NKMAX>
-__device__ __forceinline__ void hip_bispec_primary(const BispecArgs<T> &a, int g, BWarpSmem<T, NKMAX> &sm, T *Tc,
-                                                   const T (&kk)[NCH], const T (&kl)[NCH], const T (&k3)[NCH],
-                                                   const T (&k3n)[NCH], const T (&jfac)[NCH], int lane,
-                                                   unsigned long long &cnt_d, unsigned long long &cnt_r)
+// One primary g (data first, then randoms) of catalog a: the 27-cell neighbour
+// scan and the queued flushes; then A^a_lm = jfac_a (k_{a+1}^3 E_{a+1} - k_a^3 E_a)
+// into Xp[lm][a] and s_p into *spp.
+template <typename T, int NCH>
+__device__ __forceinline__ void bk_primary(const BkCat<T> &a, int g, BkWarpSmem<T> &sm, T *cm,
+                                           const BkEdges<T, NCH> &ed, int lane, T *Xp, T *spp,
+                                           unsigned long long &cnt_d, unsigned long long &cnt_r)
 {
     const int n_e = a.n_e, nk = n_e - 1, n_c = a.data.n_c;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const T R0sq = a.R0 * a.R0, invR0 = T(1) / a.R0;
-    const int ntri = nk * (nk + 1) / 2;
     const bool is_rand = g >= a.n_data;
     const CellList<T> &pl = is_rand ? a.rand : a.data;
     const int p = is_rand ? g - a.n_data : g;
+    const long long oi = pl.idx[p];
+    const bool excluded = is_rand ? (oi < a.rp0 || oi >= a.rp1) : (oi < a.dp0 || oi >= a.dp1);
+    const T s_p = excluded ? T(0) : (is_rand ? a.rand_weight : T(pl.w[p]));
+    if (lane == 0) *spp = s_p;
+    if (excluded) return;
+    const T R0sq = a.R0 * a.R0, invR0 = T(1) / a.R0, cc_scale = a.cc_scale;
+    const int n_cc = a.n_cc;
     const int c = is_rand ? a.rcell[p] : a.dcell[p];
     const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
     const T px = pl.x[p], py = pl.y[p], pz = pl.z[p];
-    const T sp = is_rand ? a.rand_weight : T(pl.w[p]);
     const int self = is_rand ? -1 : p;
-    {
-        const long long oi = pl.idx[p];
-        if (is_rand ? (oi < a.rp0 || oi >= a.rp1) : (oi < a.dp0 || oi >= a.dp1)) return;
-    }
     T E[NCH][HIP_NLM];
 #pragma unroll
     for (int t = 0; t < NCH; ++t)
 #pragma unroll
         for (int i = 0; i < HIP_NLM; ++i) E[t][i] = T(0);
     int qn = 0;
-    // cell shifts of this primary: lane 3 axis + d + 1 holds the shift
-    // of neighbour offset d along that axis (the shift's low part, below
-    // 1e-6 of the cell side, is under the FP32 B budget and dropped)
+    // cell shifts of this primary: lane 3 axis + d + 1 holds the shift of
+    // neighbour offset d along that axis (the shift's low part, below 1e-6 of the
+    // cell side, is under the FP32 budget of B and dropped)
     T shl = T(0);
     if (lane < 9) {
         const int ax = lane / 3, cc = ax == 0 ? cx : (ax == 1 ? cy : cz);
@@ -347,28 +326,21 @@ __device__ __forceinline__ void hip_bispec_primary(const BispecArgs<T> &a, int g
         for (int jb = b0; jb < b1; jb += 32) {
             const int j = jb + lane;
             bool ok = false;
-            T ddx = T(0), ddy = T(0), ddz = T(0), r2 = T(0);
+            T ddx = T(0), ddy = T(0), ddz = T(0);
             if (j < b1) {
                 ddx = ox - a.data.x[j];
                 ddy = oy - a.data.y[j];
                 ddz = oz - a.data.z[j];
-                r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
                 ok = (r2 < R0sq) && (r2 > T(0)) && (j != self);
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
             if (ok) {
-                const T r = hip_sqrt_b(r2);
-                const T ir = T(1) / r;
-                const T W = hip_W<T>(r * invR0);
-                const T wj = T(a.data.w[j]);
                 const int slot = qn + __popc(m & lt_mask);
-                T R[HIP_NLM];
-                hip_real_ylm<T>(ddx * ir, ddy * ir, ddz * ir, R);
-                sm.qr[slot] = r;
-                sm.qw[slot] = wj * W;
-                sm.qpsi[slot] = wj * wj * W * W;
-#pragma unroll
-                for (int i = 0; i < HIP_NLM; ++i) sm.qy[slot][i] = R[i];
+                sm.qa[slot][0] = ddx;
+                sm.qa[slot][1] = ddy;
+                sm.qa[slot][2] = ddz;
+                sm.qa[slot][3] = T(a.data.w[j]);
             }
             const int nq = __popc(m);
             if (is_rand)
@@ -376,29 +348,19 @@ __device__ __forceinline__ void hip_bispec_primary(const BispecArgs<T> &a, int g
             else
                 cnt_d += nq;
             qn += nq;
-            while (qn >= HIP_BQ) {
-                // drain the first HIP_BQ entries, move the rest (< 32) down
+            if (qn >= 32) {
                 __syncwarp();
-                hip_bdrain<T, NCH, NKMAX>(sm, HIP_BQ, kk, kl, k3, k3n, jfac, lane, n_e, E);
-                __syncwarp();
-                hip_cterm_any<T, NKMAX>(sm, HIP_BQ, nk, sp, lane, Tc);
-                const int rest = qn - HIP_BQ;
-                T mv[3] = {T(0), T(0), T(0)};
+                bk_flush<T, NCH>(sm, cm, 32, s_p, invR0, cc_scale, n_cc, n_e, ed, lane, E);
+                const int rest = qn - 32;
+                T mv[4] = {T(0), T(0), T(0), T(0)};
                 if (lane < rest) {
-                    mv[0] = sm.qr[HIP_BQ + lane];
-                    mv[1] = sm.qw[HIP_BQ + lane];
-                    mv[2] = sm.qpsi[HIP_BQ + lane];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mv[k] = sm.qa[32 + lane][k];
                 }
-                T my[HIP_NLM];
-#pragma unroll
-                for (int i = 0; i < HIP_NLM; ++i) my[i] = lane < rest ? sm.qy[HIP_BQ + lane][i] : T(0);
                 __syncwarp();
                 if (lane < rest) {
-                    sm.qr[lane] = mv[0];
-                    sm.qw[lane] = mv[1];
-                    sm.qpsi[lane] = mv[2];
 #pragma unroll
-                    for (int i = 0; i < HIP_NLM; ++i) sm.qy[lane][i] = my[i];
+                    for (int k = 0; k < 4; ++k) sm.qa[lane][k] = mv[k];
                 }
                 qn = rest;
                 __syncwarp();
@@ -407,242 +369,387 @@ __device__ __forceinline__ void hip_bispec_primary(const BispecArgs<T> &a, int g
     }
     if (qn > 0) {
         __syncwarp();
-        hip_bdrain<T, NCH, NKMAX>(sm, qn, kk, kl, k3, k3n, jfac, lane, n_e, E);
-        __syncwarp();
-        hip_cterm_any<T, NKMAX>(sm, qn, nk, sp, lane, Tc);
-        qn = 0;
+        bk_flush<T, NCH>(sm, cm, qn, s_p, invR0, cc_scale, n_cc, n_e, ed, lane, E);
     }
-    // edge sums -> A^a_lm = jfac_a (k_{a+1}^3 E_{a+1} - k_a^3 E_a)
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < NCH; ++t) {
-        const int e = lane + 32 * t;
-        if (e < n_e)
-#pragma unroll
-            for (int i = 0; i < HIP_NLM; ++i) sm.X[e][i] = k3[t] * E[t][i];
-    }
-    __syncwarp();
-    T Aa[NCH][HIP_NLM];
-#pragma unroll
-    for (int t = 0; t < NCH; ++t) {
-        const int e = lane + 32 * t;
-#pragma unroll
-        for (int i = 0; i < HIP_NLM; ++i) Aa[t][i] = e < nk ? jfac[t] * (sm.X[e + 1][i] - sm.X[e][i]) : T(0);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < NCH; ++t) {
-        const int e = lane + 32 * t;
-        if (e < nk)
-#pragma unroll
-            for (int i = 0; i < HIP_NLM; ++i) sm.X[e][i] = Aa[t][i];
-    }
-    __syncwarp();
-    // contraction: Tc[l][a<=b] += s_p sum_m A^a_lm A^b_lm  (lane owns rows a)
 #pragma unroll
     for (int t = 0; t < NCH; ++t) {
         const int aa = lane + 32 * t;
-        if (aa < nk) {
-            for (int b = aa; b < nk; ++b) {
 #pragma unroll
-                for (int l = 0; l <= HIP_LMAX; ++l) {
-                    T d = T(0);
-#pragma unroll
-                    for (int mm = -l; mm <= l; ++mm) d += Aa[t][l * l + l + mm] * sm.X[b][l * l + l + mm];
-                    atomicAdd(&Tc[l * ntri + hip_tri(aa, b, nk)], sp * d);
-                }
-            }
+        for (int i = 0; i < HIP_NLM; ++i) {
+            T nxt = __shfl_down_sync(0xffffffffu, E[t][i], 1);
+            const T wrap = __shfl_sync(0xffffffffu, E[(t + 1 < NCH) ? t + 1 : t][i], 0);
+            if (lane == 31 && t + 1 < NCH) nxt = wrap;
+            if (aa < nk) Xp[i * nk + aa] = ed.jfac[t] * (ed.k3n[t] * nxt - ed.k3[t] * E[t][i]);
         }
     }
+}
+
+template <typename T>
+size_t hip_bk_alm_smem_bytes(int ncc_max)
+{
+    return HIP_BK_WARPS * (sizeof(BkWarpSmem<T>) + sizeof(T) * (size_t)ncc_max * HIP_BK_NM);
+}
+
+// The a_lm pass: persistent CTAs of 4 warps; each warp takes work items (8
+// consecutive primaries of one span) from an atomic counter.  Per warp, the
+// C-term moments of the current catalog sit in an FP32 (FP64 on the plain path)
+// shared array, added to the warp's FP64 slot after every item and to the
+// catalog's moments when the warp leaves the catalog.
+template <typename T, int NCH>
+__global__ void __launch_bounds__(HIP_BK_THREADS) k_bk_alm(const BkCat<T> *__restrict__ cats,
+                                                           const BkSpan *__restrict__ spans, int n_spans, int n_items,
+                                                           int ncc_max, T *__restrict__ X, T *__restrict__ sp,
+                                                           double *__restrict__ cm_slots, int *counter)
+{
+    extern __shared__ __align__(16) unsigned char bk_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    BkWarpSmem<T> &sm = reinterpret_cast<BkWarpSmem<T> *>(bk_raw)[warp];
+    T *cm = reinterpret_cast<T *>(bk_raw + HIP_BK_WARPS * sizeof(BkWarpSmem<T>)) + (size_t)warp * ncc_max * HIP_BK_NM;
+    double *slot = cm_slots + ((size_t)blockIdx.x * HIP_BK_WARPS + warp) * ncc_max * HIP_BK_NM;
+    for (int i = lane; i < ncc_max * HIP_BK_NM; i += 32) cm[i] = T(0);
     __syncwarp();
-}
-
-template <typename T, int NCH, int NKMAX>
-__global__ void __launch_bounds__(HIP_BTHREADS) k_bispec(BispecArgs<T> a)
-{
-    __shared__ BWarpSmem<T, NKMAX> smem[HIP_BWARPS];
-    extern __shared__ __align__(16) unsigned char tc_raw[];
-    T *Tc = reinterpret_cast<T *>(tc_raw);  // [5][nk][nk] CTA accumulator
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    BWarpSmem<T, NKMAX> &sm = smem[warp];
-    const int n_e = a.n_e, nk = n_e - 1;
-    const int ntri = nk * (nk + 1) / 2;
-    for (int i = threadIdx.x; i < (HIP_LMAX + 1) * ntri; i += HIP_BTHREADS) Tc[i] = T(0);
-    __syncthreads();
-
-    T kk[NCH], kl[NCH], k3[NCH], k3n[NCH], jfac[NCH];
-#pragma unroll
-    for (int t = 0; t < NCH; ++t) {
-        const int e = lane + 32 * t;
-        kk[t] = e < n_e ? a.k[e] : T(0);
-        kl[t] = e < n_e ? a.klo[e] : T(0);
-        k3[t] = e < n_e ? a.k3[e] : T(0);
-        k3n[t] = e + 1 < n_e ? a.k3[e + 1] : T(0);
-        jfac[t] = e + 1 < n_e ? a.jfac[e] : T(0);
-    }
+    BkEdges<T, NCH> ed;
     unsigned long long cnt_d = 0, cnt_r = 0;
-    const int n_prim = a.n_data + a.n_rand;
-    const int n_items = (n_prim + HIP_BPRIM - 1) / HIP_BPRIM;
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(a.work_counter, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= n_items) break;
-        const int g0 = item * HIP_BPRIM, g1 = min(g0 + HIP_BPRIM, n_prim);
-        for (int g = g0; g < g1; ++g)
-            hip_bispec_primary<T, NCH, NKMAX>(a, g, sm, Tc, kk, kl, k3, k3n, jfac, lane, cnt_d, cnt_r);
-    }
-    __syncthreads();
-    double *out = a.partials + (size_t)blockIdx.x * (HIP_LMAX + 1) * nk * nk;
-    for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) {
-        const int l = i / (nk * nk), ab = i - l * nk * nk, x = ab / nk, y = ab - x * nk;
-        out[i] = (double)Tc[l * ntri + (x <= y ? hip_tri(x, y, nk) : hip_tri(y, x, nk))];
-    }
-    // cnt_d, cnt_r are warp-uniform (every lane added each ballot's count)
-    if (lane == 0) {
-        if (cnt_d) atomicAdd(a.npairs, cnt_d);
-        if (cnt_r) atomicAdd(a.npairs + 1, cnt_r);
-    }
-}
-
-// Many catalogs in one persistent launch: CTA work items of HIP_BCTA_PRIM
-// primaries (8 per warp) of one catalog, the catalogs' items laid end to end.
-// All warps of a CTA work on the same catalog, so the CTA accumulator Tc serves
-// one catalog at a time: when the CTA moves to another catalog it adds Tc to the
-// previous catalog's FP64 sums (FP64 atomics), clears it and loads the new
-// catalog's edges.
-template <typename T, int NCH, int NKMAX>
-__global__ void __launch_bounds__(HIP_BTHREADS)
-    k_bispec_batched(const BispecCat<T> *__restrict__ cats, int n_cats, int n_items, int *counter)
-{
-    __shared__ BWarpSmem<T, NKMAX> smem[HIP_BWARPS];
-    __shared__ int s_item;
-    extern __shared__ __align__(16) unsigned char tc_raw[];
-    T *Tc = reinterpret_cast<T *>(tc_raw);  // [5][upper triangle of n_k x n_k]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    BWarpSmem<T, NKMAX> &sm = smem[warp];
-    T kk[NCH], kl[NCH], k3[NCH], k3n[NCH], jfac[NCH];
-    unsigned long long cnt_d = 0, cnt_r = 0;
-    int cur = -1;
+    int cur = -1, si = 0;
     auto leave = [&](int c) {
-        __syncthreads();
-        const int nk = cats[c].a.n_e - 1, ntri = nk * (nk + 1) / 2;
-        double *acc = cats[c].acc;
-        for (int i = threadIdx.x; i < (HIP_LMAX + 1) * nk * nk; i += HIP_BTHREADS) {
-            const int l = i / (nk * nk), ab = i - l * nk * nk, x = ab / nk, y = ab - x * nk;
-            const T v = Tc[l * ntri + (x <= y ? hip_tri(x, y, nk) : hip_tri(y, x, nk))];
-            if (v != T(0)) atomicAdd(&acc[i], (double)v);
+        const BkCat<T> &a = cats[c];
+        for (int i = lane; i < a.n_cc * HIP_BK_NM; i += 32) {
+            const double v = slot[i];
+            if (v != 0.0) {
+                atomicAdd(&a.cmom[i], v);
+                slot[i] = 0.0;
+            }
         }
         if (lane == 0) {  // cnt_d, cnt_r are warp-uniform
-            if (cnt_d) atomicAdd(cats[c].a.npairs, cnt_d);
-            if (cnt_r) atomicAdd(cats[c].a.npairs + 1, cnt_r);
+            if (cnt_d) atomicAdd(a.npairs, cnt_d);
+            if (cnt_r) atomicAdd(a.npairs + 1, cnt_r);
         }
         cnt_d = cnt_r = 0;
-        __syncthreads();
     };
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        int c = cur < 0 ? 0 : cur;
-        while (item >= cats[c].item_end) ++c;
-        while (item < cats[c].item_begin) --c;
-        if (c != cur) {
+        while (si + 1 < n_spans && item >= spans[si].item_end) ++si;
+        while (si > 0 && item < spans[si].item_begin) --si;
+        const BkSpan sp_ = spans[si];
+        if (sp_.cat != cur) {
             if (cur >= 0) leave(cur);
-            cur = c;
-            const BispecArgs<T> &a = cats[c].a;
-            const int n_e = a.n_e, nk = n_e - 1, ntri = nk * (nk + 1) / 2;
-            for (int i = threadIdx.x; i < (HIP_LMAX + 1) * ntri; i += HIP_BTHREADS) Tc[i] = T(0);
-#pragma unroll
-            for (int t = 0; t < NCH; ++t) {
-                const int e = lane + 32 * t;
-                kk[t] = e < n_e ? a.k[e] : T(0);
-                kl[t] = e < n_e ? a.klo[e] : T(0);
-                k3[t] = e < n_e ? a.k3[e] : T(0);
-                k3n[t] = e + 1 < n_e ? a.k3[e + 1] : T(0);
-                jfac[t] = e + 1 < n_e ? a.jfac[e] : T(0);
-            }
-            __syncthreads();
+            cur = sp_.cat;
+            bk_load_edges<T, NCH>(cats[cur], lane, ed);
         }
-        const BispecArgs<T> &a = cats[c].a;
-        const int n_prim = a.n_data + a.n_rand;
-        const int g0 = (item - cats[c].item_begin) * HIP_BCTA_PRIM + warp * HIP_BPRIM;
-        const int g1 = min(g0 + HIP_BPRIM, n_prim);
-        for (int g = g0; g < g1; ++g)
-            hip_bispec_primary<T, NCH, NKMAX>(a, g, sm, Tc, kk, kl, k3, k3n, jfac, lane, cnt_d, cnt_r);
+        const BkCat<T> &a = cats[cur];
+        const int nk = a.n_e - 1;
+        const int g0 = sp_.g0 + (item - sp_.item_begin) * HIP_BK_PRIM;
+        const int g1 = min(g0 + HIP_BK_PRIM, sp_.g1);
+        for (int g = g0; g < g1; ++g) {
+            const long long o = g - sp_.g0;
+            bk_primary<T, NCH>(a, g, sm, cm, ed, lane, X + sp_.x_off + o * HIP_NLM * nk, sp + sp_.sp_off + o, cnt_d,
+                               cnt_r);
+        }
+        __syncwarp();
+        // the item's C-term moments into the warp's FP64 slot
+        for (int i = lane; i < a.n_cc * HIP_BK_NM; i += 32) {
+            const T v = cm[i];
+            if (v != T(0)) {
+                slot[i] += (double)v;
+                cm[i] = T(0);
+            }
+        }
+        __syncwarp();
     }
     if (cur >= 0) leave(cur);
 }
 
-template <typename T, int NCH, int NKMAX>
-static cudaError_t launch_bispec_batched(const BispecCat<T> *cats, int n_cats, int n_items, int nk_max, int *counter,
-                                         int *grid_out, cudaStream_t st)
+template <typename T>
+size_t hip_bk_alm_slot_bytes(int ncc_max)
 {
-    const size_t dyn = sizeof(T) * (HIP_LMAX + 1) * (nk_max * (nk_max + 1) / 2);
-    cudaError_t e = cudaFuncSetAttribute(k_bispec_batched<T, NCH, NKMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dyn);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // at most 16 CTAs per SM (the shared memory of a CTA is > 14 KB)
+    return sizeof(double) * (size_t)sms * 16 * HIP_BK_WARPS * ncc_max * HIP_BK_NM;
+}
+
+template <typename T, int NCH>
+static cudaError_t launch_bk_alm(const BkCat<T> *cats, const BkSpan *spans, int n_spans, int n_items, int ncc_max,
+                                 T *X, T *sp, double *cm_slots, int *counter, cudaStream_t st)
+{
+    const size_t smem = hip_bk_alm_smem_bytes<T>(ncc_max);
+    cudaError_t e = cudaFuncSetAttribute(k_bk_alm<T, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, nb = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bispec_batched<T, NCH, NKMAX>, HIP_BTHREADS, dyn);
-    int grid = sms * (nb < 1 ? 1 : nb);
-    if (grid > n_items) grid = n_items < 1 ? 1 : n_items;
-    *grid_out = grid;
-    k_bispec_batched<T, NCH, NKMAX><<<grid, HIP_BTHREADS, dyn, st>>>(cats, n_cats, n_items, counter);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bk_alm<T, NCH>, HIP_BK_THREADS, smem);
+    if (nb < 1) nb = 1;
+    if (nb > 16) nb = 16;
+    int grid = sms * nb;
+    const int need = (n_items + HIP_BK_WARPS - 1) / HIP_BK_WARPS;
+    if (grid > need) grid = need < 1 ? 1 : need;
+    k_bk_alm<T, NCH><<<grid, HIP_BK_THREADS, smem, st>>>(cats, spans, n_spans, n_items, ncc_max, X, sp, cm_slots,
+                                                         counter);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t hip_bispec_pairs_batched(const BispecCat<T> *cats, int n_cats, int n_items, int nk_max, int *counter,
-                                     int *grid_out, cudaStream_t st)
+cudaError_t hip_bk_alm(const BkCat<T> *cats, const BkSpan *spans, int n_spans, int n_items, int nk_max, int ncc_max,
+                       T *X, T *sp, double *cm_slots, int *counter, cudaStream_t st)
 {
-    if (nk_max <= 31) return launch_bispec_batched<T, 1, 32>(cats, n_cats, n_items, nk_max, counter, grid_out, st);
+    if (nk_max <= 31) return launch_bk_alm<T, 1>(cats, spans, n_spans, n_items, ncc_max, X, sp, cm_slots, counter, st);
     if constexpr (sizeof(T) == 4) {
         if (nk_max <= 63)
-            return launch_bispec_batched<T, 2, 64>(cats, n_cats, n_items, nk_max, counter, grid_out, st);
+            return launch_bk_alm<T, 2>(cats, spans, n_spans, n_items, ncc_max, X, sp, cm_slots, counter, st);
     }
     return cudaErrorInvalidValue;
 }
-template cudaError_t hip_bispec_pairs_batched<float>(const BispecCat<float> *, int, int, int, int *, int *,
-                                                     cudaStream_t);
-template cudaError_t hip_bispec_pairs_batched<double>(const BispecCat<double> *, int, int, int, int *, int *,
-                                                      cudaStream_t);
+template size_t hip_bk_alm_slot_bytes<float>(int);
+template size_t hip_bk_alm_slot_bytes<double>(int);
+template cudaError_t hip_bk_alm<float>(const BkCat<float> *, const BkSpan *, int, int, int, int, float *, float *,
+                                       double *, int *, cudaStream_t);
+template cudaError_t hip_bk_alm<double>(const BkCat<double> *, const BkSpan *, int, int, int, int, double *, double *,
+                                        double *, int *, cudaStream_t);
 
-template <typename T, int NCH, int NKMAX>
-static cudaError_t launch_bispec(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st)
+// ------------------------------------------------------- FP64 contraction ----
+// sum_p s_p sum_m X_p[lm][a] X_p[lm][b] for a <= b (plain path): CTAs of 256
+// threads take contiguous ranges of the segments' primaries (laid end to end),
+// stage four primaries' X in shared memory at a time, and keep up to
+// HIP_BK64_NE upper-triangle entries (l, a <= b) per thread in FP64 registers;
+// on leaving a segment they are added to its accumulator (both triangles).
+#define HIP_BK64_THREADS 256
+#define HIP_BK64_NE 40    // ceil(5 * 63 * 64 / 2 / 256): every upper-triangle entry up to 63 bins
+#define HIP_BK64_STAGE 4  // primaries staged per step
+
+template <typename T>
+__global__ void __launch_bounds__(HIP_BK64_THREADS) k_bk_contract_f64(const BkSeg *__restrict__ segs, int n_segs,
+                                                                     long long n_total)
 {
-    const int nk = a.n_e - 1;
-    const size_t dyn = sizeof(T) * (HIP_LMAX + 1) * (nk * (nk + 1) / 2);
-    cudaError_t e = cudaFuncSetAttribute(k_bispec<T, NCH, NKMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dyn);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, nb = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bispec<T, NCH, NKMAX>, HIP_BTHREADS, dyn);
-    int grid = sms * (nb < 1 ? 1 : nb);
-    if (grid > max_grid) grid = max_grid;
-    *grid_out = grid;
-    k_bispec<T, NCH, NKMAX><<<grid, HIP_BTHREADS, dyn, st>>>(a);
-    return cudaGetLastError();
+    extern __shared__ __align__(16) unsigned char c64_raw[];
+    double *xs = reinterpret_cast<double *>(c64_raw);  // [HIP_BK64_STAGE][25][n_k]
+    __shared__ double s_sp[HIP_BK64_STAGE];
+    const long long per = (n_total + gridDim.x - 1) / gridDim.x;
+    const long long q0 = blockIdx.x * per, q1 = min(q0 + per, n_total);
+    if (q0 >= q1) return;
+    // first segment of this CTA
+    int sg = 0;
+    long long base = 0;
+    while (sg < n_segs && base + segs[sg].n_p <= q0) base += segs[sg++].n_p;
+    double acc[HIP_BK64_NE];
+    int ent[HIP_BK64_NE];  // (l << 16) | (a << 8) | b, or -1
+    int cur_nk = -1;
+    auto setup = [&](int nk) {
+        const int ntri = nk * (nk + 1) / 2;
+#pragma unroll
+        for (int i = 0; i < HIP_BK64_NE; ++i) {
+            acc[i] = 0.0;
+            const int e = threadIdx.x + HIP_BK64_THREADS * i;
+            ent[i] = -1;
+            if (e < (HIP_LMAX + 1) * ntri) {
+                const int l = e / ntri;
+                int r = e - l * ntri, aa = 0;
+                while (r >= nk - aa) {
+                    r -= nk - aa;
+                    ++aa;
+                }
+                ent[i] = (l << 16) | (aa << 8) | (aa + r);
+            }
+        }
+        cur_nk = nk;
+    };
+    auto flush = [&](const BkSeg &s) {
+        const int nk = s.n_k;
+#pragma unroll
+        for (int i = 0; i < HIP_BK64_NE; ++i)
+            if (ent[i] >= 0 && acc[i] != 0.0) {
+                const int l = ent[i] >> 16, aa = (ent[i] >> 8) & 255, bb = ent[i] & 255;
+                atomicAdd(&s.acc[((size_t)l * nk + aa) * nk + bb], acc[i]);
+                if (aa != bb) atomicAdd(&s.acc[((size_t)l * nk + bb) * nk + aa], acc[i]);
+                acc[i] = 0.0;
+            }
+    };
+    long long q = q0;
+    while (q < q1 && sg < n_segs) {
+        const BkSeg s = segs[sg];
+        const int nk = s.n_k;
+        if (nk != cur_nk) setup(nk);
+        const long long s_end = min(q1, base + s.n_p);
+        const T *Xd = reinterpret_cast<const T *>(s.X);
+        const T *spd = reinterpret_cast<const T *>(s.sp);
+        while (q < s_end) {
+            const int np = (int)min((long long)HIP_BK64_STAGE, s_end - q);
+            const long long p0 = q - base;
+            __syncthreads();
+            for (int i = threadIdx.x; i < np * HIP_NLM * nk; i += HIP_BK64_THREADS)
+                xs[i] = (double)Xd[p0 * HIP_NLM * nk + i];
+            if (threadIdx.x < HIP_BK64_STAGE)
+                s_sp[threadIdx.x] = threadIdx.x < np ? (double)spd[p0 + threadIdx.x] : 0.0;
+            __syncthreads();
+            for (int pp = 0; pp < np; ++pp) {
+                const double spv = s_sp[pp];
+                if (spv == 0.0) continue;
+                const double *xp = xs + (size_t)pp * HIP_NLM * nk;
+#pragma unroll
+                for (int i = 0; i < HIP_BK64_NE; ++i) {
+                    if (ent[i] < 0) continue;
+                    const int l = ent[i] >> 16, aa = (ent[i] >> 8) & 255, bb = ent[i] & 255;
+                    double d = 0.0;
+                    for (int m = l * l; m <= l * l + 2 * l; ++m) d += xp[m * nk + aa] * xp[m * nk + bb];
+                    acc[i] += spv * d;
+                }
+            }
+            q += np;
+        }
+        flush(s);
+        if (q >= base + s.n_p) {
+            base += s.n_p;
+            ++sg;
+        }
+    }
 }
 
 template <typename T>
-cudaError_t hip_bispec_pairs(const BispecArgs<T> &a, int max_grid, int *grid_out, cudaStream_t st)
+cudaError_t hip_bk_contract_f64(const BkSeg *segs, int n_segs, long long n_p_total, int nk_max, cudaStream_t st)
 {
-    const int nk = a.n_e - 1;
-    if (nk <= 31) return launch_bispec<T, 1, 32>(a, max_grid, grid_out, st);
-    if constexpr (sizeof(T) == 4) {
-        if (nk <= 63) return launch_bispec<T, 2, 64>(a, max_grid, grid_out, st);
-    }
-    return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * HIP_BK64_STAGE * HIP_NLM * nk_max;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_bk_contract_f64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long grid = (long long)sms * 4;
+    if (grid > n_p_total / 16 + 1) grid = n_p_total / 16 + 1;
+    k_bk_contract_f64<T><<<(int)grid, HIP_BK64_THREADS, smem, st>>>(segs, n_segs, n_p_total);
+    return cudaGetLastError();
 }
-template cudaError_t hip_bispec_pairs<float>(const BispecArgs<float> &, int, int *, cudaStream_t);
-template cudaError_t hip_bispec_pairs<double>(const BispecArgs<double> &, int, int *, cudaStream_t);
+template cudaError_t hip_bk_contract_f64<float>(const BkSeg *, int, long long, int, cudaStream_t);
+template cudaError_t hip_bk_contract_f64<double>(const BkSeg *, int, long long, int, cudaStream_t);
 
+// ------------------------------------------------------------ the C term ----
+// sum_(p,j) s_p w_j^2 W^2 jbar^a_l(r) jbar^b_l(r) from the moments
+// M[c][m] = sum over pairs in interval c of s_p w_j^2 W^2 P_m(t): on each interval
+// the pair density in t is rho_c(t) = sum_m (2m+1)/2 M[c][m] P_m(t), so the sum is
+// sum_c int_{-1}^{1} rho_c(t) f(r_c(t)) dt, taken by 48-point Gauss-Legendre
+// (exact for the degree-31 rho times the band-limited f).  All FP64.
+#define HIP_BK_CQ 48
+
+static double s_cq_x[HIP_BK_CQ], s_cq_w[HIP_BK_CQ];
+static bool s_cq_ready = false;
+
+static void cq_nodes()
+{
+    if (s_cq_ready) return;
+    const int n = HIP_BK_CQ;
+    for (int i = 0; i < n; ++i) {
+        double x = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double dp = n * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        const double dp = n * (x * p1 - p0) / (x * x - 1.0);
+        s_cq_x[i] = x;
+        s_cq_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    s_cq_ready = true;
+}
+
+struct BkCQ {
+    double x[HIP_BK_CQ], w[HIP_BK_CQ];
+};
+
+size_t hip_bk_cterm_scratch_bytes(int n_cc, int n_k)
+{
+    const size_t nodes = (size_t)n_cc * HIP_BK_CQ;
+    return sizeof(double) * nodes * (1 + (HIP_LMAX + 1) * (size_t)n_k);
+}
+
+// Per node: its weight w_q rho_c(t_q) and jbar^a_l(r_q) for every l, a.
+__global__ void k_bk_cc_nodes(BkCTerm c, BkCQ q, double *__restrict__ wn, double *__restrict__ J)
+{
+    const int n_nodes = c.n_cc * HIP_BK_CQ, nk = c.n_e - 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += gridDim.x * blockDim.x) {
+        const int cc = i / HIP_BK_CQ, iq = i - cc * HIP_BK_CQ;
+        const double t = q.x[iq];
+        const double r = (cc + 0.5 * (1.0 + t)) * (c.R0 / c.n_cc);
+        double rho = 0.0, p0 = 1.0, p1 = t;
+        const double *M = c.cmom + (size_t)cc * HIP_BK_NM;
+        rho += 0.5 * M[0] * p0 + 1.5 * M[1] * p1;
+        for (int m = 1; m < HIP_BK_NM - 1; ++m) {
+            const double p2 = ((2.0 * m + 1.0) * t * p1 - m * p0) / (m + 1.0);
+            rho += (m + 1.5) * M[m + 1] * p2;
+            p0 = p1;
+            p1 = p2;
+        }
+        wn[i] = q.w[iq] * rho;
+        // jbar^a_l(r) = 3 [k_{a+1}^3 F_l(r k_{a+1}) - k_a^3 F_l(r k_a)] / (k_{a+1}^3 - k_a^3)
+        double Fp[HIP_LMAX + 1];
+        hip_F_f64<31>(r * c.k[0], c_coeffs, Fp);
+        double k3p = c.k[0] * c.k[0] * c.k[0];
+        for (int a = 0; a < nk; ++a) {
+            double Fn[HIP_LMAX + 1];
+            hip_F_f64<31>(r * c.k[a + 1], c_coeffs, Fn);
+            const double k3n = c.k[a + 1] * c.k[a + 1] * c.k[a + 1];
+            const double jf = 3.0 / (k3n - k3p);
+            for (int l = 0; l <= HIP_LMAX; ++l) {
+                J[((size_t)l * nk + a) * n_nodes + i] = jf * (k3n * Fn[l] - k3p * Fp[l]);
+                Fp[l] = Fn[l];
+            }
+            k3p = k3n;
+        }
+    }
+}
+
+// acc[l][a][b] -= sum_q wn[q] J[l][a][q] J[l][b][q]: one warp per (l, a, b).
+__global__ void k_bk_cc_contract(BkCTerm c, const double *__restrict__ wn, const double *__restrict__ J)
+{
+    const int nk = c.n_e - 1, n_nodes = c.n_cc * HIP_BK_CQ;
+    const int lane = threadIdx.x & 31;
+    const int n_out = (HIP_LMAX + 1) * nk * nk;
+    for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n_out; o += (gridDim.x * blockDim.x) >> 5) {
+        const int l = o / (nk * nk), ab = o - l * nk * nk, a = ab / nk, b = ab - a * nk;
+        const double *Ja = J + ((size_t)l * nk + a) * n_nodes, *Jb = J + ((size_t)l * nk + b) * n_nodes;
+        double s = 0.0;
+        for (int i = lane; i < n_nodes; i += 32) s += wn[i] * Ja[i] * Jb[i];
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) c.acc[o] -= s;
+    }
+}
+
+cudaError_t hip_bk_cterm(const BkCTerm &c, void *scratch, cudaStream_t st)
+{
+    cq_nodes();
+    BkCQ q;
+    for (int i = 0; i < HIP_BK_CQ; ++i) {
+        q.x[i] = s_cq_x[i];
+        q.w[i] = s_cq_w[i];
+    }
+    const int n_nodes = c.n_cc * HIP_BK_CQ, nk = c.n_e - 1;
+    double *wn = reinterpret_cast<double *>(scratch);
+    double *J = wn + n_nodes;
+    k_bk_cc_nodes<<<(n_nodes + 127) / 128, 128, 0, st>>>(c, q, wn, J);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int n_out = (HIP_LMAX + 1) * nk * nk;
+    k_bk_cc_contract<<<(n_out + 7) / 8, 256, 0, st>>>(c, wn, J);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- finalize -----
 // B^ab_l = (-1)^l (2l+1) T^ab_l / (V n_w^3)
 //          - delta_l0 (W~^a S^b + W~^b S^a) / (V n_w^2) + 2 delta_l0 W~^a W~^b   (Sec. 4.5)
 __global__ void k_bispec_final(const double *__restrict__ partials, int nparts, int nk, int lmax, double L,

@@ -98,7 +98,7 @@ extern "C" hip_status hip_power_noalloc(const float *pos, const float *w, int64_
     if (cv.total > HIP_NOALLOC_BYTES) {
         std::snprintf(g_noalloc_msg, sizeof(g_noalloc_msg),
                       "hip_power_noalloc: this call needs %zu bytes of scratch, the static array holds %zu "
-                      "(about 40 bytes per particle for host inputs, 24 for device inputs)",
+                      "(about 24 bytes per particle for device inputs, 36 for host positions, 40 with host weights)",
                       cv.total, (size_t)HIP_NOALLOC_BYTES);
         return HIP_ERR_RANGE;
     }

@@ -4,6 +4,8 @@ primaries) against the FP64 oracle and against single-catalog calls."""
 import numpy as np
 import pytest
 
+import parity_metrics
+
 import oracle
 from paper_2005_01739_gb300 import binding, catalogs
 
@@ -20,10 +22,9 @@ def _cuda():
     binding.load()
 
 
-def _err(P, Pref):
-    floor = 1e-2 * np.max(np.abs(Pref[0]))
-    scale = np.maximum(np.maximum(np.abs(Pref), np.abs(Pref[0])[None, :]), floor)
-    return float(np.max(np.abs(P - Pref) / scale))
+def _err(P, Pref, what=""):
+    # the asserted metric and its two companions are printed (run with -s)
+    return parity_metrics.report("P", P, Pref, what)["floored"]
 
 
 def _batch(device):

@@ -12,6 +12,8 @@ Tolerances: plain FP64 path 1e-10, mixed path 1e-4.
 import numpy as np
 import pytest
 
+import parity_metrics
+
 import oracle
 from paper_2005_01739_gb300 import binding, catalogs
 
@@ -35,10 +37,9 @@ def _dev(a):
     return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _err(B, Bref):
-    floor = 1e-2 * np.max(np.abs(Bref), axis=(1, 2))[:, None, None]
-    scale = np.maximum(np.maximum(np.abs(Bref), np.abs(Bref[0])[None]), floor)
-    return float(np.max(np.abs(B - Bref) / scale))
+def _err(B, Bref, what=""):
+    # the asserted metric and its two companions are printed (run with -s)
+    return parity_metrics.report("B", B, Bref, what)["floored"]
 
 
 _cache = {}
@@ -86,6 +87,49 @@ def test_bispectrum_parity_two_chunks():
     Bref, _ = _oracle_B("chunks", pos, w, rnd, L, R0, edges, lmax=2)
     B, _ = binding.hip_bispectrum(_dev(pos), None, _dev(rnd), L, R0, edges, 2, "mixed")
     assert _err(B, Bref) < TOL["mixed"]
+
+
+def test_bispectrum_sixty_bins():
+    # 60 bins: 61 edges (two 32-edge chunks per lane in the a_lm pass) and three
+    # 128-row tiles of (l, a) rows in the tensor-core contraction
+    pos, w, rnd, L, R0 = _case(seed=55, N=500)
+    edges = catalogs.linear_edges(0.3, 6.3, 60)
+    Bref, _ = _oracle_B("sixty", pos, w, rnd, L, R0, edges, lmax=4)
+    B, _ = binding.hip_bispectrum(_dev(pos), None, _dev(rnd), L, R0, edges, 4, "mixed")
+    assert _err(B, Bref) < TOL["mixed"]
+
+
+def test_bispectrum_one_cta_many_primaries():
+    # a single contraction CTA takes all 3000 data and 9000 random primaries: the
+    # FP32 accumulators in tensor memory are folded into FP64 every 64 primaries,
+    # so the error must not grow with the number of primaries a CTA accumulates
+    pos, w, rnd, L, R0 = _case(seed=51, N=3000)
+    edges = catalogs.linear_edges(0.3, 2.4, 12)
+    Bref, _ = _oracle_B("one_cta", pos, w, rnd, L, R0, edges)
+    binding.debug_bk_caps(tc_grid_cap=1)
+    try:
+        B, _ = binding.hip_bispectrum(_dev(pos), None, _dev(rnd), L, R0, edges, 4, "mixed")
+    finally:
+        binding.debug_bk_caps(0, 0)
+    assert _err(B, Bref) < TOL["mixed"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_bispectrum_chunks_and_both_signs(prec):
+    # the primaries pass in chunks of 1000 (several a_lm / contraction launches),
+    # and every seventh data weight is negative, so tensor-core stages hold
+    # primaries of both signs (issued once per sign)
+    pos, w, rnd, L, R0 = _case(seed=53, N=1000, weights="u05_15")
+    w = w.copy()
+    w[::7] = -0.4
+    edges = catalogs.linear_edges(0.3, 2.4, 12)
+    Bref, _ = _oracle_B("signs", pos, w, rnd, L, R0, edges)
+    binding.debug_bk_caps(chunk_cap=1000)
+    try:
+        B, _ = binding.hip_bispectrum(_dev(pos), _dev(w), _dev(rnd), L, R0, edges, 4, prec)
+    finally:
+        binding.debug_bk_caps(0, 0)
+    assert _err(B, Bref) < TOL[prec]
 
 
 def test_bispectrum_symmetric_and_translation_invariant():

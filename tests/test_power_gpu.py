@@ -15,6 +15,8 @@ Tolerances: plain FP64 path 1e-10 (summation order only), mixed path 1e-5.
 import numpy as np
 import pytest
 
+import parity_metrics
+
 import oracle
 from paper_2005_01739_gb300 import binding, catalogs
 
@@ -38,8 +40,9 @@ def _scale(Pref):
     return np.maximum(np.maximum(np.abs(Pref), np.abs(Pref[0])[None, :]), floor)
 
 
-def _err(P, Pref):
-    return float(np.max(np.abs(P - Pref) / _scale(Pref)))
+def _err(P, Pref, what=""):
+    # the asserted metric and its two companions are printed (run with -s)
+    return parity_metrics.report("P", P, Pref, what)["floored"]
 
 
 def _same_count(prec, n, nref):
