@@ -106,6 +106,8 @@ def load(path: str | None = None):
         L.hip_debug_F.argtypes = [i, i, d]
         L.hip_debug_D.restype = d
         L.hip_debug_D.argtypes = [i, i, d]
+        L.hip_debug_Fb.restype = d
+        L.hip_debug_Fb.argtypes = [i, d]
         L.hip_debug_F_array.restype = None
         L.hip_debug_F_array.argtypes = [i, i, P, P, i64]
         L.hip_debug_bk_caps.restype = None
@@ -425,6 +427,12 @@ def debug_D(variant: str, l: int, u: float) -> float:
     (closed form, asymptotic auxiliaries).  sin u and cos u are passed in correctly
     rounded, so the result isolates the D-form arithmetic."""
     return load().hip_debug_D({"series": 0, "fit": 1, "asym": 2}[variant], int(l), float(u))
+
+
+def debug_Fb(l: int, u: float) -> float:
+    """F_l(u) = D_l(u)/u^3 as the bispectrum's FP32 a_lm pass evaluates it (host
+    build of the same source)."""
+    return load().hip_debug_Fb(int(l), float(u))
 
 
 def debug_bk_caps(tc_grid_cap: int = 0, chunk_cap: int = 0) -> None:

@@ -1150,6 +1150,15 @@ extern "C" double hip_debug_D(int variant, int l, double u)
     return (double)D[l];
 }
 
+// F_l(u) as the bispectrum's FP32 a_lm pass evaluates it (host build of the same code).
+extern "C" double hip_debug_Fb(int l, double u)
+{
+    if (l < 0 || l > HIP_LMAX) return NAN;
+    float F[5] = {0, 0, 0, 0, 0};
+    hip_F_b32((float)u, hip_host_coeffs(), F);
+    return (double)F[l];
+}
+
 // Vector form of hip_debug_F: out[i] = F_l(u[i]).
 extern "C" void hip_debug_F_array(int prec, int l, const double *u, double *out, int64_t n)
 {

@@ -159,15 +159,7 @@ __device__ __forceinline__ float hip_sqrt_b(float v) { return sqrtf(v); }
 __device__ __forceinline__ double hip_sqrt_b(double v) { return sqrt(v); }
 
 // F_l(u), l = 0..4, as one number per l.
-__device__ __forceinline__ void hip_F_all(float u, float *F)
-{
-    float Fm[5], Fc[5];
-    bool series;
-    hip_F_f32<31>(u, c_coeffs, Fm, Fc, series);
-#pragma unroll
-    for (int l = 0; l <= HIP_LMAX; ++l) F[l] = Fm[l] + Fc[l];
-    if (series) F[0] += c_coeffs.ser32[0][0];
-}
+__device__ __forceinline__ void hip_F_all(float u, float *F) { hip_F_b32(u, c_coeffs, F); }
 __device__ __forceinline__ void hip_F_all(double u, double *F) { hip_F_f64<31>(u, c_coeffs, F); }
 
 __device__ __forceinline__ float hip_arg(float r, float khi, float klo) { return fmaf(r, khi, r * klo); }

@@ -43,6 +43,12 @@
 
 #define HIP_LMAX 4
 
+// FP32 edge functions of the bispectrum pass: a short polynomial below HIP_FB_U
+// and the closed forms above (see hip_F_b32)
+#define HIP_FB_U 4.0f          // polynomial below, closed form above
+#define HIP_FB_NPOLY 7         // terms of F_l(u)/u^l as a polynomial in x = u^2 on [0, 16]
+#define HIP_FB_SIDEG 10        // degree of the u f(u), u^2 g(u) fits in t = (4/u)^2
+
 // The FP32 series coefficients are stored as unevaluated sums hi + lo of two
 // floats; the lo halves are evaluated by a second, shorter Horner chain whose
 // result is accumulated separately (see hip_F_f32).  Rounding a coefficient to a
@@ -61,6 +67,11 @@ struct HipCoeffs {
     double sig64[HIP_F64_SIDEG + 1];
     // Si(u) / u = sum_n a_n x^n (FP64 middle range)
     double siser64[HIP_F64_NSISER];
+    // bispectrum pass: F_l(u)/u^l on u < 4 as monomials in x = u^2 (Chebyshev
+    // interpolant of degree 6), and the f, g fits in t = (4/u)^2 for u >= 4
+    float fbpoly[HIP_LMAX + 1][HIP_FB_NPOLY];
+    float fbsif[HIP_FB_SIDEG + 1];
+    float fbsig[HIP_FB_SIDEG + 1];
 };
 
 #define HIP_HALF_PI_F 1.57079632679489661923f
@@ -249,6 +260,60 @@ __host__ __device__ __forceinline__ void hip_F_f32(float u, const HipCoeffs &C, 
     hip_F_f32_closed<MASK>(u, s, c, C, Fm);
 #pragma unroll
     for (int l = 0; l <= HIP_LMAX; ++l) Fc[l] = 0.0f;
+}
+
+// ------------------------------------------------- F_l (FP32, bispectrum) ---
+// F_l(u), l = 0..4, for the bispectrum's a_lm pass, where every lane of a warp
+// evaluates one bin edge of the same pair and the two branches below diverge
+// whenever some edges fall below the switch: the branches are kept short.
+//   u < 4:  F_l(u) = u^l p_l(u^2), p_l the degree-6 Chebyshev interpolant of
+//           F_l(u)/u^l on x in [0, 16] (made in FP64 at library load), evaluated
+//           by Horner in x: ~2e-7 relative in FP32;
+//   u >= 4: the closed forms with Si = pi/2 - f cos - g sin from degree-10 fits
+//           of u f(u), u^2 g(u) in t = (4/u)^2: ~1.5e-7 absolute in Si; the
+//           closed forms cancel by at most ~10x at u = 4 for l = 4.
+// Unlike hip_F_f32 (the power spectrum's direct pass, held to 1e-5 on sums of
+// 1e9 pairs) there is no low-order correction chain: the bispectrum's budget is
+// 1e-4.
+__host__ __device__ __forceinline__ void hip_F_b32(float u, const HipCoeffs &C, float *F)
+{
+    if (u < HIP_FB_U) {
+        const float x = u * u;
+        float ul = 1.0f;
+#pragma unroll
+        for (int l = 0; l <= HIP_LMAX; ++l) {
+            float acc = C.fbpoly[l][HIP_FB_NPOLY - 1];
+#pragma unroll
+            for (int q = HIP_FB_NPOLY - 2; q >= 0; --q) acc = fmaf(acc, x, C.fbpoly[l][q]);
+            F[l] = acc * ul;
+            ul *= u;
+        }
+        return;
+    }
+    float s, c;
+#ifdef __CUDA_ARCH__
+    sincosf(u, &s, &c);
+    const float w = __fdividef(1.0f, u);
+#else
+    s = sinf(u);
+    c = cosf(u);
+    const float w = 1.0f / u;
+#endif
+    const float w2 = w * w;
+    const float w3 = w2 * w;
+    const float t = 16.0f * w2;
+    float pf = C.fbsif[HIP_FB_SIDEG], pg = C.fbsig[HIP_FB_SIDEG];
+#pragma unroll
+    for (int q = HIP_FB_SIDEG - 1; q >= 0; --q) {
+        pf = fmaf(pf, t, C.fbsif[q]);
+        pg = fmaf(pg, t, C.fbsig[q]);
+    }
+    const float si = HIP_HALF_PI_F - fmaf(w, fmaf(pf, c, w * pg * s), -HIP_HALF_PI_F_LO);
+    F[0] = fmaf(w3, s, -w2 * c);
+    F[1] = fmaf(w3, 2.0f - 2.0f * c, -w2 * s);
+    F[2] = fmaf(w3, fmaf(3.0f, si, -4.0f * s), w2 * c);
+    F[3] = fmaf(w2, s, w3 * fmaf(7.0f, c, 8.0f - 15.0f * w * s));
+    F[4] = fmaf(w3, fmaf(fmaf(-52.5f, w2, 11.0f), s, 7.5f * si), w2 * fmaf(52.5f, w2, -1.0f) * c);
 }
 
 // Total F_l(u) of the FP32 path (host self-checks).

@@ -158,6 +158,32 @@ void hip_build_coeffs(HipCoeffs *C)
     for (int q = 0; q <= HIP_F32_SIDEG; ++q) C->sif32[q] = (float)m[q];
     fit(6.0, HIP_F32_SIDEG, 1, m);
     for (int q = 0; q <= HIP_F32_SIDEG; ++q) C->sig32[q] = (float)m[q];
+    fit(4.0, HIP_FB_SIDEG, 0, m);
+    for (int q = 0; q <= HIP_FB_SIDEG; ++q) C->fbsif[q] = (float)m[q];
+    fit(4.0, HIP_FB_SIDEG, 1, m);
+    for (int q = 0; q <= HIP_FB_SIDEG; ++q) C->fbsig[q] = (float)m[q];
+    // F_l(u)/u^l on x = u^2 in [0, 16]: Chebyshev interpolation of degree 6 of
+    // its Taylor series (40 terms, FP64), returned as monomials in x
+    for (int l = 0; l <= HIP_LMAX; ++l) {
+        cheb_fit_monomial(HIP_FB_NPOLY - 1, [&](double tt) {
+            const double x = 16.0 * tt;
+            double dfac = 1.0;
+            for (int k = 1; k <= 2 * l + 1; k += 2) dfac *= k;
+            double coef = 1.0 / dfac, xs = 1.0, sum = 0.0;
+            for (int q = 0; q < 40; ++q) {
+                sum += coef / (2.0 * q + l + 3.0) * xs;
+                coef *= -1.0 / (2.0 * (q + 1) * (2.0 * l + 2.0 * q + 3.0));
+                xs *= x;
+            }
+            return sum;
+        }, m);
+        // monomials in t = x / 16 -> monomials in x
+        double sc = 1.0;
+        for (int q = 0; q < HIP_FB_NPOLY; ++q) {
+            C->fbpoly[l][q] = (float)(m[q] * sc);
+            sc /= 16.0;
+        }
+    }
     fit(HIP_F64_USI, HIP_F64_SIDEG, 0, m);
     for (int q = 0; q <= HIP_F64_SIDEG; ++q) C->sif64[q] = m[q];
     fit(HIP_F64_USI, HIP_F64_SIDEG, 1, m);

@@ -99,6 +99,23 @@ def test_kernel_F_fp32_error_budget(lib, l):
 
 
 @pytest.mark.parametrize("l", [0, 1, 2, 3, 4])
+def test_kernel_F_bispectrum_error_budget(lib, l):
+    # The bispectrum pass's FP32 F_l: a degree-6 polynomial in u^2 below u = 4,
+    # closed forms with degree-10 Si auxiliaries above (host build of the same
+    # code), against the oracle's D_l.  Same envelope as the power path, with the
+    # bispectrum's looser constant (its tolerance is 1e-4, not 1e-5).
+    us = np.concatenate([np.geomspace(1e-4, 4, 80), np.linspace(4, 60, 200), np.linspace(60, 1500, 200)])
+    worst = 0.0
+    for u in us:
+        ref = oracle.dhat(l, u) / u ** 3
+        env = 1.0 / 3.0 if u < 1 else 1.0 / u ** 2
+        err = abs(binding.debug_Fb(l, u) - ref)
+        assert err < env * (2e-6 + 1.2e-7 * u), (l, u, err / env)
+        worst = max(worst, err / env / (1.0 + u))
+    assert worst > 0.0  # the FP32 path is not secretly exact
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("variant,lo,hi", [("series", 1e-4, 6.0), ("fit", 6.0, 3000.0), ("asym", 24.0, 3000.0)])
 def test_kernel_D_fp32_branches(lib, variant, lo, hi, l):
     # D_l(u) = u^3 F_l(u) as the FP32 pair kernels accumulate it, each branch on
