@@ -311,6 +311,15 @@ hip_status hip_subsample(const float *pos, const float *w, int64_t N, double fra
 void hip_set_profiling(int on);
 int hip_stage_times(double *ms, int n);
 
+/* Stage timing of the most recent bispectrum primary sum (hip_bispectrum,
+ * hip_bispectrum_partial, hip_bispectrum_analytic, hip_bispectrum_batched) with
+ * profiling on: ms[0] the a_lm pass (per-primary A^a_lm and the C-term moments
+ * of Eq. AC-def), ms[1] the contraction sum_p s_p sum_m A^a_lm A^b_lm (tensor
+ * cores on the mixed path), both summed over the call's chunks of primaries,
+ * ms[2] the C terms, ms[3] the number of chunks.  Writes min(n, 4) entries and
+ * returns that number (0 if profiling was off during the last such call). */
+int hip_bispectrum_stage_times(double *ms, int n);
+
 /* The pair pass hip_power uses for these arguments (k_max = k_edges[n_k]):
  *   0  direct: every bin edge's function k^3 F_l(r k) (App. C) evaluated per pair;
  *   1  Legendre moments: per separation interval of width R0/n_c,

@@ -114,6 +114,8 @@ def load(path: str | None = None):
         L.hip_debug_bk_caps.argtypes = [i, i]
         L.hip_debug_bk_mode.restype = None
         L.hip_debug_bk_mode.argtypes = [i, i]
+        L.hip_bispectrum_stage_times.restype = i
+        L.hip_bispectrum_stage_times.argtypes = [P, i]
         L.hip_set_profiling.restype = None
         L.hip_set_profiling.argtypes = [i]
         L.hip_stage_times.restype = i
@@ -467,6 +469,15 @@ def power_pair_pass(R0, k_max, prec="mixed"):
     if r < 0:
         raise ValueError("hip_power_pair_pass: invalid arguments")
     return r
+
+
+def bispectrum_stage_times():
+    """Stage times (ms) of the last bispectrum primary sum with profiling on:
+    the a_lm passes, the contractions, the C terms (summed over chunks), and the
+    number of chunks."""
+    out = np.zeros(4)
+    n = load().hip_bispectrum_stage_times(out.ctypes.data_as(ctypes.c_void_p), 4)
+    return out[:n]
 
 
 def stage_times():

@@ -351,6 +351,20 @@ static int g_bk_chunk_cap = 0;    // tests: caps the primaries per chunk (0 = by
 static int g_bk_fold = 0;         // tests: primaries between the contraction's FP64 folds (0 = default)
 static int g_bk_cores = 0;        // tests: contract FP32 accumulators on the CUDA cores in FP64
 
+// Stage timing of the last bispectrum primary sum (when profiling is on): the
+// a_lm passes, the contractions and the C terms, summed over chunks, in ms, and
+// the number of chunks.
+static double g_bk_ms[4];
+static bool g_bk_ms_valid = false;
+
+extern "C" int hip_bispectrum_stage_times(double *ms, int n)
+{
+    if (!g_bk_ms_valid || !ms) return 0;
+    const int m = n < 4 ? n : 4;
+    for (int i = 0; i < m; ++i) ms[i] = g_bk_ms[i];
+    return m;
+}
+
 struct BkPlan {
     int nc = 0, nk_max = 0, ncc_max = 0;
     long long chunk = 0;
@@ -427,6 +441,17 @@ static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCa
     HIP_CK(cudaMemsetAsync(cnt, 0, sizeof(int) * 4, st), "memset");
     HIP_CK(cudaMemcpyAsync(dcats, cats.data(), sizeof(BkCat<T>) * nc, cudaMemcpyHostToDevice, st), "H2D catalogs");
     const int P = hip_bk_tc_stage_prims(pl.nk_max);
+    // optional event pairs around the stages: [chunk][a_lm, contraction], then the C terms
+    std::vector<cudaEvent_t> evs;
+    auto mark = [&]() {
+        if (!g_prof) return;
+        cudaEvent_t ev;
+        cudaEventCreate(&ev);
+        cudaEventRecord(ev, st);
+        evs.push_back(ev);
+    };
+    g_bk_ms_valid = false;
+    int n_chunks = 0;
     // walk the catalogs' primaries end to end, one chunk at a time
     int ci = 0;
     long long gi = 0;  // next primary of catalog ci
@@ -474,15 +499,20 @@ static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCa
         HIP_CK(cudaMemcpyAsync(dsegs, segs.data(), sizeof(BkSeg) * segs.size(), cudaMemcpyHostToDevice, st),
                "H2D segments");
         HIP_CK(cudaMemsetAsync(cnt, 0, sizeof(int), st), "memset");
+        ++n_chunks;
+        mark();
         HIP_CK(hip_bk_alm<T>(dcats, dspans, (int)spans.size(), items, pl.nk_max, pl.ncc_max, X, sp, slots, cnt, st),
                "bispectrum a_lm pass");
+        mark();
         if (pl.tc && !g_bk_cores)
             HIP_CK(hip_bk_contract_tc(dsegs, (int)segs.size(), stages, pl.nk_max, cnt + 1, g_bk_tc_grid_cap, g_bk_fold,
                                       st),
                    "bispectrum contraction (tensor cores)");
         else
             HIP_CK(hip_bk_contract_f64<T>(dsegs, (int)segs.size(), used, pl.nk_max, st), "bispectrum contraction");
+        mark();
     }
+    mark();
     for (int i = 0; i < nc; ++i) {
         BkCTerm c;
         std::memset(&c, 0, sizeof(c));
@@ -496,8 +526,25 @@ static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCa
     }
     int status = 0;
     HIP_CK(cudaMemcpyAsync(&status, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H status");
+    mark();
     HIP_CK(cudaStreamSynchronize(st), "bispectrum sync");
 #undef HIP_CK
+    if (g_prof && (int)evs.size() == 3 * n_chunks + 2) {
+        for (double &v : g_bk_ms) v = 0.0;
+        for (int c = 0; c < n_chunks; ++c) {
+            float a = 0.f, k = 0.f;
+            cudaEventElapsedTime(&a, evs[3 * c], evs[3 * c + 1]);
+            cudaEventElapsedTime(&k, evs[3 * c + 1], evs[3 * c + 2]);
+            g_bk_ms[0] += a;
+            g_bk_ms[1] += k;
+        }
+        float ct = 0.f;
+        cudaEventElapsedTime(&ct, evs[3 * n_chunks], evs[3 * n_chunks + 1]);
+        g_bk_ms[2] = ct;
+        g_bk_ms[3] = n_chunks;
+        g_bk_ms_valid = true;
+    }
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
     if (status) {
         std::snprintf(g_errbuf, sizeof(g_errbuf), "bispectrum contraction: a bounded device wait gave up");
         return HIP_ERR_TIMEOUT;
