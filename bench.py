@@ -5,10 +5,17 @@ build, the FP32 pair pass (Legendre moments of the separation, with the FP64
 projection of the bin-edge functions and the FP64 contraction), FP64 finalize
 (W~^a, reduction, normalisation) and the download of P and DD.  Metric:
 unordered pairs with 0 < r < R0, times the number of k bins, per second
-(pairs x k-bins / s).  The same line also reports the plain FP64 path, the
-bispectrum (with and without randoms), the parity of both precisions against
-the oracle on a primary sample, the subsample selection, the clocks seen and
-the oracle's own rate on the host cores.
+(pairs x k-bins / s).  The same line also reports, each with its own event
+timing: the plain FP64 path on the same catalog; the bispectrum workload
+(5e5 particles, 1.5e6 randoms: rate, stage times, the rooflines of the a_lm
+pass and of the tensor-core contraction, parity of a primary sample against the
+oracle, and the random-free variant); the 64-catalog batch (graph replays of
+the mixed plan, the FP64 plan, their ratio and the mixed-vs-FP64 parity of
+every catalog, and B of 16 catalogs); the 5e4-particle plain configuration in
+both precisions with parity against the oracle; the parity of the timed
+workload on the oracle's sample (floored, unfloored and plain errors); the
+subsample selection, the clocks seen and the oracle's own rate on the host
+cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,13 +45,13 @@ UNIT = "pairs*kbins/s"
 WORKLOAD = "pk_mixed_n2e6"
 FLOPS_PER_PAIR_BIN = 12.0  # nominal algorithmic FP32 flops per (unordered pair, k bin)
 # DRAM bytes (read + write) of one pair-pass launch on the 2e6-particle workload: ncu measured
-# 5.16 MB for the moment pass (5.18 MB for the direct pass) on the same workload shrunk to 2.5e5
+# 5.46 MB for the moment pass (5.18 MB for the direct pass) on the same workload shrunk to 2.5e5
 # particles; the traffic is the particle data read once, so it scales with N: x 8.
-PAIR_KERNEL_DRAM_BYTES = {1: 5.16e6 * 8, 0: 5.18e6 * 8}
-PAIR_KERNEL_NAME = {1: "k_power_moments<float,21>", 0: "k_power_pairs<float,4,21>"}
-# kernels one hip_power call launches: cell build 3, pair pass (moments: coefficients, pairs, contraction)
-# 3 or 1, finalize 2
-PAIR_PASS_LAUNCHES = {1: 8, 0: 6}
+PAIR_KERNEL_DRAM_BYTES = {1: 5.46e6 * 8, 0: 5.18e6 * 8}
+PAIR_KERNEL_NAME = {1: "k_power_moments<float,21,8>", 0: "k_power_pairs<float,4,21>"}
+# kernels one FP32 hip_power call launches: cell build 3, pair pass (moments: coefficients, sum |w|,
+# pairs, contraction) 4 or 1, finalize 2
+PAIR_PASS_LAUNCHES = {1: 9, 0: 6}
 
 
 def _peaks():
@@ -183,20 +190,41 @@ def sample_parity(binding, dpos, dw, wl, cpu):
     ref = cpu["DD"]
     floor = 1e-2 * np.max(np.abs(ref[0]))
     scale = np.maximum(np.maximum(np.abs(ref), np.abs(ref[0])[None, :]), floor)
-    out = {}
+    out, unf = {}, {}
     for prec in ("mixed", "fp64"):
         _, DD, _ = binding.hip_power(dpos, dw, wl["L"], wl["R0"], wl["edges"], 4, 2, prec,
                                      prim_range=(0, cpu["primaries"]))
         out[prec] = [float(x) for x in np.max(np.abs(DD - ref) / scale, axis=1)]
+        unf[prec] = _pk_metrics(DD, ref)
     return {"metric": "max over k bins of |DD_l - DD_l,oracle| / max(|DD_l|, |DD_0|, 1e-2 max|DD_0|)",
             "ell": [0, 2, 4], "mixed_max_rel_err": out["mixed"], "fp64_max_rel_err": out["fp64"],
+            "mixed_all_metrics": unf["mixed"], "fp64_all_metrics": unf["fp64"],
+            "all_metrics_note": ("floored: the asserted metric; survey: the same without the 1e-2 max|DD_0| "
+                                 "floor; plain: |dDD| / |DD| per bin"),
             "tolerance": {"mixed": 1e-5, "fp64": 1e-10},
             "sample": f"the cpu_baseline sample: pair sums of the first {cpu['primaries']} primaries"}
 
 
-def bispectrum_rate(binding, stream, reps: int = 2, scale: float = 1.0):
+def _bk_metrics(B, Bref):
+    """Per-bin errors of the B parity: floored (the asserted metric of the tests),
+    the same without the floor, and the plain relative error."""
+    B, Bref = np.asarray(B, float), np.asarray(Bref, float)
+    d = np.abs(B - Bref)
+    scale = np.maximum(np.abs(Bref), np.abs(Bref[0])[None])
+    floor = 1e-2 * np.max(np.abs(Bref), axis=(1, 2))[:, None, None]
+    nz = scale > 0
+    plain = np.abs(Bref) > 0
+    return {"floored": float(np.max(d / np.maximum(scale, floor))),
+            "survey": float(np.max(d[nz] / scale[nz])) if np.any(nz) else 0.0,
+            "plain": float(np.max(d[plain] / np.abs(Bref[plain]))) if np.any(plain) else 0.0}
+
+
+def bispectrum_rate(binding, stream, reps: int = 2, scale: float = 1.0, parity: bool = True):
     """B_l (l = 0..4) of the 5e5-particle workload with 1.5e6 randoms: ordered
-    (primary, data) pairs, random primaries included, times bins, per second.
+    (primary, data) pairs, random primaries included, times bins, per second;
+    stage times, the rooflines of the a_lm pass and of the tensor-core
+    contraction, and the primary sums of a sample of data and random primaries
+    against the oracle (hip_bispectrum_partial vs oracle.bispectrum_primary_sum).
     `scale` < 1 shrinks the volume at fixed density (profiler captures only)."""
     import torch
     from paper_2005_01739_gb300 import catalogs
@@ -208,19 +236,63 @@ def bispectrum_rate(binding, stream, reps: int = 2, scale: float = 1.0):
     dpos = torch.from_numpy(wl["pos"]).cuda()
     drnd = torch.from_numpy(wl["rand"]).cuda()
     nk = len(wl["edges"]) - 1
+    binding.set_profiling(True)
     with torch.cuda.stream(stream):
         binding.hip_bispectrum(dpos, None, drnd, wl["L"], wl["R0"], wl["edges"], 4, "mixed", stream=stream)
-    ts = []
-    for _ in range(reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        with torch.cuda.stream(stream):
-            _, (nd, nr) = binding.hip_bispectrum(dpos, None, drnd, wl["L"], wl["R0"], wl["edges"], 4, "mixed",
-                                                 stream=stream)
-        b.record(stream)
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
+    ts, stages = [], []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            with torch.cuda.stream(stream):
+                _, (nd, nr) = binding.hip_bispectrum(dpos, None, drnd, wl["L"], wl["R0"], wl["edges"], 4, "mixed",
+                                                     stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+            stages.append(binding.bispectrum_stage_times())
     ms = float(np.mean(ts))
+    st = np.mean(np.array(stages), axis=0)
+    n_prim = len(wl["pos"]) + len(wl["rand"])
+    pk = _peaks()
+    fp32 = fp32_peak_tflops(pk)
+    bf16 = float(pk.get("bf16_tflops", 1906.9))
+    alm_flops = 60.0 * (nd + nr) * nk              # 25 harmonic FMAs + 5 jbar per (p, j)-bin
+    con_alg = 2.0 * 25 * nk * nk * n_prim          # sum_l (2l+1) n_k^2 MACs per primary
+    P = 8 if 128 // nk >= 5 else 4
+    K = ((9 * P + 15) // 16) * 16
+    tiles = (5 + min(5, 128 // nk) - 1) // min(5, 128 // nk)
+    con_exec = 2.0 * 128 * 128 * K * 6 * tiles * np.ceil(n_prim / P)  # 6 slice products per K step
+    out = {"workload": "bk_n5e5" if scale == 1.0 else f"bk_n5e5 x{scale}", "value": (nd + nr) * nk / (ms / 1e3),
+           "unit": UNIT, "ms_per_call": ms, "pairs_data_primaries": nd, "pairs_random_primaries": nr, "n_k": nk,
+           "ell": [0, 1, 2, 3, 4], "clocks": clk.summary(),
+           "stage_ms": {"alm_pass": float(st[0]), "contraction": float(st[1]), "c_term": float(st[2]),
+                        "chunks": int(st[3]), "rest": ms - float(st[0] + st[1] + st[2])},
+           "roofline_alm": {"bound": "alu", "kernel": "k_bk_alm<float,1>", "achieved": alm_flops / (st[0] / 1e3) / 1e12,
+                            "peak": fp32, "unit": "TFLOP/s", "frac": alm_flops / (st[0] / 1e3) / 1e12 / fp32,
+                            "flops_per_pair_bin": 60.0, "peak_note": "derived FP32 FMA peak"},
+           "roofline_contraction": {"bound": "tensor", "kernel": "k_bk_contract_tc", "unit": "TFLOP/s",
+                                    "achieved": con_alg / (st[1] / 1e3) / 1e12, "peak": bf16,
+                                    "frac": con_alg / (st[1] / 1e3) / 1e12 / bf16,
+                                    "executed_tflops": con_exec / (st[1] / 1e3) / 1e12,
+                                    "flops_per_primary": 2.0 * 25 * nk * nk,
+                                    "note": ("achieved = algorithmic 2 sum_l (2l+1) n_k^2 flops per primary; "
+                                             "executed counts the padded 128-row tiles and the 6 exact-split "
+                                             "products (BF16 MMAs); peak = measured BF16 burst")}}
+    if parity:
+        import oracle
+        p64, r64 = wl["pos"].astype(np.float64), wl["rand"].astype(np.float64)
+        dS, rS = (1000, 1064), (3000, 3064)
+        T, _ = binding.hip_bispectrum_partial(dpos, None, drnd, wl["L"], wl["R0"], wl["edges"], 4, "mixed",
+                                              data_range=dS, rand_range=rS)
+        Td, _ = oracle.bispectrum_primary_sum(p64[dS[0]:dS[1]], np.ones(dS[1] - dS[0]), np.arange(*dS), p64, None,
+                                              wl["L"], wl["R0"], wl["edges"], 4)
+        Tr, _ = oracle.bispectrum_primary_sum(r64[rS[0]:rS[1]], np.ones(rS[1] - rS[0]), None, p64, None,
+                                              wl["L"], wl["R0"], wl["edges"], 4)
+        Tref = Td - (len(wl["pos"]) / len(wl["rand"])) * Tr
+        out["parity"] = dict(_bk_metrics(T, Tref), tolerance=1e-4,
+                             sample=(f"primary sums of data primaries {dS[0]}..{dS[1]} and random primaries "
+                                     f"{rS[0]}..{rS[1]} (input order) against the FP64 oracle"))
     # the same estimator without randoms: the DDR^II term from the E^II kernel (App. A)
     with torch.cuda.stream(stream):
         binding.hip_bispectrum_analytic(dpos, None, wl["L"], wl["R0"], wl["edges"], 4, "mixed", stream=stream)
@@ -233,10 +305,125 @@ def bispectrum_rate(binding, stream, reps: int = 2, scale: float = 1.0):
         b.record(stream)
         b.synchronize()
         ta.append(a.elapsed_time(b))
-    analytic = {"ms_per_call": float(np.mean(ta)), "note": "same B without the random catalog (E^II kernel, App. A)"}
-    return {"workload": "bk_n5e5", "value": (nd + nr) * nk / (ms / 1e3), "unit": UNIT, "ms_per_call": ms,
-            "analytic_ddr2": analytic,
-            "pairs_data_primaries": nd, "pairs_random_primaries": nr, "n_k": nk, "ell": [0, 1, 2, 3, 4]}
+    out["analytic_ddr2"] = {"ms_per_call": float(np.mean(ta)),
+                            "note": "same B without the random catalog (E^II kernel, App. A)"}
+    return out
+
+
+def _pk_metrics(P, Pref):
+    """Per-bin errors of a P (or DD) array [n_ell][n_k]: floored (the asserted
+    metric of the tests), the same without the floor, and the plain relative error."""
+    P, Pref = np.asarray(P, float), np.asarray(Pref, float)
+    d = np.abs(P - Pref)
+    scale = np.maximum(np.abs(Pref), np.abs(Pref[0])[None, :])
+    floor = 1e-2 * np.max(np.abs(Pref[0]))
+    nz, plain = scale > 0, np.abs(Pref) > 0
+    return {"floored": float(np.max(d / np.maximum(scale, floor))),
+            "survey": float(np.max(d[nz] / scale[nz])) if np.any(nz) else 0.0,
+            "plain": float(np.max(d[plain] / np.abs(Pref[plain]))) if np.any(plain) else 0.0}
+
+
+def batched_summary(binding, stream, steps: int = 2, fp64: bool = True, bispectrum: bool = True):
+    """The 64-catalog batch: graph replays of the mixed plan (timed), one replay of
+    the same plan in FP64 (the plain baseline, and the parity reference of every
+    catalog's P), and B of the first 16 catalogs in one hip_bispectrum_batched call."""
+    import torch
+    from paper_2005_01739_gb300 import catalogs
+    cats = catalogs.workload("batched64")["catalogs"]
+    for c in cats:
+        c["pos"] = torch.from_numpy(c["pos"]).cuda()
+        c["w"] = torch.from_numpy(c["w"]).cuda()
+    plan = binding.BatchPlan(cats, "mixed", stream=stream)
+    res = plan.run(stream)
+    ts = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = plan.run(stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+    work = sum((n // 2) * (len(c["edges"]) - 1) for c, (_, _, n) in zip(cats, res))
+    ms = float(np.mean(ts))
+    out = {"workload": "batched64", "catalogs": len(cats),
+           "particles": int(sum(int(c["pos"].shape[0]) for c in cats)), "pair_bins": int(work),
+           "value": work / (ms / 1e3), "unit": UNIT, "ms_per_replay": ms, "launches_per_replay": plan.launches,
+           "clocks": clk.summary()}
+    mixed = [(np.array(P), np.array(DD)) for P, DD, _ in res]
+    plan.close()
+    if fp64:
+        plan64 = binding.BatchPlan(cats, "fp64", stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res64 = plan64.run(stream)
+        b.record(stream)
+        b.synchronize()
+        ms64 = a.elapsed_time(b)
+        plan64.close()
+        errs = [_pk_metrics(Pm, np.array(P64)) for (Pm, _), (P64, _, _) in zip(mixed, res64)]
+        out["fp64_plain"] = {"value": work / (ms64 / 1e3), "unit": UNIT, "ms_per_replay": ms64,
+                             "mixed_over_fp64": ms64 / ms}
+        out["parity_vs_fp64"] = {k: max(e[k] for e in errs) for k in ("floored", "survey", "plain")}
+        out["parity_vs_fp64"]["note"] = ("max over the 64 catalogs and their bins of the mixed P against the same "
+                                         "plan in FP64 (which the tests hold to the oracle at 1e-10)")
+    if bispectrum:
+        bc = []
+        for i, c in enumerate(cats[:16]):
+            N = int(c["pos"].shape[0])
+            rnd = torch.from_numpy(catalogs.uniform(3 * N, c["L"], 2000 + i + 7919)).cuda()
+            bc.append(dict(pos=c["pos"], w=c["w"], rand=rnd, L=c["L"], R0=c["R0"], edges=c["edges"][:26], lmax=4))
+        with torch.cuda.stream(stream):
+            binding.hip_bispectrum_batched(bc, "mixed", stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            resb = binding.hip_bispectrum_batched(bc, "mixed", stream=stream)
+        b.record(stream)
+        b.synchronize()
+        msb = a.elapsed_time(b)
+        wb = sum((nd + nr) * 25 for _, (nd, nr) in resb)
+        out["bispectrum_batched"] = {"workload": "first 16 catalogs of batched64, first 25 bins, 3N randoms, l = 0..4",
+                                     "value": wb / (msb / 1e3), "unit": UNIT, "ms": msb, "pair_bins": int(wb)}
+    return out
+
+
+def plain_config_summary(binding, stream, cpu_seconds: float = 4.0, reps: int = 3):
+    """The 5e4-particle catalog (plain FP64 configuration): both precisions timed
+    (event-timed calls), and their pair sums on a primary sample against the oracle."""
+    import torch
+    import oracle
+    from paper_2005_01739_gb300 import catalogs
+    wl = catalogs.workload("pk_plain_n5e4")
+    dpos = torch.from_numpy(wl["pos"]).cuda()
+    nk = len(wl["edges"]) - 1
+    out = {"workload": "pk_plain_n5e4", "N": int(len(wl["pos"])), "L": wl["L"], "R0": wl["R0"], "n_k": nk}
+    ref_n = None
+    for prec in ("fp64", "mixed"):
+        with torch.cuda.stream(stream):
+            binding.hip_power(dpos, None, wl["L"], wl["R0"], wl["edges"], 4, 2, prec, stream=stream)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            with torch.cuda.stream(stream):
+                _, _, n = binding.hip_power(dpos, None, wl["L"], wl["R0"], wl["edges"], 4, 2, prec, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = float(np.mean(ts))
+        out[prec] = {"value": (n // 2) * nk / (ms / 1e3), "unit": UNIT, "ms_per_call": ms}
+        ref_n = n
+    out["mixed_over_fp64"] = out["fp64"]["ms_per_call"] / out["mixed"]["ms_per_call"]
+    m = 4000
+    DD, _ = oracle.power_pair_sum(wl["pos"].astype(np.float64), None, wl["L"], wl["R0"], wl["edges"], 4, 2,
+                                  primaries=np.arange(m))
+    for prec in ("fp64", "mixed"):
+        _, DDg, _ = binding.hip_power(dpos, None, wl["L"], wl["R0"], wl["edges"], 4, 2, prec, prim_range=(0, m))
+        out[prec]["parity_DD"] = _pk_metrics(DDg, DD)
+    out["parity_sample"] = f"DD of the first {m} primaries against the FP64 oracle"
+    out["unordered_pairs"] = int(ref_n // 2)
+    return out
 
 
 def run_reference(args):
@@ -290,82 +477,28 @@ def subsample_rate(binding, dpos, dw, stream, flush, fraction=0.01, reps=10):
 
 
 def run_batched(args):
-    """The 64-catalog batch: one graph replay (cell builds, one persistent pair
-    launch over all catalogs, FP64 finalize) per step."""
+    """The 64-catalog batch alone (batched_summary), optionally after autotuning
+    the plan's cell shape."""
     import torch
 
     from paper_2005_01739_gb300 import binding, build, catalogs
     build.build()
     binding.load()
-    cats = catalogs.workload("batched64")["catalogs"]
-    for c in cats:
-        c["pos"] = torch.from_numpy(c["pos"]).cuda()
-        c["w"] = torch.from_numpy(c["w"]).cuda()
     stream = torch.cuda.Stream()
-    plan = binding.BatchPlan(cats, "mixed", stream=stream)
     tuned = None
-    if args.tune:  # pick the cell shape by timing each candidate once (not part of the timed steps)
+    if args.tune:  # pick the cell shape by timing each candidate once
+        cats = catalogs.workload("batched64")["catalogs"]
+        for c in cats:
+            c["pos"] = torch.from_numpy(c["pos"]).cuda()
+            c["w"] = torch.from_numpy(c["w"]).cuda()
+        plan = binding.BatchPlan(cats, "mixed", stream=stream)
         chosen, tms = plan.tune(stream)
+        plan.close()
         tuned = {"chosen_particles_per_cell": chosen, "replay_ms": {str(k): v for k, v in tms.items()}}
-    for _ in range(max(1, args.warmup)):
-        res = plan.run(stream)
-    ts = []
-    with ClockSampler(0) as clk:
-        for _ in range(args.steps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            res = plan.run(stream)
-            b.record(stream)
-            b.synchronize()
-            ts.append(a.elapsed_time(b))
-    work = sum((n // 2) * (len(c["edges"]) - 1) for c, (_, _, n) in zip(cats, res))
-    ms = float(np.mean(ts))
-    launches = plan.launches
-    plan.close()
-    # the same batch through the plain FP64 path (one replay after one warm-up)
-    fp64 = None
-    if not args.skip_fp64:
-        plan64 = binding.BatchPlan(cats, "fp64", stream=stream)
-        plan64.run(stream)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        plan64.run(stream)
-        b.record(stream)
-        b.synchronize()
-        ms64 = a.elapsed_time(b)
-        plan64.close()
-        fp64 = {"value": work / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "mixed_over_fp64": ms64 / ms}
-    # B on the first 16 catalogs with the first 25 of their bins, 3N randoms each:
-    # one persistent launch over all their primaries (one warm-up, one timed call)
-    bisp = None
-    if not args.skip_bispectrum:
-        bc = []
-        for i, c in enumerate(cats[:16]):
-            N = int(c["pos"].shape[0])
-            rnd = torch.from_numpy(catalogs.uniform(3 * N, c["L"], 2000 + i + 7919)).cuda()
-            bc.append(dict(pos=c["pos"], w=c["w"], rand=rnd, L=c["L"], R0=c["R0"], edges=c["edges"][:26], lmax=4))
-        with torch.cuda.stream(stream):
-            binding.hip_bispectrum_batched(bc, "mixed", stream=stream)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        with torch.cuda.stream(stream):
-            resb = binding.hip_bispectrum_batched(bc, "mixed", stream=stream)
-        b.record(stream)
-        b.synchronize()
-        msb = a.elapsed_time(b)
-        wb = sum((nd + nr) * 25 for _, (nd, nr) in resb)
-        bisp = {"workload": "first 16 catalogs of batched64, first 25 bins, 3N randoms, l = 0..4",
-                "value": wb / (msb / 1e3), "unit": UNIT, "ms": msb, "pair_bins": int(wb),
-                "note": "hip_bispectrum_batched: cell builds and S^a per catalog, then one persistent launch"}
-    print(json.dumps({"metric": METRIC, "value": work / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
-                      "bispectrum_batched": bisp,
-                      "data": "synthetic", "config": {"workload": "batched64", "catalogs": len(cats),
-                                                      "particles": int(sum(int(c["pos"].shape[0]) for c in cats)),
-                                                      "pair_bins": int(work)},
-                      "gpu_launches": launches * args.steps, "clocks": clk.summary(), "fp64_plain": fp64,
-                      "autotune": tuned}),
-          flush=True)
+    out = batched_summary(binding, stream, steps=args.steps, fp64=not args.skip_fp64,
+                          bispectrum=not args.skip_bispectrum)
+    out["autotune"] = tuned
+    print(json.dumps({"batched": out}), flush=True)
     return 0
 
 
@@ -471,7 +604,9 @@ def run_ours(args):
             ev[i][0].record(stream)
             _, _, npairs = step()
             ev[i][1].record(stream)
-            pair_ms.append(float(binding.stage_times()[2]))
+            st_i = binding.stage_times()
+            pair_ms.append(float(st_i[2]))
+            stage_rec = [float(x) for x in st_i]
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
@@ -512,6 +647,12 @@ def run_ours(args):
     bisp = None
     if not args.skip_bispectrum:
         bisp = bispectrum_rate(binding, stream)
+    batched = None
+    plain = None
+    if rank == 0 and not args.skip_batched:
+        batched = batched_summary(binding, stream, fp64=not args.skip_fp64, bispectrum=not args.skip_bispectrum)
+    if rank == 0 and not args.skip_cpu:
+        plain = plain_config_summary(binding, stream)
 
     if rank != 0:
         if ws > 1:
@@ -543,10 +684,11 @@ def run_ours(args):
         "gpu_launches": PAIR_PASS_LAUNCHES[pair_pass] * args.steps,
         "clocks": clk.summary(),
         "pairs": int(pairs),
-        "stage_ms": dict(zip(["upload", "cells", "pairs", "finalize", "download"],
-                             [float(x) for x in binding.stage_times()])),
+        "stage_ms": dict(zip(["upload", "cells", "pairs", "finalize", "download"], stage_rec)),
         "fp64_plain": fp64,
         "bispectrum": bisp,
+        "batched": batched,
+        "plain_n5e4": plain,
         "subsample": subs,
     }
     # after stage_ms is read: these calls replace the recorded stage times
@@ -574,6 +716,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-bispectrum", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--bk-only", action="store_true", help="time only the bispectrum workload")
     ap.add_argument("--batched", action="store_true", help="time the 64-catalog batched workload")
     ap.add_argument("--large", action="store_true", help="time P and B on the 256^3 Zel'dovich lattice")

@@ -265,6 +265,7 @@ static hip_status power_impl(const float *pos, const float *w, int64_t N, double
     ka.p0 = p0;
     ka.p1 = p1;
     ka.n_items = n_cells * HIP_NSHIFT;
+    ka.n_part = N;
     ka.work_counter = counter;
     ka.partials = partials;
     ka.npairs = npairs;
@@ -575,6 +576,9 @@ static BkCat<T> bk_cat(const CellList<T> &dcl, const CellList<T> &rcl, const int
     a.R0 = (T)R0;
     a.rand_weight = (T)rand_weight;
     a.cc_scale = (T)(a.n_cc / R0);
+    a.cc_lo = (T)(a.n_cc / R0 - (double)a.cc_scale);
+    a.iR = (T)(1.0 / R0);
+    a.iR_lo = (T)(1.0 / R0 - (double)a.iR);
     a.cmom = cmom;
     a.npairs = npairs;
     for (int q = 0; q < HIP_BMAXE; ++q) {
@@ -693,6 +697,7 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
         ka.p0 = 0;
         ka.p1 = N;
         ka.n_items = n_cells * HIP_NSHIFT;
+        ka.n_part = N;
         ka.work_counter = counter;
         ka.partials = (double *)(b + o_pp);
         ka.npairs = npairs;
@@ -894,6 +899,7 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
         ka.p0 = 0;
         ka.p1 = c.N;
         ka.n_items = y.n_cells * HIP_NSHIFT;
+        ka.n_part = c.N;
         ka.work_counter = counter;
         ka.partials = (double *)(b + o_pp);
         ka.npairs = npairs;
@@ -1047,6 +1053,7 @@ static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t
     ka.p0 = 0;
     ka.p1 = N;
     ka.n_items = n_cells * HIP_NSHIFT;
+    ka.n_part = N;
     ka.work_counter = counter;
     ka.partials = (double *)(b + o_pp);
     ka.npairs = npairs;

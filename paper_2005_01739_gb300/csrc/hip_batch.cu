@@ -135,7 +135,7 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
             ne_max = std::max(ne_max, L.n_e);
             L.o_ke = cv.take(sizeof(double) * L.n_e);
             L.o_coef = cv.take(sizeof(double) * hip_pm_coef_doubles(L.n_e, L.pm_nc));
-            L.o_mg = cv.take(sizeof(double) * 3 * HIP_PM_M * L.pm_nc);
+            L.o_mg = cv.take(sizeof(double) * hip_pm_mg_doubles(L.pm_nc));
         }
     }
     const size_t o_bc = cv.take(sizeof(BatchCat<T>) * nc), o_fc = cv.take(sizeof(FinalCat) * nc);
@@ -210,7 +210,8 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
             m.item_begin = d.item_begin;
             m.item_end = d.item_end;
             m.R0 = (T)c.R0;
-            m.dc = (T)(c.R0 / L.pm_nc);
+            m.dc = (T)hip_pm_width(c.R0, L.pm_nc);
+            m.n_part = c.N;
             m.Mg = (double *)(b + L.o_mg);
             m.npairs = d.npairs;
             PmContractCat &k = cc[oi];
@@ -280,7 +281,8 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
         const float *w = c.w ? (L.dev_w ? c.w : (const float *)(b + L.o_w)) : nullptr;
         if ((ce = cudaMemsetAsync(b + L.o_acc, 0, sizeof(double) * 3 * L.n_e, st)) != cudaSuccess) break;
         if ((ce = cudaMemsetAsync(b + L.o_np, 0, sizeof(unsigned long long), st)) != cudaSuccess) break;
-        if (pm && (ce = cudaMemsetAsync(b + L.o_mg, 0, sizeof(double) * 3 * HIP_PM_M * L.pm_nc, st)) != cudaSuccess)
+        if (pm && (ce = cudaMemsetAsync(b + L.o_mg, 0, sizeof(double) * hip_pm_mg_doubles(L.pm_nc), st)) !=
+                      cudaSuccess)
             break;
         // each catalog has its own S1 and error word (the cell build clears both)
         ce = hip_build_cells<T>(pos, w, c.N, c.L, L.n_c, (T *)(b + L.o_x), (T *)(b + L.o_y), (T *)(b + L.o_z),
@@ -290,10 +292,20 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
         launches += 3;
     }
     if (pm) {
+        // particles per cell, weighted by each catalog's share of the pairs
+        double wsum = 0.0, psum = 0.0;
+        for (int i = 0; i < nc; ++i) {
+            const hip_catalog &c = pl->cats[i];
+            const double cells = (double)pl->lay[i].n_c * pl->lay[i].n_c * pl->lay[i].n_c;
+            const double pairs = (double)c.N * (double)c.N / (c.L * c.L * c.L) * c.R0 * c.R0 * c.R0;
+            wsum += pairs;
+            psum += pairs * (double)c.N / cells;
+        }
         if (ce == cudaSuccess)
             ce = hip_power_moments_batched<T>((const PmCat<T> *)(b + o_pc), nc, items, nc_max, counter,
-                                              (const PmContractCat *)(b + o_cc), ne_max, st);
-        launches += 2;
+                                              (const PmContractCat *)(b + o_cc), ne_max,
+                                              wsum > 0.0 ? psum / wsum : 0.0, st);
+        launches += sizeof(T) == 4 ? 3 : 2;  // (sum |w|,) moments, contraction
     } else {
         if (ce == cudaSuccess)
             ce = hip_power_pairs_batched<T>((const BatchCat<T> *)(b + o_bc), nc, items, nch, counter, grid, st);

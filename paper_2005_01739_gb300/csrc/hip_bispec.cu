@@ -31,10 +31,6 @@ static __constant__ HipCoeffs c_coeffs;
 // normalisation of the real harmonics: sqrt((l-m)!/(l+m)!) (times sqrt 2 for m > 0)
 static __constant__ float c_ylm_norm_f[HIP_LMAX + 1][HIP_LMAX + 1];
 static __constant__ double c_ylm_norm_d[HIP_LMAX + 1][HIP_LMAX + 1];
-// Legendre recurrence P_{m+1} = a_m t P_m - b_m P_{m-1}: a_m = (2m+1)/(m+1), b_m = m/(m+1)
-static __constant__ float c_leg_f[2][HIP_BK_NM];
-static __constant__ double c_leg_d[2][HIP_BK_NM];
-
 cudaError_t hip_upload_coeffs_bispec()
 {
     cudaError_t e = cudaMemcpyToSymbol(c_coeffs, &hip_host_coeffs(), sizeof(HipCoeffs));
@@ -54,16 +50,7 @@ cudaError_t hip_upload_coeffs_bispec()
         }
     if ((e = cudaMemcpyToSymbol(c_ylm_norm_f, nf, sizeof(nf))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_ylm_norm_d, nd, sizeof(nd))) != cudaSuccess) return e;
-    float lf[2][HIP_BK_NM];
-    double ld[2][HIP_BK_NM];
-    for (int m = 0; m < HIP_BK_NM; ++m) {
-        ld[0][m] = (2.0 * m + 1.0) / (m + 1.0);
-        ld[1][m] = (double)m / (m + 1.0);
-        lf[0][m] = (float)ld[0][m];
-        lf[1][m] = (float)ld[1][m];
-    }
-    if ((e = cudaMemcpyToSymbol(c_leg_f, lf, sizeof(lf))) != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(c_leg_d, ld, sizeof(ld));
+    return cudaSuccess;
 }
 
 int hip_bk_intervals(double R0, double k_max)
@@ -78,19 +65,6 @@ template <>
 __device__ __forceinline__ float ylm_norm<float>(int l, int m) { return c_ylm_norm_f[l][m]; }
 template <>
 __device__ __forceinline__ double ylm_norm<double>(int l, int m) { return c_ylm_norm_d[l][m]; }
-
-template <typename T>
-__device__ __forceinline__ T leg_a(int m);
-template <>
-__device__ __forceinline__ float leg_a<float>(int m) { return c_leg_f[0][m]; }
-template <>
-__device__ __forceinline__ double leg_a<double>(int m) { return c_leg_d[0][m]; }
-template <typename T>
-__device__ __forceinline__ T leg_b(int m);
-template <>
-__device__ __forceinline__ float leg_b<float>(int m) { return c_leg_f[1][m]; }
-template <>
-__device__ __forceinline__ double leg_b<double>(int m) { return c_leg_d[1][m]; }
 
 // Real harmonics R_lm(u) for l <= 4 at unit vector (x, y, z), index l*l + l + m:
 // R_l0 = P_l(z); R_l,+m = n_lm Ptilde_l^m(z) Re (x + i y)^m; R_l,-m = same with Im,
@@ -208,18 +182,27 @@ __device__ __forceinline__ void bk_load_edges(const BkCat<T> &a, int lane, BkEdg
     }
 }
 
+// Rounding error of s = a + b (Knuth's TwoSum); zero in FP64, where the
+// separations are exact enough without it.
+__device__ __forceinline__ float bk_low(float a, float b, float s)
+{
+    const float bv = __fadd_rn(s, -a);
+    return __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bv)), __fadd_rn(b, -bv));
+}
+__device__ __forceinline__ double bk_low(double, double, double) { return 0.0; }
+
 // Process the first n (<= 32) queued neighbours of the current primary: their
 // geometry and harmonics (one per lane), their C-term moments (one lane per
 // moment) and their contributions to the edge sums (one lane per bin edge).
 template <typename T, int NCH>
-__device__ __forceinline__ void bk_flush(BkWarpSmem<T> &sm, T *cm, int n, T s_p, T invR0, T cc_scale, int n_cc,
+__device__ __forceinline__ void bk_flush(BkWarpSmem<T> &sm, T *cm, int n, T s_p, T iR, T iR_lo, T cc_scale, T cc_lo, int n_cc,
                                          int n_e, const BkEdges<T, NCH> &ed, int lane, T (&E)[NCH][HIP_NLM])
 {
     if (lane < n) {
         const T dx = sm.qa[lane][0], dy = sm.qa[lane][1], dz = sm.qa[lane][2], wj = sm.qa[lane][3];
         const T r = hip_sqrt_b(dx * dx + dy * dy + dz * dz);
         const T ir = T(1) / r;
-        const T W = hip_W<T>(r * invR0);
+        const T W = hip_W<T>(fma(r, iR_lo, r * iR));
         T R[HIP_NLM];
         hip_real_ylm<T>(dx * ir, dy * ir, dz * ir, R);
 #pragma unroll
@@ -228,7 +211,7 @@ __device__ __forceinline__ void bk_flush(BkWarpSmem<T> &sm, T *cm, int n, T s_p,
         sm.qd[lane][26] = wj * W;
         sm.qd[lane][27] = T(0);
         // C term: interval c of width R0 / n_cc, coordinate t in [-1, 1]
-        const T x = r * cc_scale;
+        const T x = fma(r, cc_lo, r * cc_scale);
         int c = (int)x;
         if (c > n_cc - 1) c = n_cc - 1;
         T t = T(2) * (x - T(c)) - T(1);
@@ -239,7 +222,7 @@ __device__ __forceinline__ void bk_flush(BkWarpSmem<T> &sm, T *cm, int n, T s_p,
         sm.pt[lane][1] = p1;
 #pragma unroll
         for (int m = 1; m < HIP_BK_NM - 1; ++m) {
-            const T p2 = leg_a<T>(m) * t * p1 - leg_b<T>(m) * p0;
+            const T p2 = hip_leg_alpha<T>(m) * t * p1 - hip_leg_beta<T>(m) * p0;  // R_m = d_m P_m
             sm.pt[lane][m + 1] = p2;
             p0 = p1;
             p1 = p2;
@@ -287,7 +270,7 @@ __device__ __forceinline__ void bk_primary(const BkCat<T> &a, int g, BkWarpSmem<
     const T s_p = excluded ? T(0) : (is_rand ? a.rand_weight : T(pl.w[p]));
     if (lane == 0) *spp = s_p;
     if (excluded) return;
-    const T R0sq = a.R0 * a.R0, invR0 = T(1) / a.R0, cc_scale = a.cc_scale;
+    const T R0sq = a.R0 * a.R0, iR = a.iR, iR_lo = a.iR_lo, cc_scale = a.cc_scale, cc_lo = a.cc_lo;
     const int n_cc = a.n_cc;
     const int c = is_rand ? a.rcell[p] : a.dcell[p];
     const int cx = c / (n_c * n_c), cy = (c / n_c) % n_c, cz = c % n_c;
@@ -300,13 +283,14 @@ __device__ __forceinline__ void bk_primary(const BkCat<T> &a, int g, BkWarpSmem<
         for (int i = 0; i < HIP_NLM; ++i) E[t][i] = T(0);
     int qn = 0;
     // cell shifts of this primary: lane 3 axis + d + 1 holds the shift of
-    // neighbour offset d along that axis (the shift's low part, below 1e-6 of the
-    // cell side, is under the FP32 budget of B and dropped)
-    T shl = T(0);
+    // neighbour offset d along that axis (hi, lo).  The candidate test uses the
+    // rounded offset; an accepted neighbour's separation adds the low part (the
+    // shift's own and the rounding of p - shift), which is common to all pairs
+    // across a periodic face and would otherwise bias them alike.
+    T shl = T(0), shll = T(0);
     if (lane < 9) {
         const int ax = lane / 3, cc = ax == 0 ? cx : (ax == 1 ? cy : cz);
-        T lo;
-        hip_cell_shift(a.data, cc, lane % 3 - 1, shl, lo);
+        hip_cell_shift(a.data, cc, lane % 3 - 1, shl, shll);
     }
     for (int s = 0; s < 27; ++s) {
         const int dx = s / 9 - 1, dy = (s / 3) % 3 - 1, dz = s % 3 - 1;
@@ -315,6 +299,9 @@ __device__ __forceinline__ void bk_primary(const BkCat<T> &a, int g, BkWarpSmem<
         const T shx = __shfl_sync(0xffffffffu, shl, dx + 1), shy = __shfl_sync(0xffffffffu, shl, dy + 4),
                 shz = __shfl_sync(0xffffffffu, shl, dz + 7);
         const T ox = px - shx, oy = py - shy, oz = pz - shz;
+        const T oxl = bk_low(px, -shx, ox) - __shfl_sync(0xffffffffu, shll, dx + 1),
+                oyl = bk_low(py, -shy, oy) - __shfl_sync(0xffffffffu, shll, dy + 4),
+                ozl = bk_low(pz, -shz, oz) - __shfl_sync(0xffffffffu, shll, dz + 7);
         for (int jb = b0; jb < b1; jb += 32) {
             const int j = jb + lane;
             bool ok = false;
@@ -329,9 +316,9 @@ __device__ __forceinline__ void bk_primary(const BkCat<T> &a, int g, BkWarpSmem<
             const unsigned m = __ballot_sync(0xffffffffu, ok);
             if (ok) {
                 const int slot = qn + __popc(m & lt_mask);
-                sm.qa[slot][0] = ddx;
-                sm.qa[slot][1] = ddy;
-                sm.qa[slot][2] = ddz;
+                sm.qa[slot][0] = ddx + oxl;
+                sm.qa[slot][1] = ddy + oyl;
+                sm.qa[slot][2] = ddz + ozl;
                 sm.qa[slot][3] = T(a.data.w[j]);
             }
             const int nq = __popc(m);
@@ -342,7 +329,7 @@ __device__ __forceinline__ void bk_primary(const BkCat<T> &a, int g, BkWarpSmem<
             qn += nq;
             if (qn >= 32) {
                 __syncwarp();
-                bk_flush<T, NCH>(sm, cm, 32, s_p, invR0, cc_scale, n_cc, n_e, ed, lane, E);
+                bk_flush<T, NCH>(sm, cm, 32, s_p, iR, iR_lo, cc_scale, cc_lo, n_cc, n_e, ed, lane, E);
                 const int rest = qn - 32;
                 T mv[4] = {T(0), T(0), T(0), T(0)};
                 if (lane < rest) {
@@ -361,7 +348,7 @@ __device__ __forceinline__ void bk_primary(const BkCat<T> &a, int g, BkWarpSmem<
     }
     if (qn > 0) {
         __syncwarp();
-        bk_flush<T, NCH>(sm, cm, qn, s_p, invR0, cc_scale, n_cc, n_e, ed, lane, E);
+        bk_flush<T, NCH>(sm, cm, qn, s_p, iR, iR_lo, cc_scale, cc_lo, n_cc, n_e, ed, lane, E);
     }
 #pragma unroll
     for (int t = 0; t < NCH; ++t) {
@@ -680,10 +667,10 @@ __global__ void k_bk_cc_nodes(BkCTerm c, BkCQ q, double *__restrict__ wn, double
         const double r = (cc + 0.5 * (1.0 + t)) * (c.R0 / c.n_cc);
         double rho = 0.0, p0 = 1.0, p1 = t;
         const double *M = c.cmom + (size_t)cc * HIP_BK_NM;
-        rho += 0.5 * M[0] * p0 + 1.5 * M[1] * p1;
+        rho += 0.5 * M[0] * p0 + 1.5 * M[1] * p1;  // M[m] are moments of R_m = d_m P_m
         for (int m = 1; m < HIP_BK_NM - 1; ++m) {
             const double p2 = ((2.0 * m + 1.0) * t * p1 - m * p0) / (m + 1.0);
-            rho += (m + 1.5) * M[m + 1] * p2;
+            rho += (m + 1.5) * (M[m + 1] / hip_leg_scale(m + 1)) * p2;
             p0 = p1;
             p1 = p2;
         }

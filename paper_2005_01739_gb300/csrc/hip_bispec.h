@@ -38,7 +38,8 @@ struct BkCat {
     int n_cc;                  // C-term intervals
     T R0;
     T rand_weight;             // -S1 / N_r
-    T cc_scale;                // n_cc / R0
+    T cc_scale, cc_lo;         // n_cc / R0 = cc_scale + cc_lo
+    T iR, iR_lo;               // 1 / R0 = iR + iR_lo
     double *cmom;              // [n_cc][HIP_BK_NM] FP64 C-term moments (atomically added)
     unsigned long long *npairs;  // [0] data-primary pairs, [1] random-primary pairs
     T k[HIP_BMAXE], klo[HIP_BMAXE], k3[HIP_BMAXE], jfac[HIP_BMAXE];

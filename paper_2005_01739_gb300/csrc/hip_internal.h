@@ -71,6 +71,7 @@ struct PowerKernelArgs {
     int los;                 // line-of-sight axis
     long long p0, p1;        // primary range in input order
     int n_items;             // n_cells * HIP_NSHIFT
+    long long n_part;        // particles of the catalog (sets the moment pass's CTA size)
     int *work_counter;
     double *partials;        // [gridDim.x][3][n_e]
     unsigned long long *npairs;

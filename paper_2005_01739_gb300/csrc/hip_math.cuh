@@ -97,6 +97,37 @@ __host__ __device__ __forceinline__ T hip_W(T x)
     return T(0);
 }
 
+// ------------------------------------------------- scaled Legendre series ----
+// R_m(t) = d_m P_m(t) with d_0 = 1 and d_{m+1} = d_m (m + 1) / 2^{k_m},
+// k_m = floor(log2(m + 1)).  Bonnet's recurrence becomes
+//     R_{m+1} = alpha_m t R_m - beta_m R_{m-1},
+//     alpha_m = (2m + 1) / 2^{k_m},  beta_m = m^2 / 2^{k_m + k_{m-1}},
+// whose constants are exact in binary floating point: the recursion in FP32 then
+// has no error common to all its inputs (a rounded (2m+1)/(m+1) would scale every
+// P_{m+1} by the same factor).  d_m stays between 1 and 2^m.
+__host__ __device__ constexpr int hip_leg_k(int m)
+{
+    int k = 0;
+    while ((2 << k) <= m + 1) ++k;
+    return k;
+}
+template <typename T>
+__host__ __device__ constexpr T hip_leg_alpha(int m)
+{
+    return T(2 * m + 1) / T(1 << hip_leg_k(m));
+}
+template <typename T>
+__host__ __device__ constexpr T hip_leg_beta(int m)
+{
+    return T(m * m) / T(1 << (hip_leg_k(m) + hip_leg_k(m - 1)));
+}
+__host__ __device__ constexpr double hip_leg_scale(int m)  // d_m (exact)
+{
+    double d = 1.0;
+    for (int j = 0; j < m; ++j) d = d * (j + 1) / (1 << hip_leg_k(j));
+    return d;
+}
+
 template <typename T>
 __host__ __device__ __forceinline__ void hip_legendre24(T mu, T &l2, T &l4)
 {

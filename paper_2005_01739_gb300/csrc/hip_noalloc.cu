@@ -151,6 +151,7 @@ extern "C" hip_status hip_power_noalloc(const float *pos, const float *w, int64_
     ka.p0 = prim_begin;
     ka.p1 = prim_end;
     ka.n_items = n_cells * HIP_NSHIFT;
+    ka.n_part = N;
     ka.work_counter = counter;
     ka.partials = partials;  // every CTA overwrites its own row
     ka.npairs = npairs;

@@ -352,7 +352,8 @@ __device__ __forceinline__ float hip_two_sum_err(float a, float b, float s)
 }
 
 __device__ __forceinline__ void hip_pair_sep(float xi, float xil, float yi, float yil, float zi, float zil, float xj,
-                                             float yj, float zj, float dx, float dy, float dz, float *rh, float *rl)
+                                             float yj, float zj, float dx, float dy, float dz, int los, float *rh,
+                                             float *rl, float *dlo)
 {
     const float lx = hip_two_sum_err(xi, -xj, dx) + xil;
     const float ly = hip_two_sum_err(yi, -yj, dy) + yil;
@@ -368,15 +369,18 @@ __device__ __forceinline__ void hip_pair_sep(float xi, float xil, float yi, floa
     const float r = sqrtf(s2);
     *rh = r;
     *rl = (fmaf(-r, r, s2) + low) * (0.5f / r);
+    *dlo = los == 0 ? lx : (los == 1 ? ly : lz);  // low part of the line-of-sight component
 }
 __device__ __forceinline__ float hip_low(float a, float b, float s) { return hip_two_sum_err(a, b, s); }
 __device__ __forceinline__ double hip_low(double, double, double) { return 0.0; }
 
 __device__ __forceinline__ void hip_pair_sep(double, double, double, double, double, double, double, double, double,
-                                             double dx, double dy, double dz, double *rh, double *rl)
+                                             double dx, double dy, double dz, int, double *rh, double *rl,
+                                             double *dlo)
 {
     *rh = sqrt(dx * dx + dy * dy + dz * dz);
     *rl = 0.0;
+    *dlo = 0.0;
 }
 
 // Drain a warp's queue and fold the register sums (and, for FP32, the series
@@ -465,7 +469,7 @@ __device__ __forceinline__ double hip_qscale(double) { return 1.0; }
 // candidates one per lane, queue accepted pairs, drain the queue at 32 pairs.
 template <typename T, int NCH, int MASK>
 __device__ __forceinline__ void hip_pair_item(const CellList<T> &cl, int item, long long p0, long long p1, int los,
-                                              T R0sq, T invR0, bool lin, T dk32hi, T dk32lo, WarpSmem<T, NCH> &sm,
+                                              T R0sq, T invR0, T invR0lo, bool lin, T dk32hi, T dk32lo, WarpSmem<T, NCH> &sm,
                                               int lane, const T *kk, const T *kl, const T *kx, int n_e, int tl,
                                               int tw, T (&H)[3][NCH], double (&R)[3][NCH], int &qn,
                                               unsigned long long &cnt)
@@ -530,14 +534,16 @@ __device__ __forceinline__ void hip_pair_item(const CellList<T> &cl, int item, l
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, ok);
                     if (ok) {
-                        T r, rl;
-                        hip_pair_sep(xi, xil, yi, yil, zi, zil, sm.nx[jl], sm.ny[jl], sm.nz[jl], ddx, ddy, ddz, &r,
-                                     &rl);
-                        const T dl = los == 0 ? ddx : (los == 1 ? ddy : ddz);
-                        const T mu = dl / r;
+                        T r, rl, dlo;
+                        hip_pair_sep(xi, xil, yi, yil, zi, zil, sm.nx[jl], sm.ny[jl], sm.nz[jl], ddx, ddy, ddz, los,
+                                     &r, &rl, &dlo);
+                        // mu and W from the full separation (hi + lo): the low parts carry the
+                        // cell shift's rounding, common to all pairs across a periodic face
+                        const T rr = r + rl;
+                        const T mu = ((los == 0 ? ddx : (los == 1 ? ddy : ddz)) + dlo) / rr;
                         T l2, l4;
                         hip_legendre24<T>(mu, l2, l4);
-                        const T om = T(wi) * T(sm.nw[jl]) * hip_W<T>(r * invR0) * T(mult) * hip_qscale(r);
+                        const T om = T(wi) * T(sm.nw[jl]) * hip_W<T>(fma(rr, invR0lo, rr * invR0)) * T(mult) * hip_qscale(rr);
                         const int slot = qn + __popc(m & lt_mask);
                         sm.qr[slot] = r;
                         sm.qrl[slot] = rl;
@@ -578,7 +584,7 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
     for (int i = threadIdx.x; i < 3 * HIP_MAX_EDGES; i += HIP_PAIR_THREADS) (&red[0][0])[i] = 0.0;
     if (threadIdx.x == 0) done = 0;
     __syncthreads();
-    const T R0sq = R0 * R0, invR0 = T(1) / R0;
+    const T R0sq = R0 * R0, invR0 = T(1) / R0, invR0lo = fma(-R0, invR0, T(1)) / R0;  // 1/R0 = invR0 + invR0lo
     const int n_e = a.n_e;
     const int n_ell = (MASK & 16) ? 3 : ((MASK & 4) ? 2 : 1);
     const int tl = (n_e - 1) / 32, tw = (n_e - 32 * tl <= 16) ? n_e - 32 * tl : 0;
@@ -602,7 +608,7 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS)
         if (lane == 0) item = atomicAdd(a.work_counter, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.n_items) break;
-        hip_pair_item<T, NCH, MASK>(cl, item, a.p0, a.p1, a.los, R0sq, invR0, LIN, dk32hi, dk32lo, sm, lane, kk, kl,
+        hip_pair_item<T, NCH, MASK>(cl, item, a.p0, a.p1, a.los, R0sq, invR0, invR0lo, LIN, dk32hi, dk32lo, sm, lane, kk, kl,
                                     kx, n_e, tl, tw, H, R, qn, cnt);
     }
     if (qn > 0) hip_drain_fold<T, NCH, MASK>(sm, qn, kk, kl, kx, lane, n_e, LIN, tl, tw, H, R);
@@ -688,7 +694,7 @@ __global__ void __launch_bounds__(HIP_PAIR_THREADS, 5)
         }
         const BatchCat<T> &bc = cats[c];
         hip_pair_item<T, NCH, 21>(bc.cl, item - bc.item_begin, bc.p0, bc.p1, bc.los, bc.R0 * bc.R0, T(1) / bc.R0,
-                                  bc.lin != 0, bc.dk32hi, bc.dk32lo, sm, lane, kk, kl, kx, bc.n_e, tl, tw, H, R,
+                                  fma(-bc.R0, T(1) / bc.R0, T(1)) / bc.R0, bc.lin != 0, bc.dk32hi, bc.dk32lo, sm, lane, kk, kl, kx, bc.n_e, tl, tw, H, R,
                                   qn, cnt);
     }
     if (cur >= 0) leave(cur);

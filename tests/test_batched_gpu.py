@@ -53,10 +53,11 @@ def _batch(device):
 def test_batched_matches_oracle_and_single_calls():
     cats = _batch(device=True)
     plan = binding.BatchPlan([c for c, _, _ in cats], "mixed")
-    # cell builds (3 per catalog), the pair pass (moment pass and contraction, or the direct pass), finalize (2)
+    # cell builds (3 per catalog), the pair pass (sum |w|, moment pass and contraction, or the direct pass),
+    # finalize (2)
     pm = all(binding.power_pair_pass(c["R0"], c["edges"][-1]) == 1 for c, _, _ in cats)
     assert pm
-    assert plan.launches == 3 * len(cats) + (4 if pm else 3)
+    assert plan.launches == 3 * len(cats) + (5 if pm else 3)
     res1 = plan.run()
     res2 = plan.run()  # replay of the same graph
     for (c, pos, w), (P, DD, n), (P2, _, n2) in zip(cats, res1, res2):

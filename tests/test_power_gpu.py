@@ -129,18 +129,20 @@ def test_moment_pass_at_its_largest_range():
         assert _err(P, Pref) < TOL[prec], prec
 
 
-def test_direct_pass_beyond_moment_range():
-    # R0 k_max = 1080 > 1024: more than 256 moment intervals, so hip_power takes
-    # the direct pair pass (every edge evaluated per pair; FP64 here, the FP32
-    # direct pass is covered by the batched and allocation-free tests)
+@pytest.mark.parametrize("kmax", [90.0, 150.0])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_direct_pass_beyond_moment_range(prec, kmax):
+    # R0 k_max = 1080 and 1800 > 1024: more than 256 moment intervals, so
+    # hip_power takes the direct pair pass (every edge evaluated per pair), in
+    # FP64 and in FP32 (the regime where the FP32 arguments r k are largest)
     pos, w = catalogs.thomas(1500, 60.0, 40, 1.5, seed=35, background_frac=0.3, los_sigma=2.0)
     L, R0 = 60.0, 12.0
-    edges = catalogs.linear_edges(0.5, 90.0, 255)
-    assert binding.power_pair_pass(R0, edges[-1], "fp64") == 0
-    Pref, _, nref, _ = _oracle_P("direct_pass", pos, w, L, R0, edges)
-    P, _, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, "fp64")
-    _same_count("fp64", npairs, nref)
-    assert _err(P, Pref) < TOL["fp64"]
+    edges = catalogs.linear_edges(0.5, kmax, 255)
+    assert binding.power_pair_pass(R0, edges[-1], prec) == 0
+    Pref, _, nref, _ = _oracle_P(("direct_pass", kmax), pos, w, L, R0, edges)
+    P, _, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, prec)
+    _same_count(prec, npairs, nref)
+    assert _err(P, Pref) < TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -271,3 +273,41 @@ def test_window_transform_high_k():
     for prec in ("fp64", "mixed"):
         P, _, _ = binding.hip_power(np.array([[1.0, 2.0, 3.0]], np.float32), None, L, R0, edges, 0, 2, prec)
         assert np.max(np.abs(P[0] + Wt)) < 1e-12 * np.max(np.abs(Wt))
+
+
+def test_mixed_high_k_cancellation_against_fp64():
+    # Sparse clustered catalog at k R0 up to 100 (the 64-catalog batch's R0 = 10
+    # class): P at these k is ~1e-3 of the summed pair terms, so an error that
+    # is common to many pairs (the FP32 rounding of a periodic cell shift in mu
+    # or W, FP32 moment sums that round alike) shows at ~1e-4.  The FP64 GPU
+    # path, held to the oracle at 1e-10 above, is the reference at this size.
+    pos, w = catalogs.thomas(300000, 700.0, 7500, 1.5, seed=41, background_frac=0.1, los_sigma=3.0,
+                             weights="u05_15")
+    L, R0 = 700.0, 10.0
+    edges = catalogs.linear_edges(2.5, 10.0, 25)
+    dpos, dw = _dev(pos), _dev(w)
+    P64, _, n64 = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "fp64")
+    P, _, n = binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed")
+    _same_count("mixed", n, n64)
+    assert n64 > 5_000_000
+    assert _err(P, P64, "vs fp64") < TOL["mixed"]
+
+
+@pytest.mark.parametrize("scale", [1e-9, 1.0, 1e9])
+def test_mixed_wide_weight_range(scale):
+    # Weights over six decades, both signs, overall scale 1e-9 .. 1e9: the FP32
+    # moment sums are fixed point with a unit set per fold epoch from the
+    # largest weight a CTA has staged, raised mid-stream when a heavier one comes.
+    pos, _ = catalogs.thomas(3000, 60.0, 30, 1.5, seed=42, background_frac=0.3, los_sigma=2.0)
+    rng = np.random.default_rng(43)
+    w = rng.uniform(0.5, 1.5, len(pos))
+    w[rng.choice(len(pos), 20, replace=False)] = 300.0
+    w[rng.choice(len(pos), 300, replace=False)] = -0.7
+    w[rng.choice(len(pos), 50, replace=False)] = 3e-4
+    w = (w * scale).astype(np.float32)
+    L, R0 = 60.0, 12.0
+    edges = catalogs.linear_edges(0.2, 4.0, 30)
+    Pref, _, nref, _ = _oracle_P(("wide_w", scale), pos, w, L, R0, edges)
+    P, _, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, "mixed")
+    _same_count("mixed", npairs, nref)
+    assert _err(P, Pref, "scale %g" % scale) < TOL["mixed"]
