@@ -110,7 +110,7 @@ int hip_cells_per_side(double L, double R0)
     double q = std::floor(L / R0);
     int n = (int)q;
     if (n < 1) n = 1;
-    if (n > 128) n = 128;
+    if (n > HIP_MAX_CELLS_SIDE) n = HIP_MAX_CELLS_SIDE;
     return n;
 }
 
@@ -320,33 +320,12 @@ extern "C" hip_status hip_power(const float *pos, const float *w, int64_t N, dou
                               DD_out, npairs_out, st, dev);
 }
 
-// --------------------------------------------------------- hip_bispectrum ----
-// S^a of the bispectrum estimator (Sec. 4.5): the l = 0 pair sum of the power
-// pass over all data, finalized into DD; the Legendre-moment pass where it
-// applies (pm_scratch then holds s_pass_scratch bytes), else the direct pass.
-static size_t s_pass_scratch(double R0, const double *k_edges, int n_k, bool fp32)
-{
-    if (!hip_pm_applicable(R0, k_edges[n_k], fp32)) return 256;
-    return hip_pm_scratch_bytes(n_k + 1, hip_pm_intervals(R0, k_edges[n_k]));
-}
-template <typename T>
-static cudaError_t s_pass(const CellList<T> &cl, const PowerKernelArgs &ka, const double *k_edges, int n_k, double R0,
-                          double L, const double *S1, double *Wt, double *DD, double *P, void *pm_scratch, int pgrid,
-                          cudaStream_t st)
-{
-    const bool pm = hip_pm_applicable(R0, k_edges[n_k], sizeof(T) == 4);
-    const cudaError_t e = pm ? hip_power_moments<T>(cl, ka, k_edges, 1, R0, pm_scratch, ka.partials, st)
-                             : hip_power_pairs<T>(cl, ka, k_edges, 1, R0, pgrid, st);
-    if (e != cudaSuccess) return e;
-    return hip_power_finalize(ka.partials, pm ? 1 : pgrid, n_k + 1, 1, k_edges, R0, L, S1, Wt, DD, P, st);
-}
-
 // ------------------------------------------------ the bispectrum primary sum ----
 // Scratch plan of the B pass for catalogs whose largest n_k, n_cc are nk_max,
 // ncc_max and whose primaries (data then randoms, catalogs end to end) number
 // `total`.  Primaries go through the a_lm pass and the contraction in chunks of
 // at most `chunk` primaries, so X stays within HIP_BK_XBUDGET bytes.
-#define HIP_BK_XBUDGET ((size_t)2 << 30)
+#define HIP_BK_XBUDGET ((size_t)8 << 30)  // a few percent of the 288 GB of HBM
 static int g_bk_tc_grid_cap = 0;  // tests: caps the contraction's CTAs (0 = one per SM)
 static int g_bk_chunk_cap = 0;    // tests: caps the primaries per chunk (0 = by the X budget)
 static int g_bk_fold = 0;         // tests: primaries between the contraction's FP64 folds (0 = default)
@@ -409,6 +388,8 @@ struct BkHostCat {
     const double *k_edges;  // host
     double *cmom;           // device [n_cc][32]
     double *acc;            // device [5][n_k][n_k], zeroed by bk_run
+    long long n_data;       // the data primaries (first in the primary order)
+    double *S;              // device [n_k]: S^a from the data primaries' A^a_00 (zeroed by bk_run), or null
 };
 
 // The primary sum T of every catalog into its acc: the a_lm pass and the
@@ -434,9 +415,14 @@ static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCa
     T *sp = (T *)(b + pl.o_sp);
     double *slots = (double *)(b + pl.o_slots);
     int *cnt = (int *)(b + pl.o_cnt);  // [0] work counter, [1] status
+    bool want_s = false;
     for (int i = 0; i < nc; ++i) {
         HIP_CK(cudaMemsetAsync(hc[i].cmom, 0, sizeof(double) * hc[i].n_cc * HIP_BK_NM, st), "memset");
         HIP_CK(cudaMemsetAsync(hc[i].acc, 0, sizeof(double) * (HIP_LMAX + 1) * hc[i].n_k * hc[i].n_k, st), "memset");
+        if (hc[i].S) {
+            HIP_CK(cudaMemsetAsync(hc[i].S, 0, sizeof(double) * hc[i].n_k, st), "memset");
+            want_s = true;
+        }
     }
     HIP_CK(cudaMemsetAsync(slots, 0, pl.slots_bytes, st), "memset");
     HIP_CK(cudaMemsetAsync(cnt, 0, sizeof(int) * 4, st), "memset");
@@ -483,6 +469,8 @@ static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCa
                 stages += (int)((take + P - 1) / P);
                 g.stage_end = stages;
                 g.acc = hc[ci].acc;
+                g.n_d = (int)std::max(0LL, std::min(hc[ci].n_data - gi, take));
+                g.S = hc[ci].S;
                 segs.push_back(g);
                 x_off += ((take * HIP_NLM * hc[ci].n_k + 63) / 64) * 64;
                 sp_off += ((take + 7) / 8) * 8;
@@ -511,6 +499,7 @@ static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCa
                    "bispectrum contraction (tensor cores)");
         else
             HIP_CK(hip_bk_contract_f64<T>(dsegs, (int)segs.size(), used, pl.nk_max, st), "bispectrum contraction");
+        if (want_s) HIP_CK(hip_bk_s_sum<T>(dsegs, (int)segs.size(), pl.nk_max, st), "bispectrum S sum");
         mark();
     }
     mark();
@@ -612,7 +601,6 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     const int n_c = hip_cells_per_side(L, R0);
     const int n_cells = n_c * n_c * n_c;
     const int n_e = n_k + 1;
-    const int pgrid = hip_power_grid<T>();
     const bool dpos = hip_is_device_ptr(pos), dw = w && hip_is_device_ptr(w), drp = hip_is_device_ptr(rpos);
     const size_t tsz = (size_t)(HIP_LMAX + 1) * n_k * n_k;
     const int n_cc = hip_bk_intervals(R0, k_edges[n_k]);
@@ -629,13 +617,11 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     const size_t o_ds = cv.take(sizeof(int) * (n_cells + 1)), o_df = cv.take(sizeof(int) * n_cells);
     const size_t o_dsc = cv.take(sizeof(int) * N), o_rsc = cv.take(sizeof(int) * N_r);
     const size_t o_rs = cv.take(sizeof(int) * (n_cells + 1)), o_rf = cv.take(sizeof(int) * n_cells);
-    const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * n_e);
     const size_t o_acc = cv.take(sizeof(double) * tsz);
     const size_t o_cmom = cv.take(sizeof(double) * n_cc * HIP_BK_NM);
     const size_t o_small = cv.take(sizeof(double) * 16);
     const size_t o_wt = cv.take(sizeof(double) * n_k), o_dd = cv.take(sizeof(double) * 3 * n_k);
     const size_t o_p = cv.take(sizeof(double) * 3 * n_k), o_b = cv.take(sizeof(double) * tsz);
-    const size_t o_pm = cv.take(s_pass_scratch(R0, k_edges, n_k, sizeof(T) == 4));
     const BkPlan pl = bk_plan<T>(cv, 1, n_k, n_cc, N + N_r, hip_bk_cterm_scratch_bytes(n_cc, n_k));
     hip_status hs = ws.reserve(cv.total, st);
     if (hs != HIP_OK) return hs;
@@ -690,24 +676,15 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     HIP_CK(cudaMemsetAsync(npairs, 0, 3 * sizeof(unsigned long long), st), "memset");
     HIP_CK(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st), "memset");
     double *Wt = (double *)(b + o_wt), *DD = (double *)(b + o_dd), *P = (double *)(b + o_p);
-    if (!partial) {
-        PowerKernelArgs ka;
-        ka.n_e = n_e;
-        ka.los = 2;
-        ka.p0 = 0;
-        ka.p1 = N;
-        ka.n_items = n_cells * HIP_NSHIFT;
-        ka.n_part = N;
-        ka.work_counter = counter;
-        ka.partials = (double *)(b + o_pp);
-        ka.npairs = npairs;
-        HIP_CK(s_pass<T>(dcl, ka, k_edges, n_k, R0, L, S1, Wt, DD, P, b + o_pm, pgrid, st), "pair pass (S)");
-    }
+    (void)P;
+    // S^a (the l = 0 data pair sum) comes from the a_lm pass (hip_bk_s_sum); W~^a here
+    if (!partial) HIP_CK(hip_window_transform(n_e, k_edges, R0, Wt, st), "window transform");
     std::vector<BkCat<T>> cats(1, bk_cat<T>(dcl, rcl, (const int *)(b + o_dsc), (const int *)(b + o_rsc), N, N_r,
                                             ranges, k_edges, n_k, R0, -hS1 / (double)N_r, npairs + 1,
                                             (double *)(b + o_cmom)));
     std::vector<BkHostCat> hc(1);
-    hc[0] = BkHostCat{N + N_r, n_k, n_cc, R0, k_edges, (double *)(b + o_cmom), (double *)(b + o_acc)};
+    hc[0] = BkHostCat{N + N_r, n_k, n_cc, R0, k_edges, (double *)(b + o_cmom), (double *)(b + o_acc), N,
+                      partial ? nullptr : DD};
     if ((hs = bk_run<T>(cats, hc, pl, b, st)) != HIP_OK) return hs;
     double *acc = (double *)(b + o_acc);
     double *B = (double *)(b + o_b);
@@ -763,7 +740,6 @@ template <typename T>
 static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStream_t st, int dev)
 {
     Workspace &ws = hip_workspace(dev);
-    const int pgrid = hip_power_grid<T>();
     struct Lay {
         int n_c, n_cells, n_k, n_e;
         bool dpos, dw, drp;
@@ -806,11 +782,6 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
         y.n_cc = hip_bk_intervals(c.R0, c.k_edges[c.n_k]);
         y.o_cmom = cv.take(sizeof(double) * y.n_cc * HIP_BK_NM);
     }
-    const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * ne_max);
-    size_t pm_bytes = 256;  // the S passes run one after another in stream order and share this scratch
-    for (int i = 0; i < nc; ++i)
-        pm_bytes = std::max(pm_bytes, s_pass_scratch(cats[i].R0, cats[i].k_edges, cats[i].n_k, sizeof(T) == 4));
-    const size_t o_pm = cv.take(pm_bytes);
     int ncc_max = 1;
     size_t cc_bytes = 256;
     long long total = 0;
@@ -881,8 +852,7 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
         std::memcpy(herr, &hsm[(size_t)i * 6 + 5], sizeof(herr));
         if (herr[0] || herr[1]) return HIP_ERR_NONFINITE;
     }
-    // S^a of every catalog: the l = 0 power pair sum (one launch each; the
-    // partial rows are reused in stream order)
+    // per catalog: W~^a, the a_lm-pass descriptor (S^a comes from the a_lm pass)
     std::vector<BkCat<T>> bcats(nc);
     std::vector<BkHostCat> hcs(nc);
     for (int i = 0; i < nc; ++i) {
@@ -893,24 +863,13 @@ static hip_status bispec_batched_impl(const hip_bcatalog *cats, int nc, cudaStre
         int *counter = (int *)(small + 6);
         HIP_CK(cudaMemsetAsync(npairs, 0, 3 * sizeof(unsigned long long), st), "memset");
         HIP_CK(cudaMemsetAsync(counter, 0, sizeof(int), st), "memset");
-        PowerKernelArgs ka;
-        ka.n_e = y.n_e;
-        ka.los = 2;
-        ka.p0 = 0;
-        ka.p1 = c.N;
-        ka.n_items = y.n_cells * HIP_NSHIFT;
-        ka.n_part = c.N;
-        ka.work_counter = counter;
-        ka.partials = (double *)(b + o_pp);
-        ka.npairs = npairs;
-        HIP_CK(s_pass<T>(dcl[i], ka, c.k_edges, c.n_k, c.R0, c.L, small, (double *)(b + y.o_wt),
-                         (double *)(b + y.o_dd), (double *)(b + y.o_p), b + o_pm, pgrid, st),
-               "pair pass (S)");
+        // S^a comes from the a_lm pass (hip_bk_s_sum); W~^a here
+        HIP_CK(hip_window_transform(y.n_e, c.k_edges, c.R0, (double *)(b + y.o_wt), st), "window transform");
         bcats[i] = bk_cat<T>(dcl[i], rcl[i], (const int *)(b + y.o_dsc), (const int *)(b + y.o_rsc), c.N, c.N_r,
                              nullptr, c.k_edges, c.n_k, c.R0, -hsm[(size_t)i * 6] / (double)c.N_r, npairs + 1,
                              (double *)(b + y.o_cmom));
         hcs[i] = BkHostCat{c.N + c.N_r, c.n_k, y.n_cc, c.R0, c.k_edges, (double *)(b + y.o_cmom),
-                           (double *)(b + y.o_acc)};
+                           (double *)(b + y.o_acc), c.N, (double *)(b + y.o_dd)};
     }
     if ((hs = bk_run<T>(bcats, hcs, pl, b, st)) != HIP_OK) return hs;
     std::vector<std::vector<double>> hB(nc);
@@ -978,7 +937,6 @@ static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t
     const int n_c = hip_cells_per_side(L, R0), n_cells = n_c * n_c * n_c;
     const int n_c2 = hip_cells_per_side(L, 2.0 * R0), n_cells2 = n_c2 * n_c2 * n_c2;
     const int n_e = n_k + 1;
-    const int pgrid = hip_power_grid<T>();
     const bool dpos = hip_is_device_ptr(pos), dw = w && hip_is_device_ptr(w);
     const size_t tsz = (size_t)(HIP_LMAX + 1) * n_k * n_k;
     const int n_cc = hip_bk_intervals(R0, k_edges[n_k]);
@@ -995,14 +953,12 @@ static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t
     const size_t o_x2 = cv.take(sizeof(float) * N), o_y2 = cv.take(sizeof(float) * N), o_z2 = cv.take(sizeof(float) * N);
     const size_t o_w2 = cv.take(sizeof(float) * N), o_i2 = cv.take(sizeof(int) * N), o_c2 = cv.take(sizeof(int) * N);
     const size_t o_s2 = cv.take(sizeof(int) * (n_cells2 + 1)), o_f2 = cv.take(sizeof(int) * n_cells2);
-    const size_t o_pp = cv.take(sizeof(double) * (size_t)pgrid * 3 * n_e);
     const size_t o_acc = cv.take(sizeof(double) * 2 * tsz);  // [0] primary sum, [1] the E^II row
     const size_t o_cmom = cv.take(sizeof(double) * n_cc * HIP_BK_NM);
     const size_t o_small = cv.take(sizeof(double) * 16);
     const size_t o_wt = cv.take(sizeof(double) * n_k), o_dd = cv.take(sizeof(double) * 3 * n_k);
     const size_t o_p = cv.take(sizeof(double) * 3 * n_k), o_b = cv.take(sizeof(double) * tsz);
     const size_t o_e2 = cv.take(hip_e2_scratch_bytes(nodes, n_k));
-    const size_t o_pm = cv.take(s_pass_scratch(R0, k_edges, n_k, sizeof(T) == 4));
     const BkPlan pl = bk_plan<T>(cv, 1, n_k, n_cc, N, hip_bk_cterm_scratch_bytes(n_cc, n_k));
     hip_status hs = ws.reserve(cv.total, st);
     if (hs != HIP_OK) return hs;
@@ -1047,25 +1003,16 @@ static hip_status bispec_analytic_impl(const float *pos, const float *w, int64_t
     CellList<T> dcl{dx, dy, dz, (const float *)(b + o_dw), (const int *)(b + o_didx), dstart, n_c, L, L / n_c};
     HIP_CK(cudaMemsetAsync(npairs, 0, 3 * sizeof(unsigned long long), st), "memset");
     HIP_CK(cudaMemsetAsync(counter, 0, 3 * sizeof(int), st), "memset");
-    PowerKernelArgs ka;
-    ka.n_e = n_e;
-    ka.los = 2;
-    ka.p0 = 0;
-    ka.p1 = N;
-    ka.n_items = n_cells * HIP_NSHIFT;
-    ka.n_part = N;
-    ka.work_counter = counter;
-    ka.partials = (double *)(b + o_pp);
-    ka.npairs = npairs;
-    double *Wt = (double *)(b + o_wt), *DD = (double *)(b + o_dd), *P = (double *)(b + o_p);
-    HIP_CK(s_pass<T>(dcl, ka, k_edges, n_k, R0, L, S1, Wt, DD, P, b + o_pm, pgrid, st), "pair pass (S)");
+    double *Wt = (double *)(b + o_wt), *DD = (double *)(b + o_dd);
+    // S^a comes from the a_lm pass (hip_bk_s_sum); W~^a here
+    HIP_CK(hip_window_transform(n_e, k_edges, R0, Wt, st), "window transform");
 
     // the data primaries' sum (no random primaries)
     std::vector<BkCat<T>> cats(1, bk_cat<T>(dcl, dcl, (const int *)(b + o_dsc), (const int *)(b + o_dsc), N, 0,
                                             nullptr, k_edges, n_k, R0, 0.0, npairs + 1, (double *)(b + o_cmom)));
     std::vector<BkHostCat> hc(1);
     double *acc = (double *)(b + o_acc);
-    hc[0] = BkHostCat{N, n_k, n_cc, R0, k_edges, (double *)(b + o_cmom), acc};
+    hc[0] = BkHostCat{N, n_k, n_cc, R0, k_edges, (double *)(b + o_cmom), acc, N, DD};
     if ((hs = bk_run<T>(cats, hc, pl, b, st)) != HIP_OK) return hs;
     CellList<float> cl2{(const float *)(b + o_x2), (const float *)(b + o_y2), (const float *)(b + o_z2),
                         (const float *)(b + o_w2), (const int *)(b + o_i2), (const int *)(b + o_s2), n_c2, L,

@@ -53,6 +53,45 @@ cudaError_t hip_upload_coeffs_bispec()
     return cudaSuccess;
 }
 
+// blockIdx.y = segment; warp w of block x takes data primaries x * 8 + w, stepping
+// by gridDim.x * 8, lane l the bins l and l + 32 (n_k <= 64); the block's sums go
+// to S with one FP64 atomic per bin.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bk_s_sum(const BkSeg *__restrict__ segs)
+{
+    __shared__ double red[8][64];
+    const BkSeg sg = segs[blockIdx.y];
+    if (!sg.S) return;  // block-uniform
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nk = sg.n_k;
+    const T *X = (const T *)sg.X, *sp = (const T *)sg.sp;
+    double s0 = 0.0, s1 = 0.0;
+    for (int p = blockIdx.x * 8 + warp; p < sg.n_d; p += gridDim.x * 8) {
+        const T w = sp[p];  // 0 for an excluded primary, whose row of X is not written
+        if (w == T(0)) continue;
+        const T *row = X + (size_t)p * HIP_NLM * nk;  // harmonic (0, 0): R_00 = 1
+        if (lane < nk) s0 += (double)w * (double)row[lane];
+        if (lane + 32 < nk) s1 += (double)w * (double)row[lane + 32];
+    }
+    red[warp][lane] = s0;
+    red[warp][lane + 32] = s1;
+    __syncthreads();
+    if (threadIdx.x < 64 && threadIdx.x < nk) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
+        if (t != 0.0) atomicAdd(&sg.S[threadIdx.x], t);
+    }
+}
+
+template <typename T>
+cudaError_t hip_bk_s_sum(const BkSeg *segs, int n_segs, int, cudaStream_t st)
+{
+    k_bk_s_sum<T><<<dim3(1216, n_segs), 256, 0, st>>>(segs);
+    return cudaGetLastError();
+}
+template cudaError_t hip_bk_s_sum<float>(const BkSeg *, int, int, cudaStream_t);
+template cudaError_t hip_bk_s_sum<double>(const BkSeg *, int, int, cudaStream_t);
+
 int hip_bk_intervals(double R0, double k_max)
 {
     const double q = std::ceil(R0 * k_max / 8.0);

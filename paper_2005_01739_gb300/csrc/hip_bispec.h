@@ -72,6 +72,8 @@ struct BkSeg {
     int n_p, n_k;
     int stage_begin, stage_end;  // tensor-core path: stages of P primaries [begin, end)
     double *acc;               // [5][n_k][n_k] FP64 primary sum (atomically added)
+    int n_d;                   // the first n_d primaries are data primaries
+    double *S;                 // [n_k] S^a += sum over them of s_p A^a_00 (null: not wanted)
 };
 
 // Primaries per tensor-core stage for a launch whose largest n_k is nk_max.
@@ -89,6 +91,12 @@ cudaError_t hip_bk_contract_tc(const BkSeg *segs, int n_segs, int n_stages, int 
 // the segments' primaries (n_total of them) laid end to end.
 template <typename T>
 cudaError_t hip_bk_contract_f64(const BkSeg *segs, int n_segs, long long n_total, int nk_max, cudaStream_t st);
+
+// S^a = sum over data primaries p of w_p A^a_00(p): the ordered data pair sum
+// sum_{p != j} w_p w_j W j^a_0 (R_00 = 1), i.e. the l = 0 power pair sum DD^a_0
+// that the summary estimator of Sec. 4.5 subtracts, read from X (FP64 sums).
+template <typename T>
+cudaError_t hip_bk_s_sum(const BkSeg *segs, int n_segs, int nk_max, cudaStream_t st);
 
 // acc[l][a][b] -= sum over the C-term moments of one catalog (FP64).
 struct BkCTerm {

@@ -7,6 +7,7 @@
 #include "../../include/hipster_gb300.h"
 #include "hip_math.cuh"
 
+#define HIP_MAX_CELLS_SIDE 128  // most cells per side of a cell list
 #define HIP_MAX_EDGES (HIP_MAX_BINS + 1)
 #define HIP_PAIR_THREADS 128
 #define HIP_PAIR_WARPS (HIP_PAIR_THREADS / 32)
@@ -151,3 +152,5 @@ int hip_power_grid();
 cudaError_t hip_power_finalize(const double *partials, int nparts, int n_e, int n_ell, const double *kedges_host,
                                double R0, double L, const double *S1, double *Wt, double *DD, double *P,
                                cudaStream_t st);
+// W~^a alone (n_e edges, host array), into Wt [n_e - 1] on the device.
+cudaError_t hip_window_transform(int n_e, const double *kedges_host, double R0, double *Wt, cudaStream_t st);

@@ -306,6 +306,28 @@ __host__ __device__ __forceinline__ void hip_F_f32(float u, const HipCoeffs &C, 
 // Unlike hip_F_f32 (the power spectrum's direct pass, held to 1e-5 on sums of
 // 1e9 pairs) there is no low-order correction chain: the bispectrum's budget is
 // 1e-4.
+#ifdef __CUDA_ARCH__
+// sin and cos of u >= 0 for the bispectrum's edge functions: Cody-Waite reduction
+// u = k pi/2 + x with pi/2 split into three floats (A + B + C, each product k A,
+// k B, k C taken exactly inside an FMA; reduction error < 3e-8 for u < 1500), then
+// the hardware approximations on |x| <= pi/4 (absolute error below 4e-7 there),
+// and the quadrant k mod 4.  Cheaper than sincosf, whose full-range accuracy the
+// 1e-4 budget of B does not need.
+__device__ __forceinline__ void hip_sincos_b32(float u, float *s, float *c)
+{
+    const float k = rintf(u * 0.636619746685028f);  // 2 / pi
+    float x = fmaf(k, -1.5707963705062866f, u);
+    x = fmaf(k, 4.371138828673793e-08f, x);
+    x = fmaf(k, 1.7151245100058819e-15f, x);
+    const float sx = __sinf(x), cx = __cosf(x);
+    const int q = (int)k & 3;
+    *s = (q & 1) ? cx : sx;
+    *c = (q & 1) ? sx : cx;
+    if (q == 1 || q == 2) *c = -*c;
+    if (q >= 2) *s = -*s;
+}
+#endif
+
 __host__ __device__ __forceinline__ void hip_F_b32(float u, const HipCoeffs &C, float *F)
 {
     if (u < HIP_FB_U) {
@@ -323,7 +345,7 @@ __host__ __device__ __forceinline__ void hip_F_b32(float u, const HipCoeffs &C, 
     }
     float s, c;
 #ifdef __CUDA_ARCH__
-    sincosf(u, &s, &c);
+    hip_sincos_b32(u, &s, &c);
     const float w = __fdividef(1.0f, u);
 #else
     s = sinf(u);

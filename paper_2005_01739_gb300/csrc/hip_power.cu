@@ -5,6 +5,7 @@
 // normalises and subtracts W~^a.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
 #include "hip_internal.h"
 #include "hip_moments.h"
@@ -32,10 +33,42 @@ __device__ __forceinline__ double hip_wrap(double v, double L)
     return v;
 }
 
-__global__ void k_cell_count(const float *__restrict__ pos, const float *__restrict__ w, long long N, double L,
-                             int n_c, double inv_cs, int *__restrict__ cid, int *__restrict__ count, double *S1,
-                             int *err)
+// Box and cell geometry of a build: FP64 values and their FP32 companions.
+struct CellGeom {
+    double L, cs, inv_cs;
+    float Lf_lo;     // largest float below L: 0 <= p <= Lf_lo  <=>  p in [0, L)
+    float inv_cs_f;  // (float)(1 / cs)
+    int n_c;
+};
+
+// Cell index along one axis of the FP32 coordinate p, by the FP64 rule
+// floor(v / cs) (clamped to n_c - 1) with v = p wrapped into [0, L).  For p
+// already in [0, L) (v = p) the index comes from an FP32 product, which is
+// within 1.5e-5 of p / cs (p exact, 1/cs and the product rounded, p / cs < 128);
+// only when it lies within 4e-5 of an integer does the FP64 product decide, so
+// the index is the FP64 rule's at FP32 cost.  Other coordinates take the FP64
+// wrap; *wrapped says which way v was formed.
+__device__ __forceinline__ int hip_cell_axis(float p, const CellGeom &g, double &v, bool &wrapped)
 {
+    int ic;
+    if (p >= 0.0f && p <= g.Lf_lo) {
+        const float y = p * g.inv_cs_f;
+        ic = (int)y;
+        const float fr = y - (float)ic;
+        if (fr < 4e-5f || fr > 0.99996f) ic = (int)((double)p * g.inv_cs);
+        wrapped = false;
+    } else {
+        v = hip_wrap((double)p, g.L);
+        ic = (int)(v * g.inv_cs);
+        wrapped = true;
+    }
+    return ic >= g.n_c ? g.n_c - 1 : ic;
+}
+
+__global__ void k_cell_count(const float *__restrict__ pos, const float *__restrict__ w, long long N, CellGeom g,
+                             int *__restrict__ cid, int *__restrict__ count, double *S1, int *err)
+{
+    const int n_c = g.n_c;
     double wsum = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         float px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
@@ -49,9 +82,9 @@ __global__ void k_cell_count(const float *__restrict__ pos, const float *__restr
         float pv[3] = {px, py, pz};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double v = hip_wrap((double)pv[k], L);
-            int ic = (int)(v * inv_cs);
-            c3[k] = ic >= n_c ? n_c - 1 : ic;
+            double v;
+            bool wr;
+            c3[k] = hip_cell_axis(pv[k], g, v, wr);
         }
         int id = (c3[0] * n_c + c3[1]) * n_c + c3[2];
         cid[i] = id;
@@ -97,26 +130,34 @@ __global__ void __launch_bounds__(1024) k_cell_scan(const int *count, int n, int
 }
 
 template <typename T>
-__global__ void k_cell_scatter(const float *__restrict__ pos, const float *__restrict__ w, long long N, double L,
-                               int n_c, double cs, double inv_cs, const int *__restrict__ cid,
-                               const int *__restrict__ start, int *__restrict__ fill, T *__restrict__ x,
-                               T *__restrict__ y, T *__restrict__ z, float *__restrict__ ws, int *__restrict__ idx)
+__global__ void k_cell_scatter(const float *__restrict__ pos, const float *__restrict__ w, long long N, CellGeom g,
+                               const int *__restrict__ cid, const int *__restrict__ start, int *__restrict__ fill,
+                               T *__restrict__ x, T *__restrict__ y, T *__restrict__ z, float *__restrict__ ws,
+                               int *__restrict__ idx)
 {
+    // FP32 lists: the float cell origins, so that the offset of an unwrapped
+    // coordinate is one exact FP32 subtraction (Sterbenz)
+    __shared__ float s_org[HIP_MAX_CELLS_SIDE];
+    for (int c = threadIdx.x; c < g.n_c; c += blockDim.x) s_org[c] = (float)hip_cell_origin<float>(c, g.cs);
+    __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         int id = cid[i];
         int slot = start[id] + atomicAdd(&fill[id], 1);
         float pv[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-        double loc[3];
+        T loc[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double v = hip_wrap((double)pv[k], L);
-            int ic = (int)(v * inv_cs);
-            ic = ic >= n_c ? n_c - 1 : ic;
-            loc[k] = v - hip_cell_origin<T>(ic, cs);
+            double v;
+            bool wr;
+            const int ic = hip_cell_axis(pv[k], g, v, wr);
+            if (sizeof(T) == 4 && !wr)
+                loc[k] = T(pv[k] - s_org[ic]);
+            else
+                loc[k] = (T)((wr ? v : (double)pv[k]) - hip_cell_origin<T>(ic, g.cs));
         }
-        x[slot] = (T)loc[0];
-        y[slot] = (T)loc[1];
-        z[slot] = (T)loc[2];
+        x[slot] = loc[0];
+        y[slot] = loc[1];
+        z[slot] = loc[2];
         ws[slot] = w ? w[i] : 1.0f;
         idx[slot] = (int)i;
     }
@@ -136,10 +177,17 @@ cudaError_t hip_build_cells(const float *pos, const float *w, int64_t N, double 
     int blocks = (int)((N + 255) / 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_cell_count<<<blocks, 256, 0, st>>>(pos, w, N, L, n_c, 1.0 / cs, cid, cell_fill, S1, err);
+    CellGeom g;
+    g.L = L;
+    g.cs = cs;
+    g.inv_cs = 1.0 / cs;
+    g.inv_cs_f = (float)g.inv_cs;
+    g.Lf_lo = (float)L;
+    if ((double)g.Lf_lo >= L) g.Lf_lo = std::nextafter(g.Lf_lo, 0.0f);
+    g.n_c = n_c;
+    k_cell_count<<<blocks, 256, 0, st>>>(pos, w, N, g, cid, cell_fill, S1, err);
     k_cell_scan<<<1, 1024, 0, st>>>(cell_fill, n_cells, cell_start, cell_fill);
-    k_cell_scatter<T><<<blocks, 256, 0, st>>>(pos, w, N, L, n_c, cs, 1.0 / cs, cid, cell_start, cell_fill, x, y, z,
-                                              ws, idx);
+    k_cell_scatter<T><<<blocks, 256, 0, st>>>(pos, w, N, g, cid, cell_start, cell_fill, x, y, z, ws, idx);
     return cudaGetLastError();
 }
 
@@ -390,5 +438,15 @@ cudaError_t hip_power_finalize(const double *partials, int nparts, int n_e, int 
     gl16(f.glx, f.glw);
     k_window_transform<<<n_e - 1, 256, 0, st>>>(f, R0, Wt);
     k_power_final<<<1, 1024, 0, st>>>(f, partials, nparts, n_e, n_ell, L, S1, Wt, DD, P);
+    return cudaGetLastError();
+}
+
+cudaError_t hip_window_transform(int n_e, const double *kedges_host, double R0, double *Wt, cudaStream_t st)
+{
+    FinalArgs f;
+    std::memset(&f, 0, sizeof(f));
+    for (int e = 0; e < HIP_MAX_EDGES; ++e) f.k[e] = e < n_e ? kedges_host[e] : 0.0;
+    gl16(f.glx, f.glw);
+    k_window_transform<<<n_e - 1, 256, 0, st>>>(f, R0, Wt);
     return cudaGetLastError();
 }
