@@ -144,11 +144,12 @@ def _workload(rank: int, scale: float = 1.0):
     return wl
 
 
-def _config(wl, nranks):
+def _config(wl, nranks, shard=False):
     return {"workload": WORKLOAD, "N": int(len(wl["pos"])), "L": wl["L"], "R0": wl["R0"],
             "n_k": int(len(wl["edges"]) - 1), "k_range": [float(wl["edges"][0]), float(wl["edges"][-1])],
             "ell": [0, 2, 4], "weights": "U(0.5,1.5)", "catalog": "Thomas process, 5e4 parents, sigma 1.5",
-            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas{nranks}"}
+            "l2": "flushed between timed steps (512 MB write)",
+            "parallelism": f"{'shard' if shard else 'replicas'}{nranks}"}
 
 
 def combine_ranks(ms: float, work: float, device: str):
@@ -163,6 +164,22 @@ def combine_ranks(ms: float, work: float, device: str):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(w, op=dist.ReduceOp.SUM)
     return float(t.item()), float(w.item())
+
+
+def shard_range(rank: int, world: int, n: int):
+    """Primary range [p0, p1) of one rank when a catalog is sharded by primaries."""
+    return rank * n // world, (rank + 1) * n // world
+
+
+def combine_shards(DD, device: str):
+    """Sum over ranks of the partial ordered pair sums DD [n_ell, n_k] of disjoint
+    primary ranges (one FP64 all-reduce); their sum is the catalog's full DD."""
+    import torch
+    import torch.distributed as dist
+    t = torch.as_tensor(np.ascontiguousarray(DD, dtype=np.float64), device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.cpu().numpy()
 
 
 def oracle_sample(wl, seconds: float):
@@ -575,18 +592,30 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     binding.load()
-    wl = _workload(rank, args.scale)
+    shard = ws > 1 and args.multi == "shard"
+    # sharded: every rank holds the one catalog and takes a primary range; replicas:
+    # every rank its own catalog of the same size (another seed)
+    wl = _workload(0 if shard else rank, args.scale)
     L, R0, edges = wl["L"], wl["R0"], wl["edges"]
     nk = len(edges) - 1
     stream = torch.cuda.Stream()
     dpos = torch.from_numpy(wl["pos"]).cuda()
     dw = torch.from_numpy(wl["w"]).cuda()
+    prim = shard_range(rank, ws, len(wl["pos"])) if shard else None
+    S1 = float(np.sum(wl["w"], dtype=np.float64))
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     binding.set_profiling(True)
 
-    def step():
+    def call(pos, w):
         with torch.cuda.stream(stream):
-            return binding.hip_power(dpos, dw, L, R0, edges, 4, 2, "mixed", stream=stream)
+            P, DD, npairs = binding.hip_power(pos, w, L, R0, edges, 4, 2, "mixed", prim_range=prim, stream=stream)
+        if shard:  # the one exchange of the path: the FP64 sum of the partial DD, then P on rank 0
+            DD = combine_shards(DD, "cuda")
+            P = binding.hip_power_from_pairs(DD, L, R0, edges, S1, stream=stream) if rank == 0 else None
+        return P, DD, npairs
+
+    def step():
+        return call(dpos, dw)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -624,7 +653,7 @@ def run_ours(args):
     for i in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        binding.hip_power(hpos, hw, L, R0, edges, 4, 2, "mixed", stream=stream)
+        call(hpos, hw)
         e2e_t.append(time.perf_counter() - t0)
     e2e_ms = 1e3 * float(np.mean(e2e_t))
     e2e_max, _ = combine_ranks(e2e_ms, 0.0, "cuda")
@@ -673,8 +702,9 @@ def run_ours(args):
         oracle.set_threads(nthr)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": _config(wl, ws),
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "strong" if shard else "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": _config(wl, ws, shard),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_max},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -712,6 +742,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--multi", choices=["shard", "replicas"], default="shard",
+                    help="N > 1: shard the catalog's primaries over the ranks (one FP64 all-reduce of DD) "
+                         "or run one catalog per rank")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")

@@ -81,6 +81,25 @@ hip_status hip_power(const float *pos, const float *w, int64_t N, double L, doub
                      int64_t prim_begin, int64_t prim_end, double *P_out, double *DD_out, int64_t *npairs_out,
                      void *cuda_stream);
 
+/* P^a_l from ordered pair sums DD^a_l that the caller has added up, e.g. the
+ * DD_out of hip_power calls over disjoint primary ranges of one catalog run on
+ * several devices or processes (their sum is the full DD of Sec. 3):
+ *
+ *   P^a_l = (-i)^l (2l+1) / (n_w^2 V) * DD^a_l  -  delta_l0 W~^a(R0),  n_w = S1 / L^3,
+ *
+ * the normalisation and W~^a (Eq. wka-def) of hip_power, in FP64 on the device.
+ *
+ *   DD         [(ell_max/2+1) * n_k] float64 host, row-major (l, a)
+ *   n_k, ell_max, L, R0, window, k_edges   as for hip_power (the same values)
+ *   S1         sum of the weights of the WHOLE catalog (N for unit weights), != 0
+ *   P_out      [(ell_max/2+1) * n_k] float64 host
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
+ *
+ * Returns HIP_ERR_ARG / HIP_ERR_RANGE for invalid arguments, HIP_ERR_NONFINITE
+ * if DD holds a non-finite value; synchronises the stream. */
+hip_status hip_power_from_pairs(const double *DD, int n_k, int ell_max, double L, double R0, hip_window window,
+                                const double *k_edges, double S1, double *P_out, void *cuda_stream);
+
 /* Isotropic bispectrum multipoles of a periodic box, Sec. 4 of the paper (the
  * summary estimator of Sec. 4.5):
  *

@@ -68,6 +68,8 @@ def load(path: str | None = None):
         L.hip_bispectrum.argtypes = [P, P, i64, P, i64, d, d, i, P, i, i, i, P, P, P]
         L.hip_power_noalloc.restype = i
         L.hip_power_noalloc.argtypes = [P, P, i64, d, d, i, P, i, i, i, i64, i64, P, P, P, P]
+        L.hip_power_from_pairs.restype = i
+        L.hip_power_from_pairs.argtypes = [P, i, i, d, d, i, P, d, P, P]
         L.hip_window_omega.restype = i
         L.hip_window_omega.argtypes = [P, i, d, i, P, i, P, P]
         L.hip_subsample.restype = i
@@ -174,6 +176,22 @@ def hip_power(pos, w, L, R0, k_edges, ell_max=4, los_axis=2, prec="mixed", prim_
     _check(lib, rc, "hip_power")
     del keep_p, keep_w
     return P, DD, int(npairs.value)
+
+
+def hip_power_from_pairs(DD, L, R0, k_edges, S1, stream=None):
+    """P^a_l from summed ordered pair sums DD [n_ell, n_k] (e.g. the DD of
+    hip_power calls over disjoint primary ranges, added up); S1 = the sum of the
+    whole catalog's weights.  Returns P [n_ell, n_k] float64."""
+    lib = load()
+    DD = np.ascontiguousarray(np.asarray(DD, dtype=np.float64))
+    n_ell, n_k = DD.shape
+    edges = np.ascontiguousarray(np.asarray(k_edges, dtype=np.float64))
+    P = np.zeros((n_ell, n_k))
+    rc = lib.hip_power_from_pairs(DD.ctypes.data_as(ctypes.c_void_p), n_k, 2 * (n_ell - 1), float(L), float(R0), 0,
+                                  edges.ctypes.data_as(ctypes.c_void_p), float(S1), P.ctypes.data_as(ctypes.c_void_p),
+                                  _stream_handle(stream))
+    _check(lib, rc, "hip_power_from_pairs")
+    return P
 
 
 def hip_window_omega(k_edges, R0, lmax, p, stream=None):

@@ -320,6 +320,51 @@ extern "C" hip_status hip_power(const float *pos, const float *w, int64_t N, dou
                               DD_out, npairs_out, st, dev);
 }
 
+// ------------------------------------------------ hip_power_from_pairs ----
+extern "C" hip_status hip_power_from_pairs(const double *DD, int n_k, int ell_max, double L, double R0,
+                                           hip_window window, const double *k_edges, double S1, double *P_out,
+                                           void *cuda_stream)
+{
+    g_errbuf[0] = 0;
+    if (!DD || !P_out) return HIP_ERR_ARG;
+    if (window != HIP_WINDOW_PHILCOX) return HIP_ERR_ARG;
+    if (ell_max != 0 && ell_max != 2 && ell_max != 4) return HIP_ERR_ARG;
+    if (!(L > 0.0) || !std::isfinite(L) || !(R0 > 0.0) || !(R0 < 0.5 * L)) return HIP_ERR_RANGE;
+    if (!std::isfinite(S1) || S1 == 0.0) return HIP_ERR_RANGE;
+    hip_status hs = hip_check_edges(k_edges, n_k);
+    if (hs != HIP_OK) return hs;
+    const int n_ell = ell_max / 2 + 1;
+    for (int i = 0; i < n_ell * n_k; ++i)
+        if (!std::isfinite(DD[i])) return HIP_ERR_NONFINITE;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    int dev = 0;
+    if ((hs = hip_device_setup(&dev)) != HIP_OK) return hs;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    Workspace &ws = hip_workspace(dev);
+    Carve cv;
+    const size_t o_dd = cv.take(sizeof(double) * n_ell * n_k), o_wt = cv.take(sizeof(double) * n_k);
+    const size_t o_p = cv.take(sizeof(double) * n_ell * n_k);
+    if ((hs = ws.reserve(cv.total, st)) != HIP_OK) return hs;
+    char *b = (char *)ws.base;
+    cudaError_t e;
+#define HIP_CK(call, what)                                                                                           \
+    do {                                                                                                             \
+        if ((e = (call)) != cudaSuccess) {                                                                           \
+            set_err(what, e);                                                                                        \
+            return HIP_ERR_CUDA;                                                                                     \
+        }                                                                                                            \
+    } while (0)
+    HIP_CK(cudaMemcpyAsync(b + o_dd, DD, sizeof(double) * n_ell * n_k, cudaMemcpyHostToDevice, st), "H2D DD");
+    HIP_CK(hip_window_transform(n_k + 1, k_edges, R0, (double *)(b + o_wt), st), "window transform");
+    HIP_CK(hip_power_from_dd((const double *)(b + o_dd), n_k, n_ell, L, S1, (const double *)(b + o_wt),
+                             (double *)(b + o_p), st),
+           "finalize");
+    HIP_CK(cudaMemcpyAsync(P_out, b + o_p, sizeof(double) * n_ell * n_k, cudaMemcpyDeviceToHost, st), "D2H P");
+    HIP_CK(cudaStreamSynchronize(st), "stream sync");
+#undef HIP_CK
+    return HIP_OK;
+}
+
 // ------------------------------------------------ the bispectrum primary sum ----
 // Scratch plan of the B pass for catalogs whose largest n_k, n_cc are nk_max,
 // ncc_max and whose primaries (data then randoms, catalogs end to end) number

@@ -154,3 +154,6 @@ cudaError_t hip_power_finalize(const double *partials, int nparts, int n_e, int 
                                cudaStream_t st);
 // W~^a alone (n_e edges, host array), into Wt [n_e - 1] on the device.
 cudaError_t hip_window_transform(int n_e, const double *kedges_host, double R0, double *Wt, cudaStream_t st);
+// P [n_ell][n_k] from summed DD [n_ell][n_k] and W~ (device arrays), S1 = sum of all weights.
+cudaError_t hip_power_from_dd(const double *DD, int n_k, int n_ell, double L, double S1, const double *Wt, double *P,
+                              cudaStream_t st);

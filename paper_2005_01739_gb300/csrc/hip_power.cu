@@ -441,6 +441,27 @@ cudaError_t hip_power_finalize(const double *partials, int nparts, int n_e, int 
     return cudaGetLastError();
 }
 
+// P^a_l from summed ordered pair sums DD^a_l (the same normalisation as k_power_final).
+__global__ void k_power_from_dd(const double *__restrict__ DD, int n_k, int n_ell, double L, double S1,
+                                const double *__restrict__ Wt, double *__restrict__ P)
+{
+    const double V = L * L * L, nw = S1 / V;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_ell * n_k; i += gridDim.x * blockDim.x) {
+        const int il = i / n_k, a = i - il * n_k;
+        const double sign = (il & 1) ? -1.0 : 1.0;
+        double p = sign * (4.0 * il + 1.0) * DD[i] / (nw * nw * V);
+        if (il == 0) p -= Wt[a];
+        P[i] = p;
+    }
+}
+
+cudaError_t hip_power_from_dd(const double *DD, int n_k, int n_ell, double L, double S1, const double *Wt, double *P,
+                              cudaStream_t st)
+{
+    k_power_from_dd<<<1, 256, 0, st>>>(DD, n_k, n_ell, L, S1, Wt, P);
+    return cudaGetLastError();
+}
+
 cudaError_t hip_window_transform(int n_e, const double *kedges_host, double R0, double *Wt, cudaStream_t st)
 {
     FinalArgs f;

@@ -311,3 +311,18 @@ def test_mixed_wide_weight_range(scale):
     P, _, npairs = binding.hip_power(_dev(pos), _dev(w), L, R0, edges, 4, 2, "mixed")
     _same_count("mixed", npairs, nref)
     assert _err(P, Pref, "scale %g" % scale) < TOL["mixed"]
+
+
+def test_power_from_pairs_of_primary_shards():
+    # P from the summed DD of disjoint primary ranges (the sharded path's one
+    # exchange) equals the oracle's P of the whole catalog
+    pos, w, L, R0, edges = _dense_case()
+    Pref, _, _, _ = _oracle_P("dense", pos, w, L, R0, edges)
+    dpos, dw = _dev(pos), _dev(w)
+    n = len(pos)
+    S1 = float(np.sum(w, dtype=np.float64))
+    for prec in ("fp64", "mixed"):
+        DD = sum(binding.hip_power(dpos, dw, L, R0, edges, 4, 2, prec, prim_range=r)[1]
+                 for r in ((0, n // 3), (n // 3, n // 2), (n // 2, n)))
+        P = binding.hip_power_from_pairs(DD, L, R0, edges, S1)
+        assert _err(P, Pref, prec) < TOL[prec]
