@@ -351,22 +351,38 @@ def batched_summary(binding, stream, steps: int = 2, fp64: bool = True, bispectr
         c["pos"] = torch.from_numpy(c["pos"]).cuda()
         c["w"] = torch.from_numpy(c["w"]).cuda()
     plan = binding.BatchPlan(cats, "mixed", stream=stream)
-    res = plan.run(stream)
-    ts = []
-    with ClockSampler(torch.cuda.current_device()) as clk:
+
+    def replays():
+        ts = []
         for _ in range(steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            res = plan.run(stream)
+            r = plan.run(stream)
             b.record(stream)
             b.synchronize()
             ts.append(a.elapsed_time(b))
+        return r, float(np.mean(ts))
+
+    res = plan.run(stream)
+    default_shape = plan.shape()
+    _, ms_default = replays()
+    # the autotuner's second stage (warps per CTA, fold period) on this batch, then the tuned plan is timed
+    chosen, cand = plan.tune_kernel(stream)
+    plan.run(stream)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        res, ms = replays()
     work = sum((n // 2) * (len(c["edges"]) - 1) for c, (_, _, n) in zip(cats, res))
-    ms = float(np.mean(ts))
     out = {"workload": "batched64", "catalogs": len(cats),
            "particles": int(sum(int(c["pos"].shape[0]) for c in cats)), "pair_bins": int(work),
            "value": work / (ms / 1e3), "unit": UNIT, "ms_per_replay": ms, "launches_per_replay": plan.launches,
-           "clocks": clk.summary()}
+           "clocks": clk.summary(),
+           "autotune": {"shape": dict(zip(("particles_per_cell", "warps_per_cta", "fold_pairs"), plan.shape())),
+                        "default_shape": dict(zip(("particles_per_cell", "warps_per_cta", "fold_pairs"),
+                                                  default_shape)),
+                        "default_ms_per_replay": ms_default,
+                        "candidates_ms": {f"warps{w}_fold{f}": v for (w, f), v in cand.items()},
+                        "note": "ms_per_replay is the tuned plan (hip_batch_plan_tune_kernel at the default 64 "
+                                "particles per cell); warps 0 / fold 0 = the defaults (by occupancy / 16384)"}}
     mixed = [(np.array(P), np.array(DD)) for P, DD, _ in res]
     plan.close()
     if fp64:

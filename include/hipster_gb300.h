@@ -237,6 +237,19 @@ hip_status hip_batch_plan_run(hip_batch_plan *plan, void *cuda_stream);
  * that order, in ms.  A new plan starts at occ = 64.  Errors as in
  * hip_batch_plan_run. */
 hip_status hip_batch_plan_tune(hip_batch_plan *plan, void *cuda_stream, int *chosen_out, float *ms_out);
+/* The second stage of the autotuner, at the plan's current cell occupancy: the
+ * moment pass's warps per CTA (4, 8) and the number of pairs a CTA adds to its
+ * FP32 moment sums between folds into FP64 (4096, 8192, 16384), each of the six
+ * shapes timed on one replay after a warm-up, in that order (warps outer) into
+ * ms_out[6] (or NULL); the fastest is kept and reported through warps_out and
+ * fold_out (or NULL).  A new plan starts with warps chosen from its cells'
+ * occupancy and folds every 16384 pairs.  The tile of 128 particles per cell
+ * and the 32-pair drains are fixed.  Errors as in hip_batch_plan_run.
+ * hip_batch_plan_shape reports the plan's current occ, warps (0 = by
+ * occupancy) and fold (0 = 16384). */
+hip_status hip_batch_plan_tune_kernel(hip_batch_plan *plan, void *cuda_stream, int *warps_out, int *fold_out,
+                                      float *ms_out);
+void hip_batch_plan_shape(const hip_batch_plan *plan, int *occ, int *warps, int *fold);
 void hip_batch_plan_destroy(hip_batch_plan *plan);
 int hip_batch_plan_launches(const hip_batch_plan *plan);
 hip_status hip_power_batched(const hip_catalog *cats, int n_cats, hip_precision prec, void *cuda_stream);

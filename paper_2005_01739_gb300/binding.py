@@ -92,6 +92,10 @@ def load(path: str | None = None):
         L.hip_batch_message.argtypes = []
         L.hip_batch_plan_tune.restype = i
         L.hip_batch_plan_tune.argtypes = [P, P, P, P]
+        L.hip_batch_plan_tune_kernel.restype = i
+        L.hip_batch_plan_tune_kernel.argtypes = [P, P, P, P, P]
+        L.hip_batch_plan_shape.restype = None
+        L.hip_batch_plan_shape.argtypes = [P, P, P, P]
         L.hip_bispectrum_analytic.restype = i
         L.hip_bispectrum_analytic.argtypes = [P, P, i64, d, d, i, P, i, i, i, P, P, P]
         L.hip_bispectrum_batched.restype = i
@@ -319,6 +323,26 @@ class BatchPlan:
             raise HipError(rc, f"hip_batch_plan_tune: {self._lib.hip_status_string(rc).decode()} "
                                f"({self._lib.hip_batch_message().decode()})")
         return int(chosen.value), dict(zip((4, 8, 16, 32, 64, 128, 256, 0), (float(x) for x in ms)))
+
+    def tune_kernel(self, stream=None):
+        """Autotune the moment pass's warps per CTA and fold period at the plan's cell
+        occupancy (hip_batch_plan_tune_kernel): returns ((warps, fold) chosen,
+        {(warps, fold): replay ms})."""
+        w, f = ctypes.c_int(0), ctypes.c_int(0)
+        ms = (ctypes.c_float * 6)()
+        rc = self._lib.hip_batch_plan_tune_kernel(self._plan, _stream_handle(stream), ctypes.byref(w), ctypes.byref(f),
+                                                  ms)
+        if rc != 0:
+            raise HipError(rc, f"hip_batch_plan_tune_kernel: {self._lib.hip_status_string(rc).decode()} "
+                               f"({self._lib.hip_batch_message().decode()})")
+        shapes = [(a, b) for a in (4, 8) for b in (4096, 8192, 16384)]
+        return (int(w.value), int(f.value)), dict(zip(shapes, (float(x) for x in ms)))
+
+    def shape(self):
+        """(occ, warps, fold) of the plan (warps 0 = by occupancy, fold 0 = 16384)."""
+        o, w, f = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        self._lib.hip_batch_plan_shape(self._plan, ctypes.byref(o), ctypes.byref(w), ctypes.byref(f))
+        return int(o.value), int(w.value), int(f.value)
 
     def close(self):
         if self._plan:

@@ -74,7 +74,9 @@ struct hip_batch_plan {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;
     int launches = 0;
-    int occ = 64;  // target particles per cell (see batch_cells_per_side)
+    int occ = 64;   // target particles per cell (see batch_cells_per_side)
+    int warps = 0;  // moment pass: warps per CTA (4 or 8; 0 = by the cell occupancy)
+    int fold = 0;   // moment pass: pairs between folds of the FP32 sums (0 = the largest, 16384)
 };
 
 extern "C" const char *hip_batch_message(void) { return g_batch_msg; }
@@ -304,7 +306,7 @@ static hip_status plan_build(hip_batch_plan *pl, cudaStream_t st)
         if (ce == cudaSuccess)
             ce = hip_power_moments_batched<T>((const PmCat<T> *)(b + o_pc), nc, items, nc_max, counter,
                                               (const PmContractCat *)(b + o_cc), ne_max,
-                                              wsum > 0.0 ? psum / wsum : 0.0, st);
+                                              wsum > 0.0 ? psum / wsum : 0.0, pl->warps, pl->fold, st);
         launches += sizeof(T) == 4 ? 3 : 2;  // (sum |w|,) moments, contraction
     } else {
         if (ce == cudaSuccess)
@@ -503,6 +505,56 @@ extern "C" hip_status hip_batch_plan_tune(hip_batch_plan *pl, void *cuda_stream,
     if (hs != HIP_OK) return hs;
     if (chosen_out) *chosen_out = pl->occ;
     return HIP_OK;
+}
+
+// The in-kernel shapes of the moment pass at the plan's cell occupancy: warps per
+// CTA x fold period, each candidate timed on one replay after a warm-up.
+static const int k_tune_warps[] = {4, 8};
+static const int k_tune_fold[] = {4096, 8192, 16384};
+
+extern "C" hip_status hip_batch_plan_tune_kernel(hip_batch_plan *pl, void *cuda_stream, int *warps_out, int *fold_out,
+                                                 float *ms_out)
+{
+    g_batch_msg[0] = 0;
+    if (!pl) return HIP_ERR_ARG;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int best_w = 0, best_f = 0, i = 0;
+    float best_ms = 0.0f;
+    for (int w : k_tune_warps)
+        for (int f : k_tune_fold) {
+            plan_release(pl);
+            pl->warps = w;
+            pl->fold = f;
+            hip_status hs = pl->prec == HIP_PREC_MIXED ? plan_build<float>(pl, st) : plan_build<double>(pl, st);
+            if (hs == HIP_OK) hs = plan_run_locked(pl, st, nullptr);  // warm-up
+            float ms = 0.0f;
+            if (hs == HIP_OK) hs = plan_run_locked(pl, st, &ms);
+            if (hs != HIP_OK) return hs;
+            if (ms_out) ms_out[i] = ms;
+            ++i;
+            if (best_w == 0 || ms < best_ms) {
+                best_w = w;
+                best_f = f;
+                best_ms = ms;
+            }
+        }
+    plan_release(pl);
+    pl->warps = best_w;
+    pl->fold = best_f;
+    hip_status hs = pl->prec == HIP_PREC_MIXED ? plan_build<float>(pl, st) : plan_build<double>(pl, st);
+    if (hs != HIP_OK) return hs;
+    if (warps_out) *warps_out = pl->warps;
+    if (fold_out) *fold_out = pl->fold;
+    return HIP_OK;
+}
+
+extern "C" void hip_batch_plan_shape(const hip_batch_plan *pl, int *occ, int *warps, int *fold)
+{
+    if (!pl) return;
+    if (occ) *occ = pl->occ;
+    if (warps) *warps = pl->warps;
+    if (fold) *fold = pl->fold;
 }
 
 extern "C" void hip_batch_plan_destroy(hip_batch_plan *plan)

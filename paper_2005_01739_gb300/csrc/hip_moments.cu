@@ -32,7 +32,7 @@
 
 #define HIP_PM_NG 24
 #define HIP_PM_MAXW 8      // warps of a CTA: 4 or 8 (template NW, chosen at launch)
-#define HIP_PM_FOLD 16384  // pairs a CTA adds into its FP32 moments before folding them to FP64
+#define HIP_PM_FOLD 16384  // most pairs a CTA adds into its FP32 moments before folding them to FP64
 #define HIP_PM_TILE 128    // particles per staged tile of a cell
 // an epoch (the pairs between two folds) holds at most HIP_PM_FOLD - 1 + one tile pair
 static_assert(HIP_PM_FOLD + HIP_PM_TILE * HIP_PM_TILE <= 32768, "fixed-point moment words could overflow");
@@ -353,17 +353,18 @@ __device__ __forceinline__ void hip_pm_fold(PmA<T> *M, int n_cp, int n_c, double
 }
 
 // Adds the per-warp pair counts (written before the barrier that precedes this
-// call) into since_fold and, at HIP_PM_FOLD, folds the FP32 moments; called by
+// call) into since_fold and, at `fold` pairs (<= HIP_PM_FOLD), folds the FP32 moments; called by
 // all threads between a tile pair's barriers, when no warp is draining.  A tile
 // pair adds at most HIP_PM_TILE^2 pairs, so a fold epoch holds fewer than 2^15.
 // (The FP64 path folds once per catalog.)
 template <typename T>
-__device__ __forceinline__ void hip_pm_count(PmEpoch &ep, PmA<T> *M, int n_cp, int n_c, double *Mg, int &since_fold)
+__device__ __forceinline__ void hip_pm_count(PmEpoch &ep, PmA<T> *M, int n_cp, int n_c, double *Mg, int &since_fold,
+                                             int fold)
 {
     if (sizeof(T) == 4) {
 #pragma unroll
         for (int w = 0; w < HIP_PM_MAXW; ++w) since_fold += ep.drained[w];  // unused entries stay 0
-        if (since_fold >= HIP_PM_FOLD) {  // CTA-uniform
+        if (since_fold >= fold) {  // CTA-uniform
             hip_pm_fold<T>(M, n_cp, n_c, Mg, ep.C);
             since_fold = 0;
         }
@@ -371,10 +372,12 @@ __device__ __forceinline__ void hip_pm_count(PmEpoch &ep, PmA<T> *M, int n_cp, i
 }
 
 // Fixed-point scales of a catalog from the mean |w| of its particles (wabs =
-// sum |w|, n particles): with mean |w|^2 < 2^e and d_m <= 2^D, C_m = 2^(23 - e - D)
-// puts a typical term omega L_l R_m at ~2^21 units (rounding comparable to
-// FP32's, and unbiased), and the 2^33 range of one add holds run sums up to
-// ~2^10 typical terms.  Called by threads 0..15; the caller synchronises.
+// sum |w|, n particles): with mean |w|^2 < 2^e and d_m <= 2^D, C_m = 2^(25 - e - D)
+// puts a typical term omega L_l R_m at ~2^23 units (rounding below FP32's, and
+// unbiased); a drain whose sum of |omega| stays below Smax (2^7 mean |w|^2 and
+// more: 32 pairs of weight products up to ~4 mean |w|^2) keeps every run sum
+// within the 2^32-unit range of one add.  Called by threads 0..15; the caller
+// synchronises.
 __device__ __forceinline__ void hip_pm_units(PmEpoch &ep, const double *wabs, long long n)
 {
     const int m = threadIdx.x;
@@ -383,7 +386,7 @@ __device__ __forceinline__ void hip_pm_units(PmEpoch &ep, const double *wabs, lo
     frexp(wm > 0.0 ? wm * wm : 1.0, &e);
     int D = 0;
     while ((double)(1 << D) < hip_leg_scale(m)) ++D;
-    const int s = min(max(23 - e - D, -126), 127);
+    const int s = min(max(25 - e - D, -126), 127);
     ep.C[m] = ldexpf(1.0f, s);
     if (m == 0) {  // S d_k 2^s_k <= S 2^(D_k + s_k) <= 2^32 for every order k (a factor 2 to spare
                    // for |t| a rounding beyond 1 and the FP32 sum S)
@@ -391,7 +394,7 @@ __device__ __forceinline__ void hip_pm_units(PmEpoch &ep, const double *wabs, lo
         for (int k = 0; k < HIP_PM_M; ++k) {
             int Dk = 0;
             while ((double)(1 << Dk) < hip_leg_scale(k)) ++Dk;
-            smax = max(smax, Dk + min(max(23 - e - Dk, -126), 127));
+            smax = max(smax, Dk + min(max(25 - e - Dk, -126), 127));
         }
         ep.Smax = ldexpf(1.0f, min(max(32 - smax, -126), 127));
     }
@@ -406,7 +409,7 @@ template <typename T, int MASK, int NW>
 __device__ __forceinline__ void hip_pm_item(const CellList<T> &cl, long long p0, long long p1, int los, int item,
                                             PmTiles<T> &tl, PmStage<T> &sg, PmEpoch &ep, PmA<T> *M, int n_cp, int n_c,
                                             T R0, T dc, double *Mg, unsigned long long &cnt, int &drained,
-                                            int &since_fold)
+                                            int &since_fold, int fold)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -442,7 +445,7 @@ __device__ __forceinline__ void hip_pm_item(const CellList<T> &cl, long long p0,
             if (lane == 0) ep.drained[warp] = drained;
             drained = 0;
             __syncthreads();
-            hip_pm_count<T>(ep, M, n_cp, n_c, Mg, since_fold);
+            hip_pm_count<T>(ep, M, n_cp, n_c, Mg, since_fold, fold);
             for (int i = threadIdx.x; i < nn; i += blockDim.x) {
                 const long long oi = cl.idx[nbs + i];
                 PmPt<T> p;
@@ -524,7 +527,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW)  // <= 64 registers: 32 warp
         const int item = s_item;
         if (item >= a.n_items) break;
         hip_pm_item<T, MASK, NW>(cl, a.p0, a.p1, a.los, item, tl, stages[warp], ep, M, n_cp, n_c, R0, dc, Mr, cnt,
-                             drained, since_fold);
+                                 drained, since_fold, HIP_PM_FOLD);
     }
     __syncthreads();
     hip_pm_fold<T>(M, n_cp, n_c, Mr, ep.C);
@@ -538,7 +541,8 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW)  // <= 64 registers: 32 warp
 // the catalog it leaves.  The dynamic array is sized for the largest n_c.
 template <typename T, int NW>
 __global__ void __launch_bounds__(NW * 32, 32 / NW)
-    k_power_moments_batched(const PmCat<T> *__restrict__ cats, int n_cats, int n_items, int n_c_max, int *counter)
+    k_power_moments_batched(const PmCat<T> *__restrict__ cats, int n_cats, int n_items, int n_c_max, int *counter,
+                            int fold)
 {
     __shared__ PmTiles<T> tl;
     __shared__ PmStage<T> stages[NW];
@@ -583,7 +587,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW)
         hip_pm_item<T, 21, NW>(cat.cl, cat.p0, cat.p1, cat.los, item - cat.item_begin, tl, stages[warp], ep, M,
                            cat.n_c | 1, cat.n_c, cat.R0, cat.dc,
                            cat.Mg + (size_t)(blockIdx.x % HIP_PM_REPL) * 3 * HIP_PM_M * cat.n_c, cnt, drained,
-                           since_fold);
+                           since_fold, fold);
     }
 }
 
@@ -768,7 +772,7 @@ template cudaError_t hip_power_moments<double>(const CellList<double> &, const P
                                                int, double, void *, double *, cudaStream_t);
 
 template <typename T, int NW>
-static cudaError_t pm_batched_nw(const PmCat<T> *cats, int n_cats, int n_items, int n_c_max, int *counter,
+static cudaError_t pm_batched_nw(const PmCat<T> *cats, int n_cats, int n_items, int n_c_max, int *counter, int fold,
                                  cudaStream_t st)
 {
     if (sizeof(T) == 4) k_pm_wabs_batched<T><<<dim3(64, n_cats), 256, 0, st>>>(cats);
@@ -781,21 +785,24 @@ static cudaError_t pm_batched_nw(const PmCat<T> *cats, int n_cats, int n_items, 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_power_moments_batched<T, NW>, NW * 32, dyn);
     const int grid = sms * (nb < 1 ? 1 : nb);
-    k_power_moments_batched<T, NW><<<grid, NW * 32, dyn, st>>>(cats, n_cats, n_items, n_c_max, counter);
+    k_power_moments_batched<T, NW><<<grid, NW * 32, dyn, st>>>(cats, n_cats, n_items, n_c_max, counter, fold);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t hip_power_moments_batched(const PmCat<T> *cats, int n_cats, int n_items, int n_c_max, int *counter,
-                                      const PmContractCat *cc, int n_e_max, double per_cell, cudaStream_t st)
+                                      const PmContractCat *cc, int n_e_max, double per_cell, int warps, int fold,
+                                      cudaStream_t st)
 {
-    cudaError_t e = pm_warps(per_cell) == 8 ? pm_batched_nw<T, 8>(cats, n_cats, n_items, n_c_max, counter, st)
-                                            : pm_batched_nw<T, 4>(cats, n_cats, n_items, n_c_max, counter, st);
+    const int nw = warps == 4 || warps == 8 ? warps : pm_warps(per_cell);
+    const int fo = fold >= 1024 && fold <= HIP_PM_FOLD ? fold : HIP_PM_FOLD;
+    cudaError_t e = nw == 8 ? pm_batched_nw<T, 8>(cats, n_cats, n_items, n_c_max, counter, fo, st)
+                            : pm_batched_nw<T, 4>(cats, n_cats, n_items, n_c_max, counter, fo, st);
     if (e != cudaSuccess) return e;
     k_pm_contract_batched<<<dim3(3 * n_e_max, n_cats), 256, 0, st>>>(cc, n_e_max);
     return cudaGetLastError();
 }
 template cudaError_t hip_power_moments_batched<float>(const PmCat<float> *, int, int, int, int *,
-                                                      const PmContractCat *, int, double, cudaStream_t);
+                                                      const PmContractCat *, int, double, int, int, cudaStream_t);
 template cudaError_t hip_power_moments_batched<double>(const PmCat<double> *, int, int, int, int *,
-                                                       const PmContractCat *, int, double, cudaStream_t);
+                                                       const PmContractCat *, int, double, int, int, cudaStream_t);

@@ -51,8 +51,11 @@ size_t hip_pm_coef_doubles(int n_e, int n_c);
 cudaError_t hip_pm_coeffs(const double *d_kedges, int n_e, int n_ell, double R0, double k_max, double *coef,
                           cudaStream_t st);
 template <typename T>
+// warps: 4 or 8 per CTA (else chosen from per_cell, the pair-weighted particles
+// per cell); fold: pairs between the FP32 sums' folds, 1024..16384 (else 16384).
 cudaError_t hip_power_moments_batched(const PmCat<T> *cats, int n_cats, int n_items, int n_c_max, int *counter,
-                                      const PmContractCat *cc, int n_e_max, double per_cell, cudaStream_t st);
+                                      const PmContractCat *cc, int n_e_max, double per_cell, int warps, int fold,
+                                      cudaStream_t st);
 
 cudaError_t hip_upload_coeffs_moments();
 cudaError_t hip_upload_pm_tables();

@@ -142,14 +142,20 @@ def _berr(B, Bref):
 
 
 def test_plan_autotune_keeps_results():
-    # the autotuner only changes the cell shape; every candidate gives the same
-    # estimator, so the tuned plan's output matches the untuned one
+    # the autotuner only changes the cell shape and the moment pass's CTA shape and
+    # fold period; every candidate gives the same estimator, so the tuned plan's
+    # output matches the untuned one
     cats = [c for c, _, _ in _batch(True)]
     plan = binding.BatchPlan(cats, "mixed")
     try:
         before = [(P, n) for P, _, n in plan.run()]
         chosen, ms = plan.tune()
         assert chosen in (4, 8, 16, 32, 64, 128, 256, 0) and len(ms) == 8 and all(v > 0 for v in ms.values())
+        assert plan.shape()[0] == chosen
+        # second stage: warps per CTA and fold period of the moment pass
+        (w, f), kms = plan.tune_kernel()
+        assert (w, f) in kms and len(kms) == 6 and all(v > 0 for v in kms.values())
+        assert plan.shape() == (chosen, w, f)
         after = plan.run()
         for (P0, n0), (P1, _, n1) in zip(before, after):
             assert _err(P1, P0) < 1e-5
