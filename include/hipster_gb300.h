@@ -129,6 +129,37 @@ hip_status hip_bispectrum(const float *pos, const float *w, int64_t N, const flo
                           double R0, hip_window window, const double *k_edges, int n_k, int lmax, hip_precision prec,
                           double *B_out, int64_t *npairs_out, void *cuda_stream);
 
+/* Anisotropic bispectrum multipoles about the line of sight zhat: the extension
+ * proposed in the paper's conclusions (the sum over spherical harmonics of the
+ * isotropic estimator replaced by a product of two harmonics of different
+ * order).  The paper fixes no estimator; this one projects the triangle onto
+ *
+ *   S_{l1 l2 L}(u, v) = sum_m (l1 l2 L; m, -m, 0) y_{l1 m}(u) y_{l2 -m}(v),   y_lm = sqrt(4pi/(2l+1)) Y_lm,
+ *
+ * for the 18 combinations l1 <= l2 <= 4, l1 + l2 and L even, |l1 - l2| <= L <=
+ * min(l1 + l2, 4), in this order: (0,0,0) (0,2,2) (0,4,4) (1,1,0) (1,1,2)
+ * (1,3,2) (1,3,4) (2,2,0) (2,2,2) (2,2,4) (2,4,2) (2,4,4) (3,3,0) (3,3,2)
+ * (3,3,4) (4,4,0) (4,4,2) (4,4,4); B^ba_{l2 l1 L} = B^ab_{l1 l2 L} gives the rest.
+ *
+ *   B^ab_{l1 l2 L} = (2l1+1)(2l2+1)(-1)^((l1+l2)/2) [ T / (V n_w^3)
+ *        - d_{l2 0} d_{L l1} k_{l1} DD^a_{l1} W~^b / (V n_w^2) - d_{l1 0} d_{L l2} k_{l2} W~^a DD^b_{l2} / (V n_w^2)
+ *        + 2 d_{l1 0} d_{l2 0} W~^a W~^b ],   k_l = (-1)^l / sqrt(2l+1),
+ *   T = sum_{i data} w_i G(x_i) - (S1/N_r) sum_{r random} G(x_r),
+ *   G(x) = sum_{j != k} w_j w_k W_j W_k jbar^a_{l1}(r_j) jbar^b_{l2}(r_k) S_{l1 l2 L}(rhat_j, rhat_k),
+ *
+ * DD^a_l the ordered power pair sum of hip_power about zhat.  (l, l, 0) equals
+ * (-1)^l sqrt(2l+1) times hip_bispectrum's B_l.  Mixed precision only (the a_lm
+ * pass of hip_bispectrum, the matching-m Gram of its per-primary A_lm with
+ * compensated FP32 sums folded in FP64, FP64 C term and finalize).
+ *
+ *   arguments as for hip_bispectrum (no lmax, no precision); R0 k_max <= 768
+ *   B_out      [18 * n_k * n_k] float64 host, row-major (combination, a, b)
+ *   npairs_out [2] or NULL: data-primary and random-primary pairs
+ * Errors as for hip_bispectrum. */
+hip_status hip_bispectrum_aniso(const float *pos, const float *w, int64_t N, const float *rand_pos, int64_t N_r,
+                                double L, double R0, hip_window window, const double *k_edges, int n_k, double *B_out,
+                                int64_t *npairs_out, void *cuda_stream);
+
 /* Isotropic bispectrum multipoles without a random catalog (App. A of the paper):
  * as hip_bispectrum, but the random primaries' term (S1/N_r) sum_r G(x_r) is
  * replaced by its expectation (S1/V) sum_{j != k} w_j w_k E^{II,ab}_l(r_jk), with

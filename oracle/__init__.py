@@ -449,19 +449,35 @@ def wigner3j(j1: int, j2: int, j3: int, m1: int, m2: int, m3: int) -> float:
                                               * fac(j3 + m3) * fac(j3 - m3)) * s
 
 
+_GL_CACHE = {}
+
+
 def jbar_vec(l: int, edges, r, order: int = 32) -> np.ndarray:
     """jbar^a_l(r) of Eq. jla-def for every bin a at the separations r: [n_k][len(r)],
     the k-shell average 3 / (k_b^3 - k_a^3) int k^2 j_l(k r) dk by Gauss-Legendre
     (library Bessel function; a vectorised restatement of `jbar`)."""
     edges = np.asarray(edges, dtype=np.float64)
     r = np.atleast_1d(np.asarray(r, dtype=np.float64))
-    x, wq = np.polynomial.legendre.leggauss(order)
-    out = np.zeros((len(edges) - 1, len(r)))
-    for a in range(len(edges) - 1):
-        lo, hi = edges[a], edges[a + 1]
-        k = 0.5 * (hi - lo) * x + 0.5 * (hi + lo)
-        wk = 0.5 * (hi - lo) * wq * k * k * 3.0 / (hi ** 3 - lo ** 3)
-        out[a] = wk @ _sph_jn_vec(l, np.outer(k, r))
+    if order not in _GL_CACHE:
+        _GL_CACHE[order] = np.polynomial.legendre.leggauss(order)
+    x, wq = _GL_CACHE[order]
+    lo, hi = edges[:-1, None], edges[1:, None]
+    k = 0.5 * (hi - lo) * x[None, :] + 0.5 * (hi + lo)  # [n_k][order]
+    wk = 0.5 * (hi - lo) * wq[None, :] * k * k * 3.0 / (hi ** 3 - lo ** 3)
+    jl = _sph_jn_vec(l, k.reshape(-1, 1) * r[None, :]).reshape(k.shape[0], k.shape[1], len(r))
+    return np.einsum("aq,aqr->ar", wk, jl)
+
+
+def _ylm_vec(u) -> np.ndarray:
+    """Complex Y_lm (Condon-Shortley phase, polar axis z) of unit vectors u [n][3]
+    for l <= 4, index l*l + l + m: the library's harmonics, vectorised."""
+    from scipy.special import sph_harm_y
+    th = np.arccos(np.clip(u[:, 2], -1.0, 1.0))
+    ph = np.arctan2(u[:, 1], u[:, 0])
+    out = np.zeros((u.shape[0], 25), dtype=complex)
+    for l in range(5):
+        for m in range(-l, l + 1):
+            out[:, l * l + l + m] = sph_harm_y(l, m, th, ph)
     return out
 
 
@@ -502,7 +518,7 @@ def bispectrum_aniso_primary_sum(prim_pos, prim_w, prim_self, data_pos, data_w, 
         npairs += len(sel)
         rs = r[sel]
         wv = dw[sel] * np.array([window(x / R0) for x in rs])
-        Y = np.array([ylm(v) for v in d[sel] / rs[:, None]]) * ynorm  # [nnb][25], y_lm
+        Y = _ylm_vec(d[sel] / rs[:, None]) * ynorm  # [nnb][25], y_lm
         J = [jbar_vec(l, edges, rs) for l in range(5)]  # [l][a][j]
         for ci, ((l1, l2, _), (mm, cm)) in enumerate(zip(ANISO_COMBOS, coeffs)):
             full = np.zeros((nk, nk), dtype=complex)

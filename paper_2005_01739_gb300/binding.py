@@ -66,6 +66,8 @@ def load(path: str | None = None):
         L.hip_power.argtypes = [P, P, i64, d, d, i, P, i, i, i, i, i64, i64, P, P, P, P]
         L.hip_bispectrum.restype = i
         L.hip_bispectrum.argtypes = [P, P, i64, P, i64, d, d, i, P, i, i, i, P, P, P]
+        L.hip_bispectrum_aniso.restype = i
+        L.hip_bispectrum_aniso.argtypes = [P, P, i64, P, i64, d, d, i, P, i, P, P, P]
         L.hip_power_noalloc.restype = i
         L.hip_power_noalloc.argtypes = [P, P, i64, d, d, i, P, i, i, i, i64, i64, P, P, P, P]
         L.hip_power_from_pairs.restype = i
@@ -383,6 +385,31 @@ def hip_bispectrum(pos, w, rand_pos, L, R0, k_edges, lmax=4, prec="mixed", strea
                             int(lmax), PREC[prec], B.ctypes.data_as(ctypes.c_void_p), npairs,
                             _stream_handle(stream))
     _check(lib, rc, "hip_bispectrum")
+    del keep_p, keep_w, keep_r
+    return B, (int(npairs[0]), int(npairs[1]))
+
+
+ANISO_COMBOS = ((0, 0, 0), (0, 2, 2), (0, 4, 4), (1, 1, 0), (1, 1, 2), (1, 3, 2), (1, 3, 4), (2, 2, 0), (2, 2, 2),
+                (2, 2, 4), (2, 4, 2), (2, 4, 4), (3, 3, 0), (3, 3, 2), (3, 3, 4), (4, 4, 0), (4, 4, 2), (4, 4, 4))
+
+
+def hip_bispectrum_aniso(pos, w, rand_pos, L, R0, k_edges, stream=None):
+    """Anisotropic B^ab_{l1 l2 L} about zhat (the 18 combinations of ANISO_COMBOS),
+    mixed precision.  Returns (B [18, n_k, n_k], (data-primary pairs,
+    random-primary pairs))."""
+    lib = load()
+    n = int(pos.shape[0]) if hasattr(pos, "shape") else len(pos)
+    nr = int(rand_pos.shape[0]) if hasattr(rand_pos, "shape") else len(rand_pos)
+    pp, keep_p = _ptr(pos)
+    wp, keep_w = _ptr(w)
+    rp, keep_r = _ptr(rand_pos)
+    edges = np.ascontiguousarray(np.asarray(k_edges, dtype=np.float64))
+    n_k = len(edges) - 1
+    B = np.zeros((len(ANISO_COMBOS), n_k, n_k))
+    npairs = (ctypes.c_int64 * 2)()
+    rc = lib.hip_bispectrum_aniso(pp, wp, n, rp, nr, float(L), float(R0), 0, edges.ctypes.data_as(ctypes.c_void_p),
+                                  n_k, B.ctypes.data_as(ctypes.c_void_p), npairs, _stream_handle(stream))
+    _check(lib, rc, "hip_bispectrum_aniso")
     del keep_p, keep_w, keep_r
     return B, (int(npairs[0]), int(npairs[1]))
 

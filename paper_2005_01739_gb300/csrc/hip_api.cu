@@ -59,7 +59,7 @@ hip_status hip_device_setup(int *dev_out)
     if (dev < 0 || dev >= 64) return HIP_ERR_ARG;
     if (!g_coeffs_ready[dev]) {
         if ((e = hip_upload_coeffs_power()) != cudaSuccess || (e = hip_upload_coeffs_bispec()) != cudaSuccess ||
-            (e = hip_upload_coeffs_e2()) != cudaSuccess) {
+            (e = hip_upload_coeffs_e2()) != cudaSuccess || (e = hip_upload_aniso_tables()) != cudaSuccess) {
             set_err("coefficient upload", e);
             return HIP_ERR_CUDA;
         }
@@ -434,7 +434,10 @@ struct BkHostCat {
     double *cmom;           // device [n_cc][32]
     double *acc;            // device [5][n_k][n_k], zeroed by bk_run
     long long n_data;       // the data primaries (first in the primary order)
-    double *S;              // device [n_k]: S^a from the data primaries' A^a_00 (zeroed by bk_run), or null
+    double *S;              // device [n_S][n_k]: S^a_l from the data primaries' A^a_l0 (zeroed by bk_run), or null
+    int n_S = 1;            // 1 (l = 0) or 3 (l = 0, 2, 4)
+    double *G = nullptr;    // anisotropic: device [HIP_ANISO_NBLK][n_k][n_k] Gram blocks (zeroed by bk_run)
+    double *Tc = nullptr;   // anisotropic: device [18][n_k][n_k] primary sums (written by bk_run)
 };
 
 // The primary sum T of every catalog into its acc: the a_lm pass and the
@@ -462,10 +465,16 @@ static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCa
     int *cnt = (int *)(b + pl.o_cnt);  // [0] work counter, [1] status
     bool want_s = false;
     for (int i = 0; i < nc; ++i) {
-        HIP_CK(cudaMemsetAsync(hc[i].cmom, 0, sizeof(double) * hc[i].n_cc * HIP_BK_NM, st), "memset");
-        HIP_CK(cudaMemsetAsync(hc[i].acc, 0, sizeof(double) * (HIP_LMAX + 1) * hc[i].n_k * hc[i].n_k, st), "memset");
+        const int nL = hc[i].G ? 3 : 1;
+        HIP_CK(cudaMemsetAsync(hc[i].cmom, 0, sizeof(double) * nL * hc[i].n_cc * HIP_BK_NM, st), "memset");
+        if (hc[i].G)
+            HIP_CK(cudaMemsetAsync(hc[i].G, 0, sizeof(double) * HIP_ANISO_NBLK * hc[i].n_k * hc[i].n_k, st),
+                   "memset");
+        else
+            HIP_CK(cudaMemsetAsync(hc[i].acc, 0, sizeof(double) * (HIP_LMAX + 1) * hc[i].n_k * hc[i].n_k, st),
+                   "memset");
         if (hc[i].S) {
-            HIP_CK(cudaMemsetAsync(hc[i].S, 0, sizeof(double) * hc[i].n_k, st), "memset");
+            HIP_CK(cudaMemsetAsync(hc[i].S, 0, sizeof(double) * hc[i].n_S * hc[i].n_k, st), "memset");
             want_s = true;
         }
     }
@@ -513,9 +522,10 @@ static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCa
                 g.stage_begin = stages;
                 stages += (int)((take + P - 1) / P);
                 g.stage_end = stages;
-                g.acc = hc[ci].acc;
+                g.acc = hc[ci].G ? hc[ci].G : hc[ci].acc;
                 g.n_d = (int)std::max(0LL, std::min(hc[ci].n_data - gi, take));
                 g.S = hc[ci].S;
+                g.n_S = hc[ci].n_S;
                 segs.push_back(g);
                 x_off += ((take * HIP_NLM * hc[ci].n_k + 63) / 64) * 64;
                 sp_off += ((take + 7) / 8) * 8;
@@ -538,7 +548,9 @@ static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCa
         HIP_CK(hip_bk_alm<T>(dcats, dspans, (int)spans.size(), items, pl.nk_max, pl.ncc_max, X, sp, slots, cnt, st),
                "bispectrum a_lm pass");
         mark();
-        if (pl.tc && !g_bk_cores)
+        if (hc[0].G)  // anisotropic: the matching-m Gram blocks (every catalog of the call is anisotropic)
+            HIP_CK(hip_bk_aniso_gram(dsegs, (int)segs.size(), pl.nk_max, used, st), "anisotropic Gram");
+        else if (pl.tc && !g_bk_cores)
             HIP_CK(hip_bk_contract_tc(dsegs, (int)segs.size(), stages, pl.nk_max, cnt + 1, g_bk_tc_grid_cap, g_bk_fold,
                                       st),
                    "bispectrum contraction (tensor cores)");
@@ -557,7 +569,12 @@ static hip_status bk_run(std::vector<BkCat<T>> &cats, const std::vector<BkHostCa
         c.n_cc = hc[i].n_cc;
         c.cmom = hc[i].cmom;
         c.acc = hc[i].acc;
-        HIP_CK(hip_bk_cterm(c, b + pl.o_cc, st), "bispectrum C term");
+        if (hc[i].G) {
+            HIP_CK(hip_bk_aniso_assemble(hc[i].G, hc[i].n_k, hc[i].Tc, st), "anisotropic assembly");
+            HIP_CK(hip_bk_cterm_aniso(c, hip_aniso_tables().ct, b + pl.o_cc, hc[i].Tc, st), "anisotropic C term");
+        } else {
+            HIP_CK(hip_bk_cterm(c, b + pl.o_cc, st), "bispectrum C term");
+        }
     }
     int status = 0;
     HIP_CK(cudaMemcpyAsync(&status, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H status");
@@ -607,6 +624,7 @@ static BkCat<T> bk_cat(const CellList<T> &dcl, const CellList<T> &rcl, const int
     a.rp1 = ranges ? ranges[3] : N_r;
     a.n_e = n_k + 1;
     a.n_cc = hip_bk_intervals(R0, k_edges[n_k]);
+    a.n_L = 1;
     a.R0 = (T)R0;
     a.rand_weight = (T)rand_weight;
     a.cc_scale = (T)(a.n_cc / R0);
@@ -640,15 +658,17 @@ extern "C" void hip_debug_bk_mode(int contract_on_cores, int fold_prims)
 template <typename T>
 static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const float *rpos, int64_t N_r, double L,
                               double R0, const double *k_edges, int n_k, int lmax, double *B_out,
-                              int64_t *npairs_out, cudaStream_t st, int dev, const int64_t *ranges, bool partial)
+                              int64_t *npairs_out, cudaStream_t st, int dev, const int64_t *ranges, bool partial,
+                              bool aniso = false)
 {
     Workspace &ws = hip_workspace(dev);
     const int n_c = hip_cells_per_side(L, R0);
     const int n_cells = n_c * n_c * n_c;
     const int n_e = n_k + 1;
     const bool dpos = hip_is_device_ptr(pos), dw = w && hip_is_device_ptr(w), drp = hip_is_device_ptr(rpos);
-    const size_t tsz = (size_t)(HIP_LMAX + 1) * n_k * n_k;
+    const size_t tsz = (size_t)(aniso ? HIP_ANISO_NCOMB : HIP_LMAX + 1) * n_k * n_k;
     const int n_cc = hip_bk_intervals(R0, k_edges[n_k]);
+    const int n_L = aniso ? 3 : 1;  // C-moment sets (L_0, L_2, L_4 of mu for the anisotropic bispectrum)
 
     Carve cv;
     const size_t o_pos = dpos ? 0 : cv.take(sizeof(float) * 3 * N);
@@ -663,11 +683,14 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     const size_t o_dsc = cv.take(sizeof(int) * N), o_rsc = cv.take(sizeof(int) * N_r);
     const size_t o_rs = cv.take(sizeof(int) * (n_cells + 1)), o_rf = cv.take(sizeof(int) * n_cells);
     const size_t o_acc = cv.take(sizeof(double) * tsz);
-    const size_t o_cmom = cv.take(sizeof(double) * n_cc * HIP_BK_NM);
+    const size_t o_cmom = cv.take(sizeof(double) * n_L * n_cc * HIP_BK_NM);
     const size_t o_small = cv.take(sizeof(double) * 16);
     const size_t o_wt = cv.take(sizeof(double) * n_k), o_dd = cv.take(sizeof(double) * 3 * n_k);
     const size_t o_p = cv.take(sizeof(double) * 3 * n_k), o_b = cv.take(sizeof(double) * tsz);
-    const BkPlan pl = bk_plan<T>(cv, 1, n_k, n_cc, N + N_r, hip_bk_cterm_scratch_bytes(n_cc, n_k));
+    const size_t o_G = aniso ? cv.take(sizeof(double) * HIP_ANISO_NBLK * n_k * n_k) : 0;
+    const BkPlan pl = bk_plan<T>(cv, 1, n_k, n_L * n_cc, N + N_r,
+                                 aniso ? hip_bk_cterm_aniso_scratch_bytes(n_cc, n_k)
+                                       : hip_bk_cterm_scratch_bytes(n_cc, n_k));
     hip_status hs = ws.reserve(cv.total, st);
     if (hs != HIP_OK) return hs;
     char *b = (char *)ws.base;
@@ -727,17 +750,25 @@ static hip_status bispec_impl(const float *pos, const float *w, int64_t N, const
     std::vector<BkCat<T>> cats(1, bk_cat<T>(dcl, rcl, (const int *)(b + o_dsc), (const int *)(b + o_rsc), N, N_r,
                                             ranges, k_edges, n_k, R0, -hS1 / (double)N_r, npairs + 1,
                                             (double *)(b + o_cmom)));
+    cats[0].n_L = n_L;
     std::vector<BkHostCat> hc(1);
     hc[0] = BkHostCat{N + N_r, n_k, n_cc, R0, k_edges, (double *)(b + o_cmom), (double *)(b + o_acc), N,
                       partial ? nullptr : DD};
+    if (aniso) {
+        hc[0].n_S = 3;  // DD^a_l, l = 0, 2, 4, about zhat
+        hc[0].G = (double *)(b + o_G);
+        hc[0].Tc = (double *)(b + o_acc);
+    }
     if ((hs = bk_run<T>(cats, hc, pl, b, st)) != HIP_OK) return hs;
     double *acc = (double *)(b + o_acc);
     double *B = (double *)(b + o_b);
-    if (partial)
+    if (aniso)
+        HIP_CK(hip_bk_aniso_finalize(acc, DD, Wt, S1, n_k, L, B, st), "anisotropic finalize");
+    else if (partial)
         HIP_CK(hip_bispec_sum(acc, 1, n_k, lmax, B, st), "bispectrum sum");
     else
         HIP_CK(hip_bispec_finalize(acc, 1, n_k, lmax, L, S1, DD, Wt, B, st), "bispectrum finalize");
-    const size_t nout = (size_t)(lmax + 1) * n_k * n_k;
+    const size_t nout = aniso ? tsz : (size_t)(lmax + 1) * n_k * n_k;
     std::vector<double> hB(nout);
     unsigned long long hn[3] = {0, 0, 0};
     HIP_CK(cudaMemcpyAsync(hB.data(), B, sizeof(double) * nout, cudaMemcpyDeviceToHost, st), "D2H B");
@@ -776,6 +807,26 @@ extern "C" hip_status hip_bispectrum(const float *pos, const float *w, int64_t N
                                   nullptr, false);
     return bispec_impl<double>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, lmax, B_out, npairs_out, st, dev,
                                nullptr, false);
+}
+
+extern "C" hip_status hip_bispectrum_aniso(const float *pos, const float *w, int64_t N, const float *rand_pos,
+                                           int64_t N_r, double L, double R0, hip_window window,
+                                           const double *k_edges, int n_k, double *B_out, int64_t *npairs_out,
+                                           void *cuda_stream)
+{
+    g_errbuf[0] = 0;
+    if (!pos || !rand_pos || !B_out) return HIP_ERR_ARG;
+    if (N < 1 || N > 2000000000LL || N_r < 1 || N_r > 2000000000LL) return HIP_ERR_ARG;
+    if (window != HIP_WINDOW_PHILCOX) return HIP_ERR_ARG;
+    if (!(L > 0.0) || !std::isfinite(L) || !(R0 > 0.0) || !(R0 < 0.5 * L)) return HIP_ERR_RANGE;
+    hip_status hs = hip_check_edges(k_edges, n_k);
+    if (hs != HIP_OK) return hs;
+    if (n_k > HIP_BMAXE - 2 || hip_bk_intervals(R0, k_edges[n_k]) > HIP_ANISO_MAXCC) return HIP_ERR_RANGE;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    int dev = 0;
+    if ((hs = hip_device_setup(&dev)) != HIP_OK) return hs;
+    return bispec_impl<float>(pos, w, N, rand_pos, N_r, L, R0, k_edges, n_k, HIP_LMAX, B_out, npairs_out,
+                              (cudaStream_t)cuda_stream, dev, nullptr, false, true);
 }
 
 // Batched bispectra: per catalog the buffers of bispec_impl (one workspace

@@ -64,22 +64,26 @@ __global__ void __launch_bounds__(256) k_bk_s_sum(const BkSeg *__restrict__ segs
     if (!sg.S) return;  // block-uniform
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nk = sg.n_k;
     const T *X = (const T *)sg.X, *sp = (const T *)sg.sp;
-    double s0 = 0.0, s1 = 0.0;
-    for (int p = blockIdx.x * 8 + warp; p < sg.n_d; p += gridDim.x * 8) {
-        const T w = sp[p];  // 0 for an excluded primary, whose row of X is not written
-        if (w == T(0)) continue;
-        const T *row = X + (size_t)p * HIP_NLM * nk;  // harmonic (0, 0): R_00 = 1
-        if (lane < nk) s0 += (double)w * (double)row[lane];
-        if (lane + 32 < nk) s1 += (double)w * (double)row[lane + 32];
-    }
-    red[warp][lane] = s0;
-    red[warp][lane + 32] = s1;
-    __syncthreads();
-    if (threadIdx.x < 64 && threadIdx.x < nk) {
-        double t = 0.0;
+    for (int li = 0; li < sg.n_S; ++li) {  // l = 2 li: harmonic (l, 0) is row l^2 + l, R_l0 = L_l(mu)
+        const int hr = (2 * li) * (2 * li) + 2 * li;
+        double s0 = 0.0, s1 = 0.0;
+        for (int p = blockIdx.x * 8 + warp; p < sg.n_d; p += gridDim.x * 8) {
+            const T w = sp[p];  // 0 for an excluded primary, whose row of X is not written
+            if (w == T(0)) continue;
+            const T *row = X + ((size_t)p * HIP_NLM + hr) * nk;
+            if (lane < nk) s0 += (double)w * (double)row[lane];
+            if (lane + 32 < nk) s1 += (double)w * (double)row[lane + 32];
+        }
+        __syncthreads();
+        red[warp][lane] = s0;
+        red[warp][lane + 32] = s1;
+        __syncthreads();
+        if (threadIdx.x < 64 && threadIdx.x < nk) {
+            double t = 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
-        if (t != 0.0) atomicAdd(&sg.S[threadIdx.x], t);
+            for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
+            if (t != 0.0) atomicAdd(&sg.S[li * nk + threadIdx.x], t);
+        }
     }
 }
 
@@ -151,7 +155,8 @@ template <typename T>
 struct BkWarpSmem {
     alignas(16) T qa[64][4];            // accepted neighbours: primary minus neighbour, w_j
     alignas(16) T qd[32][HIP_NLMP];     // drained pairs: R_lm (0..24), r (25), w_j W (26)
-    T pt[32][HIP_BK_NM + 1];            // C-term weight s_p w_j^2 W^2 times P_m(t), m < 32
+    T pt[32][HIP_BK_NM + 1];            // C-term weight s_p w_j^2 W^2 times R_m(t), m < 32
+    T lq[32][2];                        // L_2, L_4 of each drained pair's mu (n_L = 3)
     int qc[32];                         // C-term interval of each drained pair
 };
 
@@ -234,7 +239,7 @@ __device__ __forceinline__ double bk_low(double, double, double) { return 0.0; }
 // geometry and harmonics (one per lane), their C-term moments (one lane per
 // moment) and their contributions to the edge sums (one lane per bin edge).
 template <typename T, int NCH>
-__device__ __forceinline__ void bk_flush(BkWarpSmem<T> &sm, T *cm, int n, T s_p, T iR, T iR_lo, T cc_scale, T cc_lo, int n_cc,
+__device__ __forceinline__ void bk_flush(BkWarpSmem<T> &sm, T *cm, int n, T s_p, T iR, T iR_lo, T cc_scale, T cc_lo, int n_cc, int n_L,
                                          int n_e, const BkEdges<T, NCH> &ed, int lane, T (&E)[NCH][HIP_NLM])
 {
     if (lane < n) {
@@ -267,9 +272,25 @@ __device__ __forceinline__ void bk_flush(BkWarpSmem<T> &sm, T *cm, int n, T s_p,
             p1 = p2;
         }
         sm.qc[lane] = c;
+        if (n_L > 1) {  // mu about the line of sight z (even L: the sign of dz does not matter)
+            T l2, l4;
+            hip_legendre24<T>(dz * ir, l2, l4);
+            sm.lq[lane][0] = l2;
+            sm.lq[lane][1] = l4;
+        }
     }
     __syncwarp();
-    for (int q = 0; q < n; ++q) cm[sm.qc[q] * HIP_BK_NM + lane] += sm.pt[q][lane];
+    if (n_L > 1) {  // warp-uniform
+        for (int q = 0; q < n; ++q) {
+            const T v = sm.pt[q][lane];
+            const int o = sm.qc[q] * HIP_BK_NM + lane;
+            cm[o] += v;
+            cm[n_cc * HIP_BK_NM + o] += v * sm.lq[q][0];
+            cm[2 * n_cc * HIP_BK_NM + o] += v * sm.lq[q][1];
+        }
+    } else {
+        for (int q = 0; q < n; ++q) cm[sm.qc[q] * HIP_BK_NM + lane] += sm.pt[q][lane];
+    }
     for (int q = 0; q < n; ++q) {
         T rec[HIP_NLMP];
         bk_load_rec(sm.qd[q], rec);
@@ -368,7 +389,7 @@ __device__ __forceinline__ void bk_primary(const BkCat<T> &a, int g, BkWarpSmem<
             qn += nq;
             if (qn >= 32) {
                 __syncwarp();
-                bk_flush<T, NCH>(sm, cm, 32, s_p, iR, iR_lo, cc_scale, cc_lo, n_cc, n_e, ed, lane, E);
+                bk_flush<T, NCH>(sm, cm, 32, s_p, iR, iR_lo, cc_scale, cc_lo, n_cc, a.n_L, n_e, ed, lane, E);
                 const int rest = qn - 32;
                 T mv[4] = {T(0), T(0), T(0), T(0)};
                 if (lane < rest) {
@@ -387,7 +408,7 @@ __device__ __forceinline__ void bk_primary(const BkCat<T> &a, int g, BkWarpSmem<
     }
     if (qn > 0) {
         __syncwarp();
-        bk_flush<T, NCH>(sm, cm, qn, s_p, iR, iR_lo, cc_scale, cc_lo, n_cc, n_e, ed, lane, E);
+        bk_flush<T, NCH>(sm, cm, qn, s_p, iR, iR_lo, cc_scale, cc_lo, n_cc, a.n_L, n_e, ed, lane, E);
     }
 #pragma unroll
     for (int t = 0; t < NCH; ++t) {
@@ -431,7 +452,7 @@ __global__ void __launch_bounds__(HIP_BK_THREADS) k_bk_alm(const BkCat<T> *__res
     int cur = -1, si = 0;
     auto leave = [&](int c) {
         const BkCat<T> &a = cats[c];
-        for (int i = lane; i < a.n_cc * HIP_BK_NM; i += 32) {
+        for (int i = lane; i < a.n_L * a.n_cc * HIP_BK_NM; i += 32) {
             const double v = slot[i];
             if (v != 0.0) {
                 atomicAdd(&a.cmom[i], v);
@@ -468,7 +489,7 @@ __global__ void __launch_bounds__(HIP_BK_THREADS) k_bk_alm(const BkCat<T> *__res
         }
         __syncwarp();
         // the item's C-term moments into the warp's FP64 slot
-        for (int i = lane; i < a.n_cc * HIP_BK_NM; i += 32) {
+        for (int i = lane; i < a.n_L * a.n_cc * HIP_BK_NM; i += 32) {
             const T v = cm[i];
             if (v != T(0)) {
                 slot[i] += (double)v;
@@ -764,6 +785,53 @@ cudaError_t hip_bk_cterm(const BkCTerm &c, void *scratch, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const int n_out = (HIP_LMAX + 1) * nk * nk;
     k_bk_cc_contract<<<(n_out + 7) / 8, 256, 0, st>>>(c, wn, J);
+    return cudaGetLastError();
+}
+
+// Anisotropic C term: Tc[c][a][b] -= g_c sum_q wn_{L_c}[q] J[l1_c][a][q] J[l2_c][b][q]
+// (g_c = (l1 l2 L; 0 0 0)), one warp per (combination, a, b).
+__global__ void k_bk_cc_contract_aniso(BkAnisoCTerm t, int nk, int n_nodes, const double *__restrict__ wn,
+                                       const double *__restrict__ J, double *__restrict__ Tc)
+{
+    const int lane = threadIdx.x & 31;
+    const int n_out = t.n_comb * nk * nk;
+    for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n_out; o += (gridDim.x * blockDim.x) >> 5) {
+        const int ci = o / (nk * nk), ab = o - ci * nk * nk, a = ab / nk, b = ab - a * nk;
+        const double *w = wn + (size_t)t.Lidx[ci] * n_nodes;
+        const double *Ja = J + ((size_t)t.l1[ci] * nk + a) * n_nodes, *Jb = J + ((size_t)t.l2[ci] * nk + b) * n_nodes;
+        double s = 0.0;
+        for (int i = lane; i < n_nodes; i += 32) s += w[i] * Ja[i] * Jb[i];
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) Tc[o] -= t.g[ci] * s;
+    }
+}
+
+size_t hip_bk_cterm_aniso_scratch_bytes(int n_cc, int n_k)
+{
+    const size_t nodes = (size_t)n_cc * HIP_BK_CQ;
+    return sizeof(double) * nodes * (3 + (HIP_LMAX + 1) * (size_t)n_k);
+}
+
+cudaError_t hip_bk_cterm_aniso(const BkCTerm &c, const BkAnisoCTerm &t, void *scratch, double *Tc, cudaStream_t st)
+{
+    cq_nodes();
+    BkCQ q;
+    for (int i = 0; i < HIP_BK_CQ; ++i) {
+        q.x[i] = s_cq_x[i];
+        q.w[i] = s_cq_w[i];
+    }
+    const int n_nodes = c.n_cc * HIP_BK_CQ, nk = c.n_e - 1;
+    double *wn = reinterpret_cast<double *>(scratch);  // [3][n_nodes]: the L = 0, 2, 4 moment sets
+    double *J = wn + 3 * (size_t)n_nodes;
+    for (int L = 0; L < 3; ++L) {
+        BkCTerm cl = c;
+        cl.cmom = c.cmom + (size_t)L * c.n_cc * HIP_BK_NM;
+        k_bk_cc_nodes<<<(n_nodes + 127) / 128, 128, 0, st>>>(cl, q, wn + (size_t)L * n_nodes, J);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int n_out = t.n_comb * nk * nk;
+    k_bk_cc_contract_aniso<<<(n_out + 7) / 8, 256, 0, st>>>(t, nk, n_nodes, wn, J, Tc);
     return cudaGetLastError();
 }
 

@@ -36,11 +36,13 @@ struct BkCat {
     long long dp0, dp1, rp0, rp1;  // primary ranges (input order) of the data and of the randoms
     int n_e;                   // bin edges = n_k + 1
     int n_cc;                  // C-term intervals
+    int n_L;                   // C-term moment sets: 1 (L_0), or 3 (L_0, L_2, L_4 of the neighbour's mu, for the
+                               // anisotropic bispectrum)
     T R0;
     T rand_weight;             // -S1 / N_r
     T cc_scale, cc_lo;         // n_cc / R0 = cc_scale + cc_lo
     T iR, iR_lo;               // 1 / R0 = iR + iR_lo
-    double *cmom;              // [n_cc][HIP_BK_NM] FP64 C-term moments (atomically added)
+    double *cmom;              // [n_L][n_cc][HIP_BK_NM] FP64 C-term moments (atomically added)
     unsigned long long *npairs;  // [0] data-primary pairs, [1] random-primary pairs
     T k[HIP_BMAXE], klo[HIP_BMAXE], k3[HIP_BMAXE], jfac[HIP_BMAXE];
 };
@@ -73,7 +75,8 @@ struct BkSeg {
     int stage_begin, stage_end;  // tensor-core path: stages of P primaries [begin, end)
     double *acc;               // [5][n_k][n_k] FP64 primary sum (atomically added)
     int n_d;                   // the first n_d primaries are data primaries
-    double *S;                 // [n_k] S^a += sum over them of s_p A^a_00 (null: not wanted)
+    double *S;                 // [n_S][n_k] S^a_l += sum over them of s_p A^a_l0, l = 0, 2, .. (null: not wanted)
+    int n_S;                   // 1 (S^a = DD^a_0) or 3 (DD^a_l, l = 0, 2, 4, about zhat: R_l0 = L_l(mu))
 };
 
 // Primaries per tensor-core stage for a launch whose largest n_k is nk_max.
@@ -108,6 +111,42 @@ struct BkCTerm {
 };
 size_t hip_bk_cterm_scratch_bytes(int n_cc, int n_k);
 cudaError_t hip_bk_cterm(const BkCTerm &c, void *scratch, cudaStream_t st);
+
+// ------------------------------------------------ anisotropic bispectrum ----
+// Combinations (l1, l2, L) of the anisotropic bispectrum (hip_bispectrum_aniso):
+// l1 <= l2 <= 4, l1 + l2 and L even, |l1 - l2| <= L <= min(l1 + l2, 4): 18 of them.
+#define HIP_ANISO_NCOMB 18
+#define HIP_ANISO_MAXCC 96  // C-term intervals of the anisotropic path (three moment sets per warp: R0 k_max <= 768)
+#define HIP_ANISO_NBLK 22  // (l1, l2, |m|) blocks of the matching-m Gram: l1 <= l2, l1 + l2 even, |m| <= l1
+struct BkAnisoCTerm {
+    int n_comb;
+    int l1[HIP_ANISO_NCOMB], l2[HIP_ANISO_NCOMB], Lidx[HIP_ANISO_NCOMB];  // Lidx = L / 2
+    double g[HIP_ANISO_NCOMB];                                           // (l1 l2 L; 0 0 0)
+};
+// The C term of the combinations from the catalog's three C-moment sets
+// (c.cmom: [3][n_cc][32], L = 0, 2, 4): Tc [18][n_k][n_k] -= g sum_j w_j^2 W^2
+// jbar^a_l1 jbar^b_l2 L_L(mu_j) summed over the primaries with s_p.
+// Host tables: the Gram blocks (l1, l2, |m|) in order and, per combination, g and
+// kappa_m = (-1)^m (l1 l2 L; m, -m, 0) (m = 0..l1), from Wigner symbols on the host.
+struct BkAnisoTables {
+    int n_blk;
+    int bl1[HIP_ANISO_NBLK], bl2[HIP_ANISO_NBLK], bm[HIP_ANISO_NBLK];
+    BkAnisoCTerm ct;
+    double kappa[HIP_ANISO_NCOMB][5];
+};
+const BkAnisoTables &hip_aniso_tables();
+cudaError_t hip_upload_aniso_tables();
+// G [HIP_ANISO_NBLK][n_k][n_k] (each segment's acc points at its catalog's G,
+// zeroed before) += the matching-m Gram blocks of the segments' X.
+cudaError_t hip_bk_aniso_gram(const BkSeg *segs, int n_segs, int nk_max, long long max_prims, cudaStream_t st);
+// Tc [18][n_k][n_k] = sum_m kappa_m G_{l1 l2 m} (overwrites).
+cudaError_t hip_bk_aniso_assemble(const double *G, int nk, double *Tc, cudaStream_t st);
+// B [18][n_k][n_k] of the reading from Tc (primary sum with s_p), S [3][n_k]
+// (DD^a_l, l = 0, 2, 4 about zhat), W~^a, S1 (device), box side L.
+cudaError_t hip_bk_aniso_finalize(const double *Tc, const double *S, const double *Wt, const double *S1, int nk,
+                                  double L, double *B, cudaStream_t st);
+size_t hip_bk_cterm_aniso_scratch_bytes(int n_cc, int n_k);
+cudaError_t hip_bk_cterm_aniso(const BkCTerm &c, const BkAnisoCTerm &t, void *scratch, double *Tc, cudaStream_t st);
 
 // Cell index of every sorted particle from the cell start table.
 cudaError_t hip_sorted_cells(const int *cell_start, int n_cells, int *scell, cudaStream_t st);

@@ -185,3 +185,42 @@ def test_bispectrum_analytic_rejects_large_R0():
     with pytest.raises(binding.HipError) as ei:
         binding.hip_bispectrum_analytic(pos, None, L, 0.26 * L, edges, 4, "mixed")
     assert ei.value.status == binding.HIP_ERR_RANGE
+
+
+# ------------------------------------------------ anisotropic bispectrum ----
+def _aniso_case():
+    # z-displaced clustering: the L > 0 components about zhat are far from zero
+    L, R0 = 50.0, 10.0
+    pos, w = catalogs.thomas(800, L, 32, 1.5, seed=71, background_frac=0.2, los_sigma=2.5, weights="u05_15")
+    rnd = catalogs.uniform(2400, L, seed=72)
+    return pos, w, rnd, L, R0
+
+
+def test_bispectrum_aniso_parity():
+    # every (l1, l2, L) combination against the oracle's per-primary Wigner-3j form
+    pos, w, rnd, L, R0 = _aniso_case()
+    edges = catalogs.linear_edges(0.3, 2.0, 8)
+    Bref, info = oracle.bispectrum_aniso(pos.astype(np.float64), w.astype(np.float64), rnd.astype(np.float64),
+                                         L, R0, edges)
+    assert tuple(binding.ANISO_COMBOS) == tuple(oracle.ANISO_COMBOS)
+    B, (nd, nr) = binding.hip_bispectrum_aniso(_dev(pos), _dev(w), _dev(rnd), L, R0, edges)
+    slack = max(2, int(2e-6 * info["npairs_data"]))
+    assert abs(nd - info["npairs_data"]) <= slack and abs(nr - info["npairs_rand"]) <= slack
+    # the L > 0 components carry signal (relative to the monopole) in this catalog
+    assert max(np.max(np.abs(Bref[c])) for c, (_, _, Lc) in enumerate(oracle.ANISO_COMBOS) if Lc > 0) \\
+        > 1e-2 * np.max(np.abs(Bref[0]))
+    assert _err(B, Bref, "aniso") < TOL["mixed"]
+
+
+def test_bispectrum_aniso_l0_matches_isotropic_path():
+    # (l, l, 0) = (-1)^l sqrt(2l+1) B_l: the matching-m Gram and the tensor-core contraction of
+    # the isotropic path give the same primary sums
+    pos, w, rnd, L, R0 = _case(seed=43, N=2000, weights="u05_15")
+    edges = catalogs.linear_edges(0.3, 2.4, 16)
+    dpos, dw, drnd = _dev(pos), _dev(w), _dev(rnd)
+    Bi, _ = binding.hip_bispectrum(dpos, dw, drnd, L, R0, edges, 4, "mixed")
+    Ba, _ = binding.hip_bispectrum_aniso(dpos, dw, drnd, L, R0, edges)
+    for l in range(5):
+        c = binding.ANISO_COMBOS.index((l, l, 0))
+        ref = (-1) ** l * np.sqrt(2 * l + 1) * Bi[l]
+        assert np.max(np.abs(Ba[c] - ref)) < 1e-5 * np.max(np.abs(ref)), l

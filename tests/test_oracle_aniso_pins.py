@@ -235,3 +235,10 @@ def test_symmetries():
             np.testing.assert_allclose(T2[ci], T0[ci], atol=1e-10 * scale)
     moved = max(np.max(np.abs(T2[ci] - T0[ci])) for ci, (_, _, Lc) in enumerate(COMBOS) if Lc > 0)
     assert moved > 1e-3 * scale
+
+
+def test_vectorised_harmonics_match_the_oracle_ylm():
+    rng = np.random.default_rng(9)
+    u = rng.normal(size=(20, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    np.testing.assert_allclose(oracle._ylm_vec(u), np.array([oracle.ylm(v) for v in u]), atol=1e-13)
