@@ -8,7 +8,9 @@
 //      A^a_lm, written to X[p][lm][a]; per pair the 32 Legendre moments of
 //      s_p w_j^2 W^2 in the separation (the C term depends on r alone);
 //   2. the contraction sum_p s_p X_p X_p^T (the block-diagonal l blocks), on the
-//      tensor cores (hip_bk_tc.cu, tcgen05 TF32 with a hi/lo split) or in FP64;
+//      tensor cores (hip_bk_tc.cu, tcgen05 kind::f16 on an exact three-slice
+//      BF16 split of X) or in FP64; for the anisotropic bispectrum the
+//      matching-m Gram blocks instead (hip_bk_aniso.cu);
 //   3. the C term from its moments, contracted in FP64 with the products
 //      jbar^a_l jbar^b_l, subtracted from the contraction.
 #pragma once
@@ -82,8 +84,9 @@ struct BkSeg {
 // Primaries per tensor-core stage for a launch whose largest n_k is nk_max.
 int hip_bk_tc_stage_prims(int nk_max);
 // Sum_p s_p X_p X_p^T over the segments (device-resident table) on the tensor
-// cores (tcgen05.mma kind::tf32, hi/lo split with the cross terms in their own
-// accumulators, folded into FP64 every fold_prims primaries, 0 = every stage).
+// cores (tcgen05.mma kind::f16 on an exact three-slice BF16 split of X, the six
+// slice products in three FP32 TMEM accumulators that stay exact, folded into
+// float-float rows every fold_prims primaries, 0 = every stage, and into FP64).
 // n_stages: total stages of all segments; status: device int, bit 0 set if a
 // bounded wait gave up (the results are then invalid).  max_grid caps the CTAs
 // (tests).  Supported for n_k <= 42 (hip_bk_tc_supported).
