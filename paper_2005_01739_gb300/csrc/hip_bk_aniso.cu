@@ -95,89 +95,138 @@ cudaError_t hip_upload_aniso_tables()
     return cudaMemcpyToSymbol(c_blk, &b, sizeof(b));
 }
 
-// The matching-m Gram: blockIdx.y = a chunk of HIP_AG_EPT * 256 output entries
-// (block, a, b), blockIdx.x = a slice of every segment's primaries.  A CTA stages
-// HIP_AG_PB primaries' rows of X (and s_p) in shared memory; each thread keeps
-// its entries as FP32 pairs (TwoSum-compensated sums of the rounded products
-// s_p X X), added to the FP64 G once at the end.
-#define HIP_AG_EPT 8
+// The matching-m Gram: thread t of blockIdx.y owns tile (blockIdx.y * 256 + t)
+// of the output, 4 x 4 entries (a0..a0+3, b0..b0+3) of one block; blockIdx.x
+// takes a slice of every segment's primaries.  A CTA stages HIP_AG_PB primaries'
+// rows of X (and s_p) in shared memory by asynchronous copies into two buffers
+// (the next stage lands while this one is used), each harmonic row padded to a multiple
+// of 4 bins (zeros), so a thread reads its 4 a values and 4 b values (and those
+// of -m) as two 16-byte loads per primary and forms 16 products from them.  The
+// products s_p X X are summed over the stage in FP32, the stage sums added to
+// FP32 pairs (TwoSum-compensated), and those to the FP64 G once at the end.
 #define HIP_AG_PB 16
+#define HIP_AG_T 4
+// 4-byte asynchronous copy global -> shared; n = 0 writes a zero (padding)
+__device__ __forceinline__ void ag_cp4(float *dst, const float *src, int n)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void ag_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void ag_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __global__ void __launch_bounds__(256) k_bk_aniso_gram(const BkSeg *__restrict__ segs, int n_segs, int nk_max)
 {
     extern __shared__ __align__(16) float ag_raw[];
-    const int row = HIP_NLM * nk_max;
-    float *Xs = ag_raw;                       // [HIP_AG_PB][25 nk]
-    float *ss = ag_raw + HIP_AG_PB * row;     // [HIP_AG_PB]
+    const int nkp_max = (nk_max + 3) & ~3;
+    const int buf = HIP_AG_PB * HIP_NLM * nkp_max + HIP_AG_PB;  // floats of one stage buffer
+    // buffer b: Xs at ag_raw + b buf ([HIP_AG_PB][25][nkp]), then the stage's s_p [HIP_AG_PB]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int sgi = 0; sgi < n_segs; ++sgi) {
         const BkSeg sg = segs[sgi];
-        const int nk = sg.n_k, n_ent = c_blk.n * nk * nk;
+        const int nk = sg.n_k, nkp = (nk + 3) & ~3, nt = nkp / HIP_AG_T, row = HIP_NLM * nkp;
         const float *X = (const float *)sg.X, *sp = (const float *)sg.sp;
-        int o1p[HIP_AG_EPT], o1n[HIP_AG_EPT], o2p[HIP_AG_EPT], o2n[HIP_AG_EPT];
-        bool neg[HIP_AG_EPT], use[HIP_AG_EPT];
-        float hi[HIP_AG_EPT], lo[HIP_AG_EPT];
+        const int tile = blockIdx.y * 256 + threadIdx.x;
+        const bool use = tile < c_blk.n * nt * nt;
+        const int q = use ? tile / (nt * nt) : 0, tab = use ? tile - q * nt * nt : 0;
+        const int a0 = (tab / nt) * HIP_AG_T, b0 = (tab - (tab / nt) * nt) * HIP_AG_T;
+        const int o1p = c_blk.r1p[q] * nkp + a0, o1n = c_blk.r1n[q] * nkp + a0;
+        const int o2p = c_blk.r2p[q] * nkp + b0, o2n = c_blk.r2n[q] * nkp + b0;
+        const bool neg = c_blk.neg[q];
+        float hi[HIP_AG_T][HIP_AG_T], lo[HIP_AG_T][HIP_AG_T];
 #pragma unroll
-        for (int k = 0; k < HIP_AG_EPT; ++k) {
-            const int e = (blockIdx.y * HIP_AG_EPT + k) * 256 + threadIdx.x;
-            use[k] = e < n_ent;
-            const int q = use[k] ? e / (nk * nk) : 0, ab = use[k] ? e - q * nk * nk : 0;
-            const int a = ab / nk, b = ab - a * nk;
-            o1p[k] = c_blk.r1p[q] * nk + a;
-            o1n[k] = c_blk.r1n[q] * nk + a;
-            o2p[k] = c_blk.r2p[q] * nk + b;
-            o2n[k] = c_blk.r2n[q] * nk + b;
-            neg[k] = c_blk.neg[q];
-            hi[k] = lo[k] = 0.0f;
-        }
-        const bool any = (blockIdx.y * HIP_AG_EPT) * 256 < n_ent;  // block-uniform
+        for (int i = 0; i < HIP_AG_T; ++i)
+#pragma unroll
+            for (int j = 0; j < HIP_AG_T; ++j) hi[i][j] = lo[i][j] = 0.0f;
+        const bool any = (blockIdx.y * 256) < c_blk.n * nt * nt;  // block-uniform
         const int per = (sg.n_p + gridDim.x - 1) / gridDim.x;
         const int p0 = blockIdx.x * per, p1 = min(sg.n_p, p0 + per);
-        for (int pb = p0; any && pb < p1; pb += HIP_AG_PB) {
+        // stage k (primaries p0 + k HIP_AG_PB ...) into buffer k & 1, one harmonic row of nk bins per warp
+        auto issue = [&](int pb, int b) {
             const int np = min(HIP_AG_PB, p1 - pb);
-            __syncthreads();
-            for (int i = threadIdx.x; i < np * HIP_NLM * nk; i += 256) {
-                const int pi = i / (HIP_NLM * nk), j = i - pi * HIP_NLM * nk;
-                Xs[pi * row + j] = X[(size_t)(pb + pi) * HIP_NLM * nk + j];
+            float *Xs = ag_raw + (size_t)b * buf;
+            const float *Xb = X + (size_t)pb * HIP_NLM * nk;
+            for (int r = warp; r < np * HIP_NLM; r += 8)
+                for (int c = lane; c < nkp; c += 32)
+                    ag_cp4(Xs + r * nkp + c, Xb + (size_t)r * nk + min(c, nk - 1), c < nk ? 4 : 0);
+            if (threadIdx.x < np) ag_cp4(Xs + HIP_AG_PB * row + threadIdx.x, sp + pb + threadIdx.x, 4);
+            ag_commit();
+        };
+        __syncthreads();  // the previous segment's last stage is done with both buffers
+        if (any && p0 < p1) issue(p0, 0);
+        for (int pb = p0, k = 0; any && pb < p1; pb += HIP_AG_PB, ++k) {
+            const int np = min(HIP_AG_PB, p1 - pb);
+            __syncthreads();  // every thread is done with stage k - 1, whose buffer the next copy takes
+            if (pb + HIP_AG_PB < p1) {
+                issue(pb + HIP_AG_PB, (k + 1) & 1);
+                ag_wait<1>();  // stage k has landed (k + 1 may be in flight)
+            } else {
+                ag_wait<0>();
             }
-            if (threadIdx.x < np) ss[threadIdx.x] = sp[pb + threadIdx.x];
-            __syncthreads();
+            __syncthreads();  // stage k is in shared memory for all threads
+            const float *Xs = ag_raw + (size_t)(k & 1) * buf, *ss = Xs + HIP_AG_PB * row;
+            if (!use) continue;
+            float st[HIP_AG_T][HIP_AG_T];
+#pragma unroll
+            for (int i = 0; i < HIP_AG_T; ++i)
+#pragma unroll
+                for (int j = 0; j < HIP_AG_T; ++j) st[i][j] = 0.0f;
             for (int pi = 0; pi < np; ++pi) {
                 const float s = ss[pi];
                 if (s == 0.0f) continue;  // excluded primary: its row of X is not written
                 const float *x = Xs + pi * row;
+                const float4 va = *reinterpret_cast<const float4 *>(x + o1p);
+                const float4 vb = *reinterpret_cast<const float4 *>(x + o2p);
+                const float ua[4] = {s * va.x, s * va.y, s * va.z, s * va.w}, ub[4] = {vb.x, vb.y, vb.z, vb.w};
 #pragma unroll
-                for (int k = 0; k < HIP_AG_EPT; ++k) {
-                    float u = x[o1p[k]] * x[o2p[k]];
-                    if (neg[k]) u = fmaf(x[o1n[k]], x[o2n[k]], u);
-                    const float v = s * u;
-                    const float t = hi[k] + v, bv = t - hi[k];
-                    lo[k] += (hi[k] - (t - bv)) + (v - bv);
-                    hi[k] = t;
+                for (int i = 0; i < HIP_AG_T; ++i)
+#pragma unroll
+                    for (int j = 0; j < HIP_AG_T; ++j) st[i][j] = fmaf(ua[i], ub[j], st[i][j]);
+                if (neg) {
+                    const float4 wa = *reinterpret_cast<const float4 *>(x + o1n);
+                    const float4 wb = *reinterpret_cast<const float4 *>(x + o2n);
+                    const float za[4] = {s * wa.x, s * wa.y, s * wa.z, s * wa.w}, zb[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                    for (int i = 0; i < HIP_AG_T; ++i)
+#pragma unroll
+                        for (int j = 0; j < HIP_AG_T; ++j) st[i][j] = fmaf(za[i], zb[j], st[i][j]);
                 }
             }
-        }
 #pragma unroll
-        for (int k = 0; k < HIP_AG_EPT; ++k) {
-            const double v = (double)hi[k] + (double)lo[k];
-            if (use[k] && v != 0.0) {
-                const int e = (blockIdx.y * HIP_AG_EPT + k) * 256 + threadIdx.x;
-                atomicAdd(&sg.acc[e], v);
-            }
+            for (int i = 0; i < HIP_AG_T; ++i)
+#pragma unroll
+                for (int j = 0; j < HIP_AG_T; ++j) {  // the stage's sum into hi + lo (TwoSum)
+                    const float t = hi[i][j] + st[i][j], bv = t - hi[i][j];
+                    lo[i][j] += (hi[i][j] - (t - bv)) + (st[i][j] - bv);
+                    hi[i][j] = t;
+                }
         }
+        if (use)
+#pragma unroll
+            for (int i = 0; i < HIP_AG_T; ++i)
+#pragma unroll
+                for (int j = 0; j < HIP_AG_T; ++j) {
+                    const double v = (double)hi[i][j] + (double)lo[i][j];
+                    if (a0 + i < nk && b0 + j < nk && v != 0.0)
+                        atomicAdd(&sg.acc[((size_t)q * nk + a0 + i) * nk + b0 + j], v);
+                }
     }
 }
 
 cudaError_t hip_bk_aniso_gram(const BkSeg *segs, int n_segs, int nk_max, long long max_prims, cudaStream_t st)
 {
-    const size_t smem = sizeof(float) * ((size_t)HIP_AG_PB * HIP_NLM * nk_max + HIP_AG_PB);
+    const int nkp = (nk_max + 3) & ~3, nt = nkp / HIP_AG_T;
+    const size_t smem = 2 * sizeof(float) * ((size_t)HIP_AG_PB * HIP_NLM * nkp + HIP_AG_PB);  // two stages
     cudaError_t e = cudaFuncSetAttribute(k_bk_aniso_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int n_ent = HIP_ANISO_NBLK * nk_max * nk_max;
-    const int chunks = (n_ent + HIP_AG_EPT * 256 - 1) / (HIP_AG_EPT * 256);
+    const int chunks = (HIP_ANISO_NBLK * nt * nt + 255) / 256;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // about 4 CTAs per SM in all; each slice keeps at least a few stages of primaries
-    long long slices = std::max(1LL, (long long)4 * sms / chunks);
+    // about 2 CTAs per SM in all (the two stage buffers); each slice keeps at least a few stages
+    long long slices = std::max(1LL, (long long)2 * sms / chunks);
     slices = std::min(slices, std::max(1LL, max_prims / (4 * HIP_AG_PB)));
     k_bk_aniso_gram<<<dim3((unsigned)slices, chunks), 256, smem, st>>>(segs, n_segs, nk_max);
     return cudaGetLastError();

@@ -18,11 +18,11 @@
 // n_c >= R0 k_max / 4, k h <= 2 and the first neglected term (m = 16) is below
 // ~4e-13 of f: exact for both precisions.  The moments are those of the scaled
 // polynomials R_m = d_m P_m, whose recurrence has exact constants.  The FP32
-// path keeps per CTA in shared memory each moment as a grid-rounded sum (exact)
-// plus a remainder sum, folded into FP64 every HIP_PM_FOLD pairs; the per-pair
-// terms are formed without an error common to many pairs (exact interval
-// origins, split reciprocals, exact recurrence constants), so what FP32 leaves
-// is rounding that averages out over the pairs.
+// path keeps per CTA in shared memory each moment as an exact fixed-point sum
+// (two 32-bit integer words, hip_pm_add), folded into FP64 every HIP_PM_FOLD
+// pairs; the per-pair terms are formed without an error common to many pairs
+// (exact interval origins, split reciprocals, exact recurrence constants), so
+// what FP32 leaves is rounding that averages out over the pairs.
 #define HIP_PAIR_UPLOAD hip_upload_coeffs_moments
 #include "hip_pair_kernel.cuh"
 
@@ -146,26 +146,51 @@ __host__ __device__ constexpr int hip_pm_words(int n_cp)
 }
 
 // Shared moment add of a run sum v.  FP32: x = v C (C = 2^s, the catalog's
-// units per value of this moment order) rounded to an integer; for |x| <= 2^33,
-// x = 2^17 a + b with b in [0, 2^17): a goes to the signed word at M, b to the
-// unsigned word at M + lo_off, and with fewer than 2^15 adds between folds
-// neither word leaves its range; a and b are read from the significands of
-// their sums with 1.5 2^23 (no conversion instruction).  With CHECK a larger
-// run sum (far above the catalog's typical term) goes to the FP64 total G[gi]
-// instead; the drain takes the unchecked form when a bound on its run sums
-// rules that out (hip_pm_walk).
+// units per value of this moment order, so x is exact); for |x| <= 2^33 it is
+// rounded to the integer 2^17 a + b with a = rint(x 2^-17) and b = rint(x - 2^17 a)
+// in [-2^16, 2^16]: a goes to the word at M, b to the word at M + lo_off (both
+// signed), and with fewer than 2^15 adds between folds neither sum leaves the
+// int32 range.  Both roundings are additions of 1.5 2^23 (the integer lands in
+// the low significand bits, read back by one integer subtraction), and
+// x - 2^17 a is exact (at most 2^16 in magnitude and a multiple of x's last
+// place).  With CHECK a larger run sum (far above the catalog's typical term)
+// goes to the FP64 total G[gi] instead; the drain takes the unchecked form when
+// a bound on its run sums rules that out (hip_pm_walk).
 template <bool CHECK>
 __device__ __forceinline__ void hip_pm_add(unsigned *M, float v, int lo_off, float C, double *G, int gi)
 {
-    const float x = rintf(v * C);
+    const float x = __fmul_rn(v, C);
     if (CHECK && !(fabsf(x) <= 8589934592.0f)) {  // 2^33
         atomicAdd(G + gi, (double)v);
         return;
     }
-    const float a = floorf(x * 7.62939453125e-06f);  // 2^-17
-    const float b = fmaf(a, -131072.0f, x);           // exact, in [0, 2^17)
-    atomicAdd(reinterpret_cast<int *>(M), __float_as_int(__fadd_rn(a, 12582912.0f)) - 0x4B400000);
-    atomicAdd(M + lo_off, (unsigned)(__float_as_int(__fadd_rn(b, 12582912.0f)) - 0x4B400000));
+    const float ab = fmaf(x, 7.62939453125e-06f, 12582912.0f);  // 1.5 2^23 + rint(x 2^-17)
+    const float a = __fsub_rn(ab, 12582912.0f);                  // exact
+    const float bb = __fadd_rn(fmaf(a, -131072.0f, x), 12582912.0f);
+    atomicAdd(reinterpret_cast<int *>(M), __float_as_int(ab) - 0x4B400000);
+    atomicAdd(reinterpret_cast<int *>(M) + lo_off, __float_as_int(bb) - 0x4B400000);
+}
+// The same add shared by the two lanes of a pair that hold the same v (the l = 4
+// sums of moment m sit in lanes m and 16 + m): lane g = 0 adds the word at M,
+// g = 1 the word at M + lo_off, so one atomic instruction of the warp covers
+// both words of all 16 sums.
+template <bool CHECK>
+__device__ __forceinline__ void hip_pm_add_half(unsigned *M, float v, int lo_off, float C, double *G, int gi, int g)
+{
+    const float x = __fmul_rn(v, C);
+    if (CHECK && !(fabsf(x) <= 8589934592.0f)) {  // 2^33
+        if (g == 0) atomicAdd(G + gi, (double)v);
+        return;
+    }
+    const float ab = fmaf(x, 7.62939453125e-06f, 12582912.0f);
+    const float a = __fsub_rn(ab, 12582912.0f);
+    const float bb = __fadd_rn(fmaf(a, -131072.0f, x), 12582912.0f);
+    atomicAdd(reinterpret_cast<int *>(M) + (g ? lo_off : 0), __float_as_int(g ? bb : ab) - 0x4B400000);
+}
+template <bool CHECK>
+__device__ __forceinline__ void hip_pm_add_half(double *M, double v, int, float, double *, int, int g)
+{
+    if (g == 0) atomicAdd(M, v);
 }
 template <bool CHECK>
 __device__ __forceinline__ void hip_pm_add(double *M, double v, int, float, double *, int)
@@ -176,7 +201,7 @@ __device__ __forceinline__ void hip_pm_add(double *M, double v, int, float, doub
 // Value of moment word i (n words per part) as FP64, clearing it.
 __device__ __forceinline__ double hip_pm_take(unsigned *M, int i, int n, float C)
 {
-    const double v = ((double)(int)M[i] * 131072.0 + (double)M[i + n]) * (double)(1.0f / C);  // C = 2^s
+    const double v = ((double)(int)M[i] * 131072.0 + (double)(int)M[i + n]) * (double)(1.0f / C);  // C = 2^s
     M[i] = 0u;
     M[i + n] = 0u;
     return v;
@@ -210,6 +235,7 @@ struct PmScale {
 // current catalog and the per-warp pair counts since the last count.
 struct PmEpoch {
     int drained[HIP_PM_MAXW];
+    int row;  // next home row of the current tile pair (taken by the warps one at a time)
     float C[HIP_PM_M];
     float Smax;  // a drain whose sum of |omega| is at most this keeps every run sum below 2^32 units
 };
@@ -222,8 +248,10 @@ struct PmShift {
 
 // The moment walk of a drain: lane 16 g + m runs over the n staged pairs in
 // interval order with register sums and adds a sum to the moment array once per
-// interval run (g = 0: l = 0 and l = 4, g = 1: l = 2).
-template <typename T, int MASK, bool CHECK>
+// interval run (g = 0: l = 0, g = 1: l = 2, and both l = 4, whose two words the
+// lane pair m, 16 + m adds with one atomic instruction), unrolled UNR times (the
+// batched kernel, short of registers, takes 4, the single-catalog one 8).
+template <typename T, int MASK, bool CHECK, int UNR>
 __device__ __forceinline__ void hip_pm_walk(const PmStage<T> &sg, int n, int lane, PmA<T> *M, int n_cp, int n_c,
                                             const float *Cg, double *Mg)
 {
@@ -231,18 +259,18 @@ __device__ __forceinline__ void hip_pm_walk(const PmStage<T> &sg, int n, int lan
     PmA<T> *Ma = M + (size_t)(g * HIP_PM_M + m) * n_cp;
     PmA<T> *Mb = M + (size_t)(2 * HIP_PM_M + m) * n_cp;
     const bool use_a = (g == 0) || (MASK & 4);
-    const bool use_b = (g == 0) && (MASK & 16);
+    const bool use_b = (MASK & 16) != 0;  // both lanes m and 16 + m sum l = 4 of moment m
     const int lo_off = 3 * HIP_PM_M * n_cp;
     const float C = Cg[m];
     const int ga = (g * HIP_PM_M + m) * n_c, gb = (2 * HIP_PM_M + m) * n_c;  // rows of the FP64 totals
     T sa = T(0), sb = T(0);
     int cur = sg.row[0].c;
-#pragma unroll 4
+#pragma unroll UNR
     for (int s = 0; s < n; ++s) {
         const PmRow<T> r = sg.row[s];
         if (r.c != cur) {  // warp-uniform
             if (use_a) hip_pm_add<CHECK>(Ma + cur, sa, lo_off, C, Mg, ga + cur);
-            if (use_b) hip_pm_add<CHECK>(Mb + cur, sb, lo_off, C, Mg, gb + cur);
+            if (use_b) hip_pm_add_half<CHECK>(Mb + cur, sb, lo_off, C, Mg, gb + cur, g);
             sa = T(0);
             sb = T(0);
             cur = r.c;
@@ -252,7 +280,7 @@ __device__ __forceinline__ void hip_pm_walk(const PmStage<T> &sg, int n, int lan
         sb += r.o4 * p;
     }
     if (use_a) hip_pm_add<CHECK>(Ma + cur, sa, lo_off, C, Mg, ga + cur);
-    if (use_b) hip_pm_add<CHECK>(Mb + cur, sb, lo_off, C, Mg, gb + cur);
+    if (use_b) hip_pm_add_half<CHECK>(Mb + cur, sb, lo_off, C, Mg, gb + cur, g);
 }
 
 // Moments of the n (1..32) queued pairs at ring positions head, head + 1, ...:
@@ -263,7 +291,7 @@ __device__ __forceinline__ void hip_pm_walk(const PmStage<T> &sg, int n, int lan
 // over the moments (lane = 16 g + m: g = 0 sums l = 0 and l = 4, g = 1 sums
 // l = 2), walk the sorted pairs with register sums, and add a sum to the shared
 // array once per interval run, at 48 distinct addresses.
-template <typename T, int MASK>
+template <typename T, int MASK, int UNR>
 __device__ __forceinline__ void hip_pm_drain(PmStage<T> &sg, const PmTiles<T> &tl, const PmShift<T> &sh, int los,
                                              int head, int n, int lane, PmA<T> *M, int n_cp, int n_c,
                                              const PmScale<T> &ps, const float *Cg, float Smax, double *Mg,
@@ -334,9 +362,9 @@ __device__ __forceinline__ void hip_pm_drain(PmStage<T> &sg, const PmTiles<T> &t
     for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
     __syncwarp();
     if (sizeof(T) == 8 || S <= T(Smax))  // warp-uniform
-        hip_pm_walk<T, MASK, false>(sg, n, lane, M, n_cp, n_c, Cg, Mg);
+        hip_pm_walk<T, MASK, false, UNR>(sg, n, lane, M, n_cp, n_c, Cg, Mg);
     else
-        hip_pm_walk<T, MASK, true>(sg, n, lane, M, n_cp, n_c, Cg, Mg);
+        hip_pm_walk<T, MASK, true, UNR>(sg, n, lane, M, n_cp, n_c, Cg, Mg);
     __syncwarp();
 }
 
@@ -401,11 +429,13 @@ __device__ __forceinline__ void hip_pm_units(PmEpoch &ep, const double *wabs, lo
 }
 
 // One work item (home cell, half-shell shift; item counts within the catalog):
-// the CTA stages the two cells' tiles, its warps split the home particles, test
+// the CTA stages the two cells' tiles, its warps take the home particles (DYN:
+// one at a time from a shared counter, so that they reach the next barrier
+// together; else warp w takes w, w + NW, ...: cheaper on small tiles), test
 // candidates one per lane and queue the accepted ones as tile indices; 32
 // queued pairs (and whatever is queued when a tile pair is done) are drained
 // into the CTA's moment array M.  Called by all threads of the CTA.
-template <typename T, int MASK, int NW>
+template <typename T, int MASK, int NW, bool DYN>
 __device__ __forceinline__ void hip_pm_item(const CellList<T> &cl, long long p0, long long p1, int los, int item,
                                             PmTiles<T> &tl, PmStage<T> &sg, PmEpoch &ep, PmA<T> *M, int n_cp, int n_c,
                                             T R0, T dc, double *Mg, unsigned long long &cnt, int &drained,
@@ -446,6 +476,7 @@ __device__ __forceinline__ void hip_pm_item(const CellList<T> &cl, long long p0,
             drained = 0;
             __syncthreads();
             hip_pm_count<T>(ep, M, n_cp, n_c, Mg, since_fold, fold);
+            if (threadIdx.x == 0) ep.row = 0;
             for (int i = threadIdx.x; i < nn; i += blockDim.x) {
                 const long long oi = cl.idx[nbs + i];
                 PmPt<T> p;
@@ -460,7 +491,12 @@ __device__ __forceinline__ void hip_pm_item(const CellList<T> &cl, long long p0,
             const bool same = self && (nbs == hb);
             int qn = 0;  // queued pairs of this warp (ring head 0 after each partial drain)
             int qh = 0;
-            for (int il = warp; il < hn; il += NW) {
+            for (int il = warp;;) {  // DYN: home rows one at a time from the shared counter
+                if (DYN) {
+                    if (lane == 0) il = atomicAdd(&ep.row, 1);
+                    il = __shfl_sync(0xffffffffu, il, 0);
+                }
+                if (il >= hn) break;
                 const PmPt<T> h = tl.h[il];
                 const T xi = h.x - sh.x, yi = h.y - sh.y, zi = h.z - sh.z;
                 const int ini = (int)h.in;
@@ -480,16 +516,18 @@ __device__ __forceinline__ void hip_pm_item(const CellList<T> &cl, long long p0,
                     qn += __popc(bal);
                     if (qn >= 32) {
                         __syncwarp();
-                        hip_pm_drain<T, MASK>(sg, tl, sh, los, qh, 32, lane, M, n_cp, n_c, ps, ep.C, ep.Smax, Mg, cnt);
+                        hip_pm_drain<T, MASK, DYN ? 8 : 4>(sg, tl, sh, los, qh, 32, lane, M, n_cp, n_c, ps, ep.C,
+                                                           ep.Smax, Mg, cnt);
                         qh = (qh + 32) & (HIP_PM_QCAP - 1);
                         qn -= 32;
                         drained += 32;
                     }
                 }
+                if (!DYN) il += NW;
             }
             if (qn > 0) {  // the tiles change after this tile pair
                 __syncwarp();
-                hip_pm_drain<T, MASK>(sg, tl, sh, los, qh, qn, lane, M, n_cp, n_c, ps, ep.C, ep.Smax, Mg, cnt);
+                hip_pm_drain<T, MASK, DYN ? 8 : 4>(sg, tl, sh, los, qh, qn, lane, M, n_cp, n_c, ps, ep.C, ep.Smax, Mg, cnt);
                 drained += qn;
             }
         }
@@ -526,7 +564,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW)  // <= 64 registers: 32 warp
         __syncthreads();
         const int item = s_item;
         if (item >= a.n_items) break;
-        hip_pm_item<T, MASK, NW>(cl, a.p0, a.p1, a.los, item, tl, stages[warp], ep, M, n_cp, n_c, R0, dc, Mr, cnt,
+        hip_pm_item<T, MASK, NW, true>(cl, a.p0, a.p1, a.los, item, tl, stages[warp], ep, M, n_cp, n_c, R0, dc, Mr, cnt,
                                  drained, since_fold, HIP_PM_FOLD);
     }
     __syncthreads();
@@ -584,7 +622,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW)
             __syncthreads();
             if (threadIdx.x < HIP_PM_M) hip_pm_units(ep, cat.Mg + hip_pm_mg_doubles(cat.n_c) - 1, cat.n_part);
         }
-        hip_pm_item<T, 21, NW>(cat.cl, cat.p0, cat.p1, cat.los, item - cat.item_begin, tl, stages[warp], ep, M,
+        hip_pm_item<T, 21, NW, false>(cat.cl, cat.p0, cat.p1, cat.los, item - cat.item_begin, tl, stages[warp], ep, M,
                            cat.n_c | 1, cat.n_c, cat.R0, cat.dc,
                            cat.Mg + (size_t)(blockIdx.x % HIP_PM_REPL) * 3 * HIP_PM_M * cat.n_c, cnt, drained,
                            since_fold, fold);

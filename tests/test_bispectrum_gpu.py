@@ -199,7 +199,7 @@ def _aniso_case():
 def test_bispectrum_aniso_parity():
     # every (l1, l2, L) combination against the oracle's per-primary Wigner-3j form
     pos, w, rnd, L, R0 = _aniso_case()
-    edges = catalogs.linear_edges(0.3, 2.0, 8)
+    edges = catalogs.linear_edges(0.3, 2.0, 9)  # 9 bins: the Gram's 4 x 4 tiles have a ragged edge
     Bref, info = oracle.bispectrum_aniso(pos.astype(np.float64), w.astype(np.float64), rnd.astype(np.float64),
                                          L, R0, edges)
     assert tuple(binding.ANISO_COMBOS) == tuple(oracle.ANISO_COMBOS)
@@ -216,7 +216,7 @@ def test_bispectrum_aniso_l0_matches_isotropic_path():
     # (l, l, 0) = (-1)^l sqrt(2l+1) B_l: the matching-m Gram and the tensor-core contraction of
     # the isotropic path give the same primary sums
     pos, w, rnd, L, R0 = _case(seed=43, N=2000, weights="u05_15")
-    edges = catalogs.linear_edges(0.3, 2.4, 16)
+    edges = catalogs.linear_edges(0.3, 2.4, 15)
     dpos, dw, drnd = _dev(pos), _dev(w), _dev(rnd)
     Bi, _ = binding.hip_bispectrum(dpos, dw, drnd, L, R0, edges, 4, "mixed")
     Ba, _ = binding.hip_bispectrum_aniso(dpos, dw, drnd, L, R0, edges)
