@@ -45,9 +45,9 @@ UNIT = "pairs*kbins/s"
 WORKLOAD = "pk_mixed_n2e6"
 FLOPS_PER_PAIR_BIN = 12.0  # nominal algorithmic FP32 flops per (unordered pair, k bin)
 # DRAM bytes (read + write) of one pair-pass launch on the 2e6-particle workload: ncu measured
-# 5.46 MB for the moment pass (5.18 MB for the direct pass) on the same workload shrunk to 2.5e5
+# 5.464 MB for the moment pass (5.18 MB for the direct pass) on the same workload shrunk to 2.5e5
 # particles; the traffic is the particle data read once, so it scales with N: x 8.
-PAIR_KERNEL_DRAM_BYTES = {1: 5.46e6 * 8, 0: 5.18e6 * 8}
+PAIR_KERNEL_DRAM_BYTES = {1: 5.464e6 * 8, 0: 5.18e6 * 8}
 PAIR_KERNEL_NAME = {1: "k_power_moments<float,21,8>", 0: "k_power_pairs<float,4,21>"}
 # kernels one FP32 hip_power call launches: cell build 3, pair pass (moments: coefficients, sum |w|,
 # pairs, contraction) 4 or 1, finalize 2
