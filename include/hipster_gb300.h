@@ -305,8 +305,7 @@ const char *hip_batch_message(void);
  * (36 for host positions, 40 with host weights), plus cell tables and per-CTA partial sums; a call that
  * would not fit returns HIP_ERR_RANGE and hip_noalloc_message() says how many
  * bytes it needed.  The array's device address is looked up on the first call
- * made with each device current: make that first call before any stream
- * capture.  Every call shares the array (it keeps the previous call's
+ * made with each device current.  Every call shares the array (it keeps the previous call's
  * contents; each call clears what must start at zero); calls that overlapped
  * on the GPU would race on it, so this entry point serialises its calls and
  * synchronises `cuda_stream` before returning, on success and on failure.

@@ -14,8 +14,8 @@
 //
 // The array below is reserved on every device that loads this library, for the
 // lifetime of the process.  Its device address is looked up once per device
-// (cudaGetSymbolAddress) on the first call made with that device current; make
-// that first call before any stream capture.  Every call reuses the same array
+// (cudaGetSymbolAddress) on the first call made with that device current.
+// Every call reuses the same array
 // and it keeps the previous call's contents, so each call clears the counters
 // and accumulators it needs.  Calls must not overlap on the GPU: two calls whose
 // kernels ran at the same time would race on the array.  This entry point
