@@ -129,6 +129,35 @@ hip_status hip_bispectrum(const float *pos, const float *w, int64_t N, const flo
                           double R0, hip_window window, const double *k_edges, int n_k, int lmax, hip_precision prec,
                           double *B_out, int64_t *npairs_out, void *cuda_stream);
 
+/* A uniform random catalog in the box, for the DDR^II term's random catalog
+ * (Sec. 4.3; the paper uses f_rand = N_r / N = 3, Sec. 9).  Coordinate d of
+ * random j is out[3j + d] = fl(u * fl(L)), u = (z >> 40) * 2^-24 in [0, 1) with z
+ * output 3j + d + 1 of SplitMix64 seeded with `seed` (the generator and
+ * constants of hip_subsample); u is exact in float32 and the product is rounded
+ * once (round to nearest), so the catalog is the same on every machine.  Every
+ * value lies in [0, fl(L)): u fl(L) <= fl(L) - fl(L) 2^-24, more than half a
+ * unit in the last place below fl(L) unless fl(L) is a power of two, where it
+ * is a float.
+ *
+ *   out         [N_r][3] float32, host or device, caller-owned
+ *   N_r         number of randoms, 0 .. 2e9 (0 writes nothing)
+ *   L           box side (> 0, finite, below the float32 range)
+ *   seed        generator seed
+ *   cuda_stream stream to run on; the call returns after `out` is written
+ * Errors: HIP_ERR_ARG (NULL out, N_r out of range), HIP_ERR_RANGE (L), HIP_ERR_CUDA. */
+hip_status hip_uniform_randoms(float *out, int64_t N_r, double L, uint64_t seed, void *cuda_stream);
+
+/* hip_bispectrum with a seeded random catalog instead of a caller-supplied one:
+ * the N_r randoms are those hip_uniform_randoms(., N_r, L, rand_seed) writes,
+ * generated on the device into a buffer the library keeps per device (grown on
+ * demand, never freed before exit), then the same computation as hip_bispectrum
+ * (identical results for the same randoms).  Calls through this entry point are
+ * serialised on the host.  Arguments and errors as in hip_bispectrum, with
+ * N_r >= 1 and rand_seed in place of rand_pos. */
+hip_status hip_bispectrum_seeded(const float *pos, const float *w, int64_t N, int64_t N_r, uint64_t rand_seed,
+                                 double L, double R0, hip_window window, const double *k_edges, int n_k, int lmax,
+                                 hip_precision prec, double *B_out, int64_t *npairs_out, void *cuda_stream);
+
 /* Anisotropic bispectrum multipoles about the line of sight zhat: the extension
  * proposed in the paper's conclusions (the sum over spherical harmonics of the
  * isotropic estimator replaced by a product of two harmonics of different

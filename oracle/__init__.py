@@ -21,8 +21,9 @@ What is computed, and where each piece comes from:
   and the random-free DDR^II term of App. A: omega^a_l (Eq. omega-ell-a-def),
   the kernel E^{II,ab}_l(r) = int p^2 dp/(2 pi^2) j_0(p r) omega^a_l omega^b_l and
   the pair sum over it, with the bipolar form of App. B for cross-checks;
-  the random subsample of Sec. 9 (a fraction 1/f_sub of the tracers), drawn
-  with SplitMix64 written here from its published definition; and the
+  the random subsample of Sec. 9 (a fraction 1/f_sub of the tracers) and a
+  seeded uniform random catalog, both drawn with SplitMix64 written here from
+  its published definition; and the
   anisotropic bispectrum the conclusions propose (two harmonics of different
   order about the line of sight), in the reading written out above
   `ANISO_COMBOS`: per-primary a_lm in complex harmonics coupled by Wigner 3j
@@ -416,6 +417,16 @@ def subsample_mask(n: int, fraction: float, seed: int) -> np.ndarray:
     import math
     thr = np.uint64(math.floor(math.ldexp(float(fraction), 53)))
     return (splitmix64(seed, n) >> np.uint64(11)) < thr
+
+
+def uniform_randoms(n: int, L: float, seed: int) -> np.ndarray:
+    """A seeded uniform random catalog for the DDR^II term's random catalog
+    (Sec. 4.3): coordinate d of random j is fl32(u * fl32(L)) with
+    u = (z >> 40) 2^-24, z output 3j + d + 1 of SplitMix64; u is exact in
+    float32 and the product is one IEEE float32 multiplication."""
+    z = splitmix64(seed, 3 * int(n))
+    u = (z >> np.uint64(40)).astype(np.float32) * np.float32(2.0 ** -24)
+    return (u * np.float32(L)).astype(np.float32).reshape(int(n), 3)
 
 
 # ------------------------------------ anisotropic bispectrum (Sec. 10 extension) --

@@ -76,6 +76,10 @@ def load(path: str | None = None):
         L.hip_window_omega.argtypes = [P, i, d, i, P, i, P, P]
         L.hip_subsample.restype = i
         L.hip_subsample.argtypes = [P, P, i64, d, ctypes.c_uint64, P, P, P, P]
+        L.hip_uniform_randoms.restype = i
+        L.hip_uniform_randoms.argtypes = [P, i64, d, ctypes.c_uint64, P]
+        L.hip_bispectrum_seeded.restype = i
+        L.hip_bispectrum_seeded.argtypes = [P, P, i64, i64, ctypes.c_uint64, d, d, i, P, i, i, i, P, P, P]
         L.hip_noalloc_capacity.restype = ctypes.c_size_t
         L.hip_noalloc_capacity.argtypes = []
         L.hip_noalloc_message.restype = ctypes.c_char_p
@@ -386,6 +390,41 @@ def hip_bispectrum(pos, w, rand_pos, L, R0, k_edges, lmax=4, prec="mixed", strea
                             _stream_handle(stream))
     _check(lib, rc, "hip_bispectrum")
     del keep_p, keep_w, keep_r
+    return B, (int(npairs[0]), int(npairs[1]))
+
+
+def hip_uniform_randoms(n_r, L, seed, device=None, stream=None):
+    """Uniform random catalog [n_r, 3] float32 from SplitMix64 (hip_uniform_randoms):
+    a torch tensor on `device` when given, else numpy."""
+    lib = load()
+    if device is not None:
+        import torch
+        out = torch.empty((int(n_r), 3), dtype=torch.float32, device=device)
+    else:
+        out = np.empty((int(n_r), 3), dtype=np.float32)
+    po, keep = _ptr(out)
+    rc = lib.hip_uniform_randoms(po, int(n_r), float(L), int(seed) & 0xFFFFFFFFFFFFFFFF, _stream_handle(stream))
+    _check(lib, rc, "hip_uniform_randoms")
+    del keep
+    return out
+
+
+def hip_bispectrum_seeded(pos, w, n_r, rand_seed, L, R0, k_edges, lmax=4, prec="mixed", stream=None):
+    """hip_bispectrum with the random catalog hip_uniform_randoms(n_r, L, rand_seed)
+    generated on the device.  Same returns as hip_bispectrum."""
+    lib = load()
+    n = int(pos.shape[0]) if hasattr(pos, "shape") else len(pos)
+    pp, keep_p = _ptr(pos)
+    wp, keep_w = _ptr(w)
+    edges = np.ascontiguousarray(np.asarray(k_edges, dtype=np.float64))
+    n_k = len(edges) - 1
+    B = np.zeros((lmax + 1, n_k, n_k))
+    npairs = (ctypes.c_int64 * 2)()
+    rc = lib.hip_bispectrum_seeded(pp, wp, n, int(n_r), int(rand_seed) & 0xFFFFFFFFFFFFFFFF, float(L), float(R0), 0,
+                                   edges.ctypes.data_as(ctypes.c_void_p), n_k, int(lmax), PREC[prec],
+                                   B.ctypes.data_as(ctypes.c_void_p), npairs, _stream_handle(stream))
+    _check(lib, rc, "hip_bispectrum_seeded")
+    del keep_p, keep_w
     return B, (int(npairs[0]), int(npairs[1]))
 
 

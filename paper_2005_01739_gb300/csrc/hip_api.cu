@@ -809,6 +809,56 @@ extern "C" hip_status hip_bispectrum(const float *pos, const float *w, int64_t N
                                nullptr, false);
 }
 
+// hip_bispectrum with its random catalog generated on the device from a seed
+// (hip_uniform_randoms' mapping) into a buffer the library keeps per device and
+// grows on demand; calls through this entry point are serialised on the host.
+extern "C" hip_status hip_bispectrum_seeded(const float *pos, const float *w, int64_t N, int64_t N_r,
+                                            uint64_t rand_seed, double L, double R0, hip_window window,
+                                            const double *k_edges, int n_k, int lmax, hip_precision prec,
+                                            double *B_out, int64_t *npairs_out, void *cuda_stream)
+{
+    g_errbuf[0] = 0;
+    if (N_r < 1 || N_r > 2000000000LL) return HIP_ERR_ARG;
+    if (!(L > 0.0) || !std::isfinite(L)) return HIP_ERR_RANGE;
+    static std::mutex mu;
+    static float *buf[64] = {nullptr};
+    static size_t cap[64] = {0};
+    std::lock_guard<std::mutex> lk(mu);
+    int dev = 0;
+    {
+        std::lock_guard<std::mutex> lk2(hip_api_mutex());
+        hip_status hs = hip_device_setup(&dev);
+        if (hs != HIP_OK) return hs;
+    }
+    if (dev < 0 || dev >= 64) return HIP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t need = sizeof(float) * 3 * (size_t)N_r;
+    cudaError_t e = cudaSuccess;
+    if (cap[dev] < need) {
+        if (buf[dev]) {
+            e = cudaStreamSynchronize(st);  // the previous call's launches have finished with the buffer
+            if (e == cudaSuccess) e = cudaFree(buf[dev]);
+            buf[dev] = nullptr;
+            cap[dev] = 0;
+        }
+        if (e == cudaSuccess) e = cudaMalloc((void **)&buf[dev], need);
+        if (e != cudaSuccess) {
+            buf[dev] = nullptr;
+            set_err("random catalog buffer", e);
+            cudaGetLastError();
+            return HIP_ERR_CUDA;
+        }
+        cap[dev] = need;
+    }
+    if ((e = hip_launch_uniform_randoms(buf[dev], N_r, L, rand_seed, st)) != cudaSuccess) {
+        set_err("uniform randoms", e);
+        cudaGetLastError();
+        return HIP_ERR_CUDA;
+    }
+    return hip_bispectrum(pos, w, N, buf[dev], N_r, L, R0, window, k_edges, n_k, lmax, prec, B_out, npairs_out,
+                          cuda_stream);
+}
+
 extern "C" hip_status hip_bispectrum_aniso(const float *pos, const float *w, int64_t N, const float *rand_pos,
                                            int64_t N_r, double L, double R0, hip_window window,
                                            const double *k_edges, int n_k, double *B_out, int64_t *npairs_out,

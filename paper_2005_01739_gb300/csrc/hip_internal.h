@@ -154,6 +154,10 @@ cudaError_t hip_power_finalize(const double *partials, int nparts, int n_e, int 
                                cudaStream_t st);
 // W~^a alone (n_e edges, host array), into Wt [n_e - 1] on the device.
 cudaError_t hip_window_transform(int n_e, const double *kedges_host, double R0, double *Wt, cudaStream_t st);
+// n_r uniform randoms in [0, L)^3 from SplitMix64 (hip_subsample.cu; the mapping is
+// documented at hip_uniform_randoms) into the device array d_out [n_r][3].
+cudaError_t hip_launch_uniform_randoms(float *d_out, long long n_r, double L, unsigned long long seed,
+                                       cudaStream_t st);
 // P [n_ell][n_k] from summed DD [n_ell][n_k] and W~ (device arrays), S1 = sum of all weights.
 cudaError_t hip_power_from_dd(const double *DD, int n_k, int n_ell, double L, double S1, const double *Wt, double *P,
                               cudaStream_t st);

@@ -14,6 +14,7 @@
 // the ordered scatter (each block re-derives its flags and ranks them with warp
 // ballots).  All are HBM-bound: 12 (16 with weights) bytes read per particle and
 // as many written per kept particle.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -26,13 +27,47 @@ std::mutex &hip_api_mutex();
 #define HIP_SUB_ITEMS 16  // particles per thread per block pass
 #define HIP_SUB_CHUNK (HIP_SUB_THREADS * HIP_SUB_ITEMS)
 
-__device__ __forceinline__ bool hip_sub_keep(unsigned long long seed, unsigned long long i, unsigned long long thr)
+// Output i + 1 of SplitMix64 seeded with `seed` (i = 0, 1, ...).
+__device__ __forceinline__ unsigned long long hip_sm64(unsigned long long seed, unsigned long long i)
 {
     unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return (z >> 11) < thr;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ bool hip_sub_keep(unsigned long long seed, unsigned long long i, unsigned long long thr)
+{
+    return (hip_sm64(seed, i) >> 11) < thr;
+}
+
+// Uniform random catalog (the random catalog of the DDR^II term, Sec. 4.3):
+// coordinate d of random j is out[3 j + d] = u L with u = (z_i >> 40) 2^-24, z_i
+// output i + 1 of SplitMix64 for i = 3 j + d, and the product rounded once to
+// float (u is exact in float, L is taken as a float).  Grid-stride, HBM-bound
+// (12 bytes written per random).
+__global__ void __launch_bounds__(HIP_SUB_THREADS) k_uniform_randoms(float *out, long long n3,
+                                                                     unsigned long long seed, float Lf)
+{
+    const long long stride = (long long)gridDim.x * HIP_SUB_THREADS;
+    for (long long i = (long long)blockIdx.x * HIP_SUB_THREADS + threadIdx.x; i < n3; i += stride) {
+        const float u = (float)(unsigned)(hip_sm64(seed, (unsigned long long)i) >> 40) * 5.9604644775390625e-08f;
+        out[i] = __fmul_rn(u, Lf);
+    }
+}
+
+cudaError_t hip_launch_uniform_randoms(float *d_out, long long n_r, double L, unsigned long long seed,
+                                       cudaStream_t st)
+{
+    if (n_r <= 0) return cudaSuccess;
+    const long long n3 = 3 * n_r;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (n3 + HIP_SUB_THREADS - 1) / HIP_SUB_THREADS;
+    const unsigned blocks = (unsigned)std::min<long long>(want, (long long)sms * 16);
+    k_uniform_randoms<<<blocks, HIP_SUB_THREADS, 0, st>>>(d_out, n3, seed, (float)L);
+    return cudaGetLastError();
 }
 
 // counts[b] = kept particles of chunk b (HIP_SUB_CHUNK particles per block)
@@ -182,5 +217,34 @@ extern "C" hip_status hip_subsample(const float *pos, const float *w, int64_t N,
         return HIP_ERR_CUDA;
     }
     *n_out = total;
+    return HIP_OK;
+}
+
+extern "C" hip_status hip_uniform_randoms(float *out, int64_t N_r, double L, uint64_t seed, void *cuda_stream)
+{
+    hip_clear_error();
+    if (!out || N_r < 0 || N_r > 2000000000LL) return HIP_ERR_ARG;
+    if (!(L > 0.0) || !std::isfinite(L) || !((float)L < 3.0e38f)) return HIP_ERR_RANGE;
+    std::lock_guard<std::mutex> lk(hip_api_mutex());
+    int dev = 0;
+    hip_status hs = hip_device_setup(&dev);
+    if (hs != HIP_OK) return hs;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const bool dout = hip_is_device_ptr(out);
+    float *d = out;
+    if (!dout && N_r > 0) {
+        Workspace &ws = hip_workspace(dev);
+        if ((hs = ws.reserve(sizeof(float) * 3 * (size_t)N_r, st)) != HIP_OK) return hs;
+        d = (float *)ws.base;
+    }
+    cudaError_t e = hip_launch_uniform_randoms(d, N_r, L, seed, st);
+    if (e == cudaSuccess && !dout && N_r > 0)
+        e = cudaMemcpyAsync(out, d, sizeof(float) * 3 * (size_t)N_r, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        hip_set_error("uniform randoms", e);
+        cudaGetLastError();
+        return HIP_ERR_CUDA;
+    }
     return HIP_OK;
 }

@@ -486,6 +486,29 @@ def test_subsample_fraction_and_limits():
     assert not (small & ~big).any()
 
 
+def test_uniform_randoms_generator():
+    # the seeded random catalog: each coordinate is the top 24 bits of one SplitMix64
+    # output (published first outputs for seed 0 above) scaled by L in one float32 product
+    r = oracle.uniform_randoms(1, 1.0, 0)
+    assert [float(x) for x in r[0]] == [(0xE220A8397B1DCDAF >> 40) / 2.0 ** 24, (0x6E789E6AA1B965F4 >> 40) / 2.0 ** 24,
+                                      (0x06C45D188009454F >> 40) / 2.0 ** 24]
+    n, L = 300_000, 1000.0
+    x = oracle.uniform_randoms(n, L, 2024).astype(np.float64)
+    assert x.shape == (n, 3) and x.min() >= 0.0 and x.max() < L
+    # uniform in the box: means, variances and the occupation of 10^3 sub-cells
+    assert np.all(np.abs(x.mean(axis=0) - L / 2) < 6.0 * L / np.sqrt(12 * n))
+    assert np.all(np.abs(x.var(axis=0) / L ** 2 - 1 / 12) < 6.0 * np.sqrt(1 / 180 / n))
+    counts = np.bincount((np.floor(x / (L / 10)).astype(int) @ np.array([100, 10, 1])), minlength=1000)
+    chi2 = float(np.sum((counts - n / 1000) ** 2 / (n / 1000)))
+    assert 800 < chi2 < 1200
+    # the largest variate times L stays below L for L a power of two and otherwise
+    top = np.float32(1.0 - 2.0 ** -24)
+    for Lt in (1.0, 1000.0, 1024.0, 777.77, 3.0e5):
+        assert top * np.float32(Lt) < np.float32(Lt)
+    # seeds give different catalogs
+    assert not np.array_equal(oracle.uniform_randoms(10, L, 1), oracle.uniform_randoms(10, L, 2))
+
+
 # ------------------------------------------- estimator assembly (l > 0) -------
 # The pins above check the raw pair and primary sums; these run the oracle's
 # finalize functions (power_from_pairs, bispectrum_from_sums via bispectrum) and

@@ -1,10 +1,14 @@
 """The random subsample of Sec. 9 (hip_subsample) against the oracle's SplitMix64
 selection: the kept set must be bit-exact, and the power spectrum of the
-subsample must equal the oracle's on the oracle-selected subsample."""
+subsample must equal the oracle's on the oracle-selected subsample.  The seeded
+random catalog (hip_uniform_randoms, hip_bispectrum_seeded) against the oracle's
+generator: bit-exact positions, and the seeded bispectrum equal to the one with
+the same randoms passed in."""
 import numpy as np
 import pytest
 
 import oracle
+import parity_metrics
 from paper_2005_01739_gb300 import binding, catalogs
 
 pytestmark = pytest.mark.gpu
@@ -60,3 +64,41 @@ def test_bad_fraction():
         with pytest.raises(binding.HipError) as ei:
             binding.hip_subsample(pos, None, f, 1)
         assert ei.value.status == binding.HIP_ERR_RANGE
+
+
+@pytest.mark.parametrize("n_r,L,seed", [(1, 1.0, 0), (5, 1000.0, 7), (100_003, 777.77, 2 ** 64 - 1)])
+def test_uniform_randoms_bit_exact(n_r, L, seed):
+    import torch
+    ref = oracle.uniform_randoms(n_r, L, seed)
+    d = binding.hip_uniform_randoms(n_r, L, seed, device="cuda")
+    h = binding.hip_uniform_randoms(n_r, L, seed)
+    assert np.array_equal(d.cpu().numpy(), ref) and np.array_equal(h, ref)
+
+
+def test_uniform_randoms_rejects():
+    import ctypes
+    lib = binding.load()
+    buf = np.empty(3, np.float32)
+    for n_r, L, status in ((1, 0.0, binding.HIP_ERR_RANGE), (1, float("inf"), binding.HIP_ERR_RANGE),
+                           (1, float("nan"), binding.HIP_ERR_RANGE), (-1, 1.0, binding.HIP_ERR_ARG)):
+        assert lib.hip_uniform_randoms(buf.ctypes.data_as(ctypes.c_void_p), n_r, L, 1, None) == status
+    assert lib.hip_uniform_randoms(None, 1, 1.0, 1, None) == binding.HIP_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_bispectrum_seeded_equals_explicit_randoms(prec):
+    # the seeded entry point is hip_bispectrum on hip_uniform_randoms' catalog; against the oracle too
+    import torch
+    pos, w = catalogs.thomas(2500, 70.0, 60, 1.0, seed=515, background_frac=0.3, weights="u05_15")
+    L, R0, edges, n_r, seed = 70.0, 14.0, catalogs.linear_edges(0.3, 2.0, 10), 7500, 99
+    dpos, dw = torch.from_numpy(pos).cuda(), torch.from_numpy(w).cuda()
+    Bs, (nds, nrs) = binding.hip_bispectrum_seeded(dpos, dw, n_r, seed, L, R0, edges, 4, prec)
+    rnd = oracle.uniform_randoms(n_r, L, seed)
+    Be, (nde, nre) = binding.hip_bispectrum(dpos, dw, torch.from_numpy(rnd).cuda(), L, R0, edges, 4, prec)
+    assert (nds, nrs) == (nde, nre)
+    # the same inputs through the same kernels: equal up to the order of the atomic adds
+    # (FP32 sums in the mixed path, FP64 in the plain one)
+    assert np.max(np.abs(Bs - Be)) <= {"mixed": 1e-6, "fp64": 1e-12}[prec] * np.max(np.abs(Be))
+    Bref, _ = oracle.bispectrum(pos.astype(np.float64), w.astype(np.float64), rnd.astype(np.float64), L, R0, edges, 4)
+    err = parity_metrics.report("B", Bs, Bref, "seeded " + prec)["floored"]
+    assert err < {"mixed": 1e-4, "fp64": 1e-10}[prec]
